@@ -1,0 +1,242 @@
+/*
+ * dem.h -- C ABI of libdem, a GB300 (sm_103a) implementation of the
+ * discrete element method for conservative, faceted (rounded polygon and
+ * polyhedron) particles of Spellings, Marson, Anderson & Glotzer,
+ * arXiv:1607.02427.
+ *
+ * What the library computes (Section "Model"):
+ *   Each particle is an inner convex polygon (2D) or polyhedron (3D) rounded
+ *   by a disk/sphere of radius sigma/2.  Particles i and j interact through
+ *   the WCA potential (Eq. LJ, Eq. WCA; r_cut = 2^(1/6) sigma) evaluated at
+ *   the nearest-point distance of every feature pair:
+ *     3D (Eq. DEM):    all edge-edge pairs, all vertex(i)-face(j) pairs and
+ *                      all vertex(j)-face(i) pairs;
+ *     2D (Eq. DEM_2D): all vertex(i)-edge(j) and vertex(j)-edge(i) pairs.
+ *   Each term's force acts along the line joining its nearest points, and
+ *   its torque about each particle's centre uses that particle's nearest
+ *   point.  Nearly parallel edges interact at the midpoint of their overlap
+ *   (parallel-edge rule, Section "Model").  Feature overcounting is kept
+ *   (Section "Model").  Two one-vertex shapes (disks/spheres) interact
+ *   through one central WCA term (the sphere limit).
+ *   The particles move with velocity Verlet and a symmetric body-axis
+ *   free-rotor splitting (a second-order integrator, Section "Energy
+ *   Conservation"), optionally coupled to a Nose-Hoover thermostat acting
+ *   on translational and rotational degrees of freedom (Section
+ *   "Assembly").
+ *
+ * Conventions for every call:
+ *   * Returns DEM_OK (0) or a negative DEM_ERR_* code; dem_last_error()
+ *     gives a one-line reason.  Nothing throws across the ABI.
+ *   * "host" arrays are read or written during the call and never kept.
+ *     When a call takes device_ptrs = 1 the same arrays are CUDA device
+ *     pointers (for example torch tensors) instead; they are used on the
+ *     context's stream and must stay valid until the call returns.
+ *   * The library owns all of its device memory; dem_destroy frees it.
+ *   * N is the total particle count over all replicas; particles of replica
+ *     r are the contiguous block after those of replicas 0..r-1.
+ *   * dim is 2 or 3 and is the same for every shape of a context.
+ *   * Positions are periodic in each replica's orthorhombic box [0, L_a).
+ *   * Orientation: 3D unit quaternion (w, x, y, z) rotating body to world;
+ *     2D angle theta (radians).
+ *   * Angular momentum: 3D world-frame vector; 2D scalar L_z.
+ *   * Mass and inertia: per shape; shapes must be given in their principal
+ *     axes (the inertia tensor of the body frame is diagonal).
+ *   * All floating-point values cross the ABI as double.
+ */
+#ifndef DEM_H
+#define DEM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define DEM_OK 0
+#define DEM_ERR_ARG (-1)             /* invalid argument or shape             */
+#define DEM_ERR_CUDA (-2)            /* a CUDA call failed                     */
+#define DEM_ERR_NONFINITE (-3)       /* a force, torque or energy is not finite */
+#define DEM_ERR_NLIST_OVERFLOW (-4)  /* neighbour list still overflowing after
+                                        growing it and retrying the call       */
+#define DEM_ERR_TIMEOUT (-5)         /* a bounded device wait gave up          */
+#define DEM_ERR_BOX (-6)             /* box below twice the neighbour cutoff   */
+#define DEM_ERR_STATE (-7)           /* no state set yet                       */
+#define DEM_ERR_NOMEM (-8)           /* device allocation failed               */
+
+/* ---- precision modes of the pair kernel ---- */
+#define DEM_FP64 0        /* geometry, force and accumulation in FP64            */
+#define DEM_FP32 1        /* geometry and force in FP32, plain FP32 sums        */
+#define DEM_FP32_COMP 2   /* geometry and force in FP32, compensated (two-sum)
+                             FP32 sums of force and torque                      */
+/* In every mode positions, velocities, orientations, angular momenta,
+ * per-particle energies and virials are held in FP64, and the pair
+ * separation x_j - x_i is formed in FP64 before it is rounded. */
+
+/* ---- ensembles ---- */
+#define DEM_NVE 0
+#define DEM_NVT 1
+
+/* ---- pair-kernel decompositions (parameter "decomp") ---- */
+#define DEM_DECOMP_AUTO 0    /* chosen by dem_autotune (default: THREAD)        */
+#define DEM_DECOMP_THREAD 1  /* one thread walks all neighbours of particle i   */
+#define DEM_DECOMP_WARP 2    /* one warp per particle i; lanes split the
+                                (neighbour, feature) work; warp-shuffle sums   */
+#define DEM_DECOMP_TILED 3   /* one warp per ordered pair (i, j); lanes take i's
+                                features as in Section "Algorithm"; a segmented
+                                sum over i's neighbours                        */
+
+typedef struct dem_ctx dem_ctx;   /* opaque; owned by the library */
+
+/* A shape (Section "Model": features V, E, F of the inner shape, rounded by
+ * radius sigma/2).
+ *   dim            2 or 3
+ *   n_verts        number of vertices, >= 1 (1 = disk / sphere)
+ *   verts          n_verts * dim body-frame coordinates, centred on the
+ *                  centre of mass, in principal axes
+ *   n_faces        3D: number of faces (0 for a sphere, else >= 4);
+ *                  2D: ignored (the polygon is the vertex loop, counter-
+ *                  clockwise; 2 vertices make one edge)
+ *   face_offsets   3D: n_faces + 1 offsets into face_verts
+ *   face_verts     3D: vertex indices of each face, counter-clockwise seen
+ *                  from outside; faces must be convex and planar
+ *   rounding_radius  sigma/2 of the shape (> 0)
+ *   mass           > 0
+ *   inertia        3D: 3 principal moments, 2D: 1 (I_z); NULL derives them
+ *                  for a uniform-density inner solid of the given mass.
+ * The inner shape must be convex.  3D edges are derived from the faces. */
+typedef struct dem_shape {
+    int dim;
+    int n_verts;
+    const double *verts;
+    int n_faces;
+    const int *face_offsets;
+    const int *face_verts;
+    double rounding_radius;
+    double mass;
+    const double *inertia;
+} dem_shape;
+
+/* Create a context for n_replicas independent periodic systems.
+ *   shapes/n_shapes  shape table (copied)
+ *   epsilon          WCA energy scale (Eq. LJ)
+ *   sigma            > 0: one sigma for all pairs; <= 0: sigma_ij =
+ *                    rounding_i + rounding_j (Eq. WCA's rounding radius
+ *                    sigma_ij / 2 per particle)
+ *   box              n_replicas * dim box lengths
+ *   replica_sizes    n_replicas particle counts (>= 1 each)
+ *   precision        DEM_FP64, DEM_FP32 or DEM_FP32_COMP
+ * Errors: DEM_ERR_ARG (bad shape, sizes, precision, box), DEM_ERR_CUDA,
+ * DEM_ERR_NOMEM.  On error *out is NULL.  Whether each box is large enough
+ * is checked by dem_set_state, once the shape of every particle is known. */
+int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsilon,
+               double sigma, const double *box, int n_replicas, const int *replica_sizes,
+               int precision);
+
+/* Set the state of all N particles (host or device arrays):
+ *   shape_id  N ints in [0, n_shapes)
+ *   pos       N * dim (wrapped into the box by the library)
+ *   orient    3D: N * 4 quaternions (w,x,y,z), normalised by the library;
+ *             2D: N angles
+ *   vel       N * dim
+ *   angmom    3D: N * 3 world-frame angular momenta; 2D: N values of L_z
+ * Rebuilds the neighbour list, evaluates forces, and resets the thermostat
+ * variables to zero.  Errors: DEM_ERR_ARG, DEM_ERR_BOX (a box edge below
+ * twice the neighbour-list cutoff R_i + R_j + r_cut + skin of the replica's
+ * largest shapes), DEM_ERR_CUDA, DEM_ERR_NONFINITE. */
+int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const double *orient,
+                  const double *vel, const double *angmom, int device_ptrs);
+
+/* Read the state (host or device arrays; any pointer may be NULL):
+ * pos N*dim, orient N*4 (3D) or N (2D), vel N*dim, angmom N*3 (3D, world
+ * frame) or N (2D), thermostat n_replicas * 2 (xi, eta). */
+int dem_get_state(dem_ctx *ctx, double *pos, double *orient, double *vel, double *angmom,
+                  double *thermostat, int device_ptrs);
+
+/* Set the Nose-Hoover variables (xi, eta) of each replica (host array,
+ * n_replicas * 2).  xi is the friction coefficient, eta its time integral. */
+int dem_set_thermostat(dem_ctx *ctx, const double *thermostat);
+
+/* Advance all replicas n steps of size dt.
+ *   ensemble  DEM_NVE, or DEM_NVT (Nose-Hoover at temperature kT with
+ *             time constant tau_T: dxi/dt = (2K/(g kT) - 1) / tau_T^2,
+ *             g = dim (N_r - 1) + rotational degrees of freedom)
+ * One step: thermostat half step (NVT), half kick of v and L, drift and
+ * free rotation, neighbour-list rebuild if some particle moved more than
+ * skin/2 since the last build, pair forces, half kick, thermostat half step.
+ * Errors: DEM_ERR_STATE, DEM_ERR_NONFINITE, DEM_ERR_NLIST_OVERFLOW (after
+ * an internal grow-and-retry from the state at the start of the call),
+ * DEM_ERR_CUDA. */
+int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T);
+
+/* Evaluate forces, torques, energies and virials at the current state. */
+int dem_compute(dem_ctx *ctx);
+
+/* Forces (N*dim, world frame) and torques about each centre (3D N*3 world
+ * frame; 2D N) of the last force evaluation. */
+int dem_get_forces(dem_ctx *ctx, double *force, double *torque, int device_ptrs);
+
+/* Per-replica totals (host arrays of n_replicas, any may be NULL):
+ * potential energy U (sum over pairs of Eq. DEM / Eq. DEM_2D), kinetic
+ * energy K (translational + rotational) and the conserved quantity
+ * (K + U in NVE; K + U + g kT (tau_T^2 xi^2 / 2 + eta) after an NVT call).
+ * Per-particle energies (N, half of each pair's energy to each particle)
+ * may be read with dem_get_particle_energy. */
+int dem_get_energy(dem_ctx *ctx, double *per_replica_U, double *per_replica_K,
+                   double *conserved);
+int dem_get_particle_energy(dem_ctx *ctx, double *energy, int device_ptrs);
+
+/* Per-replica centre-of-mass pair virial W = sum_{i<j} x_ij (x) f_ij
+ * (x_ij = x_i - x_j, f_ij the force of j on i), symmetric part as 6 values
+ * xx, xy, xz, yy, yz, zz (2D: xx, xy, 0, yy, 0, 0).  Host array of
+ * n_replicas * 6.  The pressure of an MD barostat follows from it
+ * (Section "Assembly"). */
+int dem_get_virial(dem_ctx *ctx, double *per_replica_W6);
+
+/* Change the boxes (host array n_replicas * dim), scaling centre positions
+ * affinely; rebuilds the neighbour list and re-evaluates forces.
+ * Errors: DEM_ERR_ARG, DEM_ERR_BOX. */
+int dem_set_box(dem_ctx *ctx, const double *box);
+
+/* Named numeric parameters:
+ *   "skin"        neighbour-list skin (default: the largest sigma_ij)
+ *   "par_eps"     squared-sine threshold of the parallel-edge rule (1e-6)
+ *   "decomp"      DEM_DECOMP_* of the pair kernel
+ *   "block"       threads per block of the pair kernel (0 = default)
+ *   "graph"       1 = replay each step as a captured CUDA graph (default 1)
+ *   "nlist_cap"   neighbour slots per particle (grown automatically)
+ * Setting an unknown name or an invalid value returns DEM_ERR_ARG. */
+int dem_set_param(dem_ctx *ctx, const char *name, double value);
+int dem_get_param(dem_ctx *ctx, const char *name, double *value);
+
+/* Run every pair-kernel decomposition and block size on the current state
+ * and keep the fastest (timed with CUDA events).  Results are identical for
+ * every choice up to floating-point summation order. */
+int dem_autotune(dem_ctx *ctx);
+
+/* Work counters of the last force evaluation (host array of 4 long longs):
+ * [0] ordered particle pairs within the bounding-sphere range,
+ * [1] feature pairs of those ordered pairs (the work Eq. DEM defines),
+ * [2] feature pairs with r < r_cut, [3] neighbour-list rebuilds so far.
+ * Counting runs a separate instrumented evaluation (not the timed path). */
+int dem_get_counters(dem_ctx *ctx, long long *counts);
+
+/* Use this CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream()).
+ * NULL selects the library's own stream. */
+int dem_set_stream(dem_ctx *ctx, void *stream);
+
+/* Host-only helper, no GPU needed: derived properties of a shape:
+ * out[0] circumradius of the inner shape, out[1] number of edges,
+ * out[2..4] principal moments of the uniform inner solid of the shape's
+ * mass (2D: out[2] = I_z), out[5] inner volume (3D) or area (2D),
+ * out[6] largest off-diagonal inertia element (0 in principal axes). */
+int dem_shape_info(const dem_shape *shape, double *out);
+
+/* One-line description of the last error of ctx (or of the last failed
+ * dem_create when ctx is NULL). */
+const char *dem_last_error(const dem_ctx *ctx);
+
+void dem_destroy(dem_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEM_H */

@@ -1,0 +1,1145 @@
+// api.cu -- the C ABI of libdem (include/dem.h): context lifetime, shape
+// preprocessing, state transfer and the per-step launch sequence, replayed
+// as a captured CUDA graph.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "dem_internal.cuh"
+
+using namespace dem;
+
+namespace {
+
+constexpr double WCA_CUT = 1.122462048309373;   // 2^(1/6)
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------------------
+// Shape preprocessing (host)
+// ---------------------------------------------------------------------------
+struct HostGeom {
+    int dim = 3;
+    std::vector<double> v;                // nv * 3
+    std::vector<std::vector<int>> faces;  // 3D
+    std::vector<std::pair<int, int>> edges;
+    double R = 0.0;
+};
+
+struct HostShape {
+    int geom = 0;
+    double rounding = 0, mass = 1, inertia[3] = {0, 0, 0};
+    double R = 0;
+    double volume = 0, offdiag = 0;
+};
+
+struct D3 { double x, y, z; };
+static D3 d3(const double *p) { return {p[0], p[1], p[2]}; }
+static D3 sub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+static D3 add(D3 a, D3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+static D3 scl(D3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+static double dotp(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static D3 crossp(D3 a, D3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+static double norm(D3 a) { return sqrt(dotp(a, a)); }
+
+// Validate one shape, derive its geometry (edges, circumradius) and, when
+// not given, the principal moments of the uniform inner solid.  The
+// integrals use the divergence theorem over a fan of simplices from the
+// origin: for a tetrahedron (0, a, b, c),
+//   int x x^T dV = det/120 (a a^T + b b^T + c c^T + s s^T), s = a + b + c,
+// and for a triangle (0, a, b), int x x^T dA = det/24 (a a^T + b b^T + s s^T).
+static int preprocess_shape(const dem_shape &s, HostGeom *g, HostShape *h, std::string *err) {
+    char buf[256];
+    auto fail = [&](const char *fmt, ...) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        *err = buf;
+        return DEM_ERR_ARG;
+    };
+    if (s.dim != 2 && s.dim != 3) return fail("shape dim must be 2 or 3");
+    if (s.n_verts < 1 || s.n_verts > MAX_VERTS) return fail("shape needs 1..%d vertices", MAX_VERTS);
+    if (!s.verts) return fail("shape vertices missing");
+    if (!(s.rounding_radius > 0.0)) return fail("rounding radius must be > 0");
+    if (!(s.mass > 0.0)) return fail("mass must be > 0");
+    g->dim = s.dim;
+    g->v.assign(3 * s.n_verts, 0.0);
+    for (int k = 0; k < s.n_verts; ++k)
+        for (int a = 0; a < s.dim; ++a) {
+            double x = s.verts[s.dim * k + a];
+            if (!isfinite(x)) return fail("non-finite vertex");
+            g->v[3 * k + a] = x;
+        }
+    g->R = 0.0;
+    for (int k = 0; k < s.n_verts; ++k) g->R = std::max(g->R, norm(d3(&g->v[3 * k])));
+    const int nv = s.n_verts;
+    double I[3][3] = {{0}};
+    double vol = 0.0;
+    D3 cen = {0, 0, 0};
+    if (s.dim == 2) {
+        if (nv == 2) g->edges.push_back({0, 1});
+        if (nv >= 3) {
+            for (int k = 0; k < nv; ++k) g->edges.push_back({k, (k + 1) % nv});
+            // counter-clockwise and convex: every turn is a left turn
+            for (int k = 0; k < nv; ++k) {
+                D3 a = d3(&g->v[3 * k]), b = d3(&g->v[3 * ((k + 1) % nv)]),
+                   c = d3(&g->v[3 * ((k + 2) % nv)]);
+                if (crossp(sub(b, a), sub(c, b)).z <= 0.0)
+                    return fail("2D polygon must be convex and counter-clockwise");
+            }
+            for (int k = 0; k < nv; ++k) {
+                D3 a = d3(&g->v[3 * k]), b = d3(&g->v[3 * ((k + 1) % nv)]);
+                double det = a.x * b.y - a.y * b.x;
+                vol += det / 2.0;
+                cen = add(cen, scl(add(a, b), det / 6.0));
+                D3 sv = add(a, b);
+                double xx = a.x * a.x + b.x * b.x + sv.x * sv.x;
+                double yy = a.y * a.y + b.y * b.y + sv.y * sv.y;
+                double xy = a.x * a.y + b.x * b.y + sv.x * sv.y;
+                I[0][0] += det / 24.0 * yy;   // int y^2
+                I[1][1] += det / 24.0 * xx;   // int x^2
+                I[0][1] -= det / 24.0 * xy;
+                I[2][2] += det / 24.0 * (xx + yy);
+            }
+        }
+        if (nv == 2) {   // thin rod: I_z = m L^2 / 12 about its midpoint
+            D3 a = d3(&g->v[0]), b = d3(&g->v[3]);
+            double L = norm(sub(b, a));
+            I[2][2] = L * L / 12.0;
+            vol = 1.0;   // mass normalisation below uses the per-length measure
+            cen = scl(add(a, b), 0.5);
+        }
+    } else {
+        if (nv == 1) {
+            if (s.n_faces != 0) return fail("a one-vertex 3D shape has no faces");
+        } else {
+            if (s.n_faces < 4 || !s.face_offsets || !s.face_verts)
+                return fail("3D polyhedron needs >= 4 faces");
+            for (int f = 0; f < s.n_faces; ++f) {
+                int b = s.face_offsets[f], e = s.face_offsets[f + 1];
+                if (e - b < 3 || e - b > MAX_FACE_VERTS)
+                    return fail("face %d must have 3..%d vertices", f, MAX_FACE_VERTS);
+                std::vector<int> loop;
+                for (int k = b; k < e; ++k) {
+                    int idx = s.face_verts[k];
+                    if (idx < 0 || idx >= nv) return fail("face vertex index out of range");
+                    loop.push_back(idx);
+                }
+                g->faces.push_back(loop);
+            }
+            // edges: distinct vertex pairs adjacent on a face loop
+            for (auto &loop : g->faces)
+                for (size_t k = 0; k < loop.size(); ++k) {
+                    int a = loop[k], b = loop[(k + 1) % loop.size()];
+                    std::pair<int, int> e = {std::min(a, b), std::max(a, b)};
+                    if (std::find(g->edges.begin(), g->edges.end(), e) == g->edges.end())
+                        g->edges.push_back(e);
+                }
+            if ((int)g->edges.size() > 3 * MAX_VERTS) return fail("too many edges");
+            // faces planar, convex, counter-clockwise seen from outside
+            D3 vc = {0, 0, 0};
+            for (int k = 0; k < nv; ++k) vc = add(vc, d3(&g->v[3 * k]));
+            vc = scl(vc, 1.0 / nv);
+            double scale = g->R > 0 ? g->R : 1.0;
+            for (auto &loop : g->faces) {
+                size_t m = loop.size();
+                D3 n = {0, 0, 0};
+                for (size_t k = 0; k < m; ++k)
+                    n = add(n, crossp(d3(&g->v[3 * loop[k]]), d3(&g->v[3 * loop[(k + 1) % m]])));
+                double ln = norm(n);
+                if (!(ln > 0)) return fail("degenerate face");
+                n = scl(n, 1.0 / ln);
+                D3 a0 = d3(&g->v[3 * loop[0]]);
+                for (size_t k = 0; k < m; ++k)
+                    if (fabs(dotp(sub(d3(&g->v[3 * loop[k]]), a0), n)) > 1e-9 * scale)
+                        return fail("face is not planar");
+                if (dotp(sub(a0, vc), n) <= 0.0)
+                    return fail("face normal points inward (faces must be counter-clockwise from outside)");
+                for (size_t k = 0; k < m; ++k) {
+                    D3 p = d3(&g->v[3 * loop[k]]), q = d3(&g->v[3 * loop[(k + 1) % m]]),
+                       r = d3(&g->v[3 * loop[(k + 2) % m]]);
+                    if (dotp(crossp(sub(q, p), sub(r, q)), n) <= 0.0) return fail("face is not convex");
+                }
+                // solid integrals over the fan tetrahedra (origin, a0, a_k, a_k+1)
+                for (size_t k = 1; k + 1 < m; ++k) {
+                    D3 a = a0, b = d3(&g->v[3 * loop[k]]), c = d3(&g->v[3 * loop[k + 1]]);
+                    double det = dotp(a, crossp(b, c));
+                    vol += det / 6.0;
+                    cen = add(cen, scl(add(add(a, b), c), det / 24.0));
+                    D3 sv = add(add(a, b), c);
+                    double P[3][3];
+                    const D3 vs[4] = {a, b, c, sv};
+                    for (int r_ = 0; r_ < 3; ++r_)
+                        for (int c_ = 0; c_ < 3; ++c_) {
+                            double acc = 0;
+                            for (int t = 0; t < 4; ++t) {
+                                const double *pt = &vs[t].x;
+                                acc += pt[r_] * pt[c_];
+                            }
+                            P[r_][c_] = det / 120.0 * acc;
+                        }
+                    double tr = P[0][0] + P[1][1] + P[2][2];
+                    for (int r_ = 0; r_ < 3; ++r_)
+                        for (int c_ = 0; c_ < 3; ++c_) I[r_][c_] += (r_ == c_ ? tr : 0.0) - P[r_][c_];
+                }
+            }
+        }
+    }
+    h->R = g->R;
+    h->rounding = s.rounding_radius;
+    h->mass = s.mass;
+    h->volume = vol;
+    double off = 0.0, trace = 0.0;
+    if (vol > 0.0) {
+        for (int r_ = 0; r_ < 3; ++r_)
+            for (int c_ = 0; c_ < 3; ++c_) I[r_][c_] *= s.mass / vol;
+        cen = scl(cen, 1.0 / vol);
+        off = std::max(fabs(I[0][1]), std::max(fabs(I[0][2]), fabs(I[1][2])));
+        trace = I[0][0] + I[1][1] + I[2][2];
+    }
+    h->offdiag = off;
+    if (s.inertia) {
+        if (s.dim == 3) {
+            for (int k = 0; k < 3; ++k) {
+                if (!(s.inertia[k] >= 0.0)) return fail("inertia must be >= 0");
+                h->inertia[k] = s.inertia[k];
+            }
+        } else {
+            if (!(s.inertia[0] >= 0.0)) return fail("inertia must be >= 0");
+            h->inertia[0] = h->inertia[1] = 0.0;
+            h->inertia[2] = s.inertia[0];
+        }
+    } else {
+        if (vol > 0.0 && norm(cen) > 1e-9 * (g->R > 0 ? g->R : 1.0))
+            return fail("vertices must be centred on the centre of mass");
+        // in 2D only I_z is used, so any body frame will do
+        if (s.dim == 3 && off > 1e-9 * (trace > 0 ? trace : 1.0))
+            return fail("shape is not in principal axes; pass the inertia explicitly");
+        if (s.dim == 3) {
+            for (int k = 0; k < 3; ++k) h->inertia[k] = I[k][k];
+        } else {
+            h->inertia[0] = h->inertia[1] = 0.0;
+            h->inertia[2] = I[2][2];
+        }
+    }
+    return DEM_OK;
+}
+
+bool same_geom(const HostGeom &a, const HostGeom &b) {
+    return a.dim == b.dim && a.v == b.v && a.faces == b.faces;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct dem_ctx {
+    int dim = 3, n_shapes = 0, R = 0, N = 0, precision = DEM_FP32_COMP;
+    double eps = 1.0, sigma = 0.0;
+    std::vector<HostGeom> geoms;
+    std::vector<HostShape> shapes;
+    std::vector<int> sizes, offs;
+    std::vector<double> box;   // R * 3
+    std::vector<Rep> reps;
+    std::vector<int> shape_host;
+    int n_cells = 0;
+    // parameters
+    double skin = -1, par_eps = 1e-6;
+    int decomp = DEM_DECOMP_THREAD, block = 0, use_graph = 1, cap = 0, cell_cap = 0;
+    bool cap_fixed = false;   // capacity set explicitly: grown only on overflow
+    // stream / graph
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    double g_dt = 0, g_kT = 0, g_tau = 0;
+    int g_ens = -1;
+    // thermostat parameters of the last NVT call (conserved quantity)
+    double last_kT = 1.0, last_tau = 1.0;
+    int last_ens = DEM_NVE;
+    // device memory
+    double4_32a *pos = nullptr, *vel = nullptr, *quat = nullptr, *angmom = nullptr;
+    double4_32a *force = nullptr, *torque = nullptr, *x_last = nullptr;
+    float4 *quatf = nullptr;
+    int *shape = nullptr, *rep = nullptr, *nlist = nullptr, *nn = nullptr;
+    int *cell_count = nullptr, *cell_slots = nullptr;
+    double *energy = nullptr, *virial = nullptr, *ke = nullptr;
+    double *staging = nullptr;        // N * 4 doubles
+    double *red = nullptr;            // R * 6 doubles
+    double *scale3 = nullptr;         // R * 3
+    Status *status = nullptr;
+    Thermo *thermo = nullptr;
+    Rep *d_reps = nullptr;
+    ShapeDev *d_shapes = nullptr;
+    Geom *d_geoms = nullptr;
+    void *d_table = nullptr;
+    int *d_itable = nullptr;
+    unsigned long long *d_counters = nullptr;
+    int table_len = 0, itable_len = 0, n_geoms = 0;
+    // snapshot for the overflow retry
+    double4_32a *snap = nullptr;
+    Thermo *snap_thermo = nullptr;
+    bool have_state = false;
+    long long rebuilds = 0;
+    std::string err;
+};
+
+namespace {
+
+int set_err(dem_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return set_err(ctx, e_ == cudaErrorMemoryAllocation ? DEM_ERR_NOMEM : DEM_ERR_CUDA, \
+                           "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+template <class T> cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+void free_graph(dem_ctx *ctx) {
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+    ctx->g_ens = -1;
+}
+
+// Upload geometry tables (FP64 and FP32 copies) and per-shape records.
+int upload_tables(dem_ctx *ctx) {
+    std::vector<double4_32a> tab;
+    std::vector<int> itab;
+    std::vector<Geom> gd;
+    for (auto &g : ctx->geoms) {
+        Geom G = {};
+        G.nv = (int)(g.v.size() / 3);
+        G.ne = (int)g.edges.size();
+        G.nf = (int)g.faces.size();
+        // conservative (slightly enlarged) radii for the exact culls
+        G.R = (float)(g.R * (1.0 + 1e-6) + 1e-7);
+        G.v_off = (int)tab.size();
+        for (int k = 0; k < G.nv; ++k) tab.push_back(make_double4_32a(g.v[3 * k], g.v[3 * k + 1], g.v[3 * k + 2], 0.0));
+        G.e_off = (int)tab.size();
+        for (auto &e : g.edges) {
+            D3 a = d3(&g.v[3 * e.first]), b = d3(&g.v[3 * e.second]);
+            D3 d = sub(b, a);
+            double ln = norm(d);
+            tab.push_back(make_double4_32a(a.x, a.y, a.z, 0.5 * ln * (1.0 + 1e-5) + 1e-6));
+            tab.push_back(make_double4_32a(d.x, d.y, d.z, 1.0 / (ln * ln)));
+        }
+        G.f_off = (int)tab.size();
+        std::vector<D3> normals;
+        for (auto &loop : g.faces) {
+            size_t m = loop.size();
+            D3 n = {0, 0, 0};
+            for (size_t k = 0; k < m; ++k)
+                n = add(n, crossp(d3(&g.v[3 * loop[k]]), d3(&g.v[3 * loop[(k + 1) % m]])));
+            n = scl(n, 1.0 / norm(n));
+            normals.push_back(n);
+            tab.push_back(make_double4_32a(n.x, n.y, n.z, dotp(n, d3(&g.v[3 * loop[0]]))));
+        }
+        G.fe_off = (int)tab.size();
+        G.fi_off = (int)itab.size();
+        int nfe = 0;
+        for (size_t f = 0; f < g.faces.size(); ++f) {
+            auto &loop = g.faces[f];
+            size_t m = loop.size();
+            itab.push_back((int)tab.size());
+            itab.push_back((int)m);
+            for (size_t k = 0; k < m; ++k) {
+                D3 a = d3(&g.v[3 * loop[k]]), b = d3(&g.v[3 * loop[(k + 1) % m]]);
+                D3 e = sub(b, a);
+                D3 mm = crossp(normals[f], e);
+                mm = scl(mm, 1.0 / norm(mm));
+                tab.push_back(make_double4_32a(a.x, a.y, a.z, 0.0));
+                tab.push_back(make_double4_32a(e.x, e.y, e.z, 1.0 / dotp(e, e)));
+                tab.push_back(make_double4_32a(mm.x, mm.y, mm.z, dotp(mm, a)));
+                ++nfe;
+            }
+        }
+        G.nfe = nfe;
+        gd.push_back(G);
+    }
+    if (itab.empty()) { itab.push_back(0); itab.push_back(0); }
+    ctx->table_len = (int)tab.size();
+    ctx->itable_len = (int)itab.size();
+    ctx->n_geoms = (int)gd.size();
+    CK(dalloc(&ctx->d_geoms, gd.size()));
+    CK(cudaMemcpy(ctx->d_geoms, gd.data(), sizeof(Geom) * gd.size(), cudaMemcpyHostToDevice));
+    CK(dalloc(&ctx->d_itable, itab.size()));
+    CK(cudaMemcpy(ctx->d_itable, itab.data(), sizeof(int) * itab.size(), cudaMemcpyHostToDevice));
+    if (ctx->precision == DEM_FP64) {
+        CK(dalloc((double4_32a **)&ctx->d_table, tab.size()));
+        CK(cudaMemcpy(ctx->d_table, tab.data(), sizeof(double4_32a) * tab.size(), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float4> tf(tab.size());
+        for (size_t k = 0; k < tab.size(); ++k)
+            tf[k] = make_float4((float)tab[k].x, (float)tab[k].y, (float)tab[k].z, (float)tab[k].w);
+        CK(dalloc((float4 **)&ctx->d_table, tf.size()));
+        CK(cudaMemcpy(ctx->d_table, tf.data(), sizeof(float4) * tf.size(), cudaMemcpyHostToDevice));
+    }
+    std::vector<ShapeDev> sd(ctx->shapes.size());
+    for (size_t s = 0; s < sd.size(); ++s) {
+        sd[s].geom = ctx->shapes[s].geom;
+        sd[s].R = gd[ctx->shapes[s].geom].R;
+        sd[s].rounding = ctx->shapes[s].rounding;
+        sd[s].mass = ctx->shapes[s].mass;
+        for (int k = 0; k < 3; ++k) sd[s].inertia[k] = ctx->shapes[s].inertia[k];
+    }
+    CK(dalloc(&ctx->d_shapes, sd.size()));
+    CK(cudaMemcpy(ctx->d_shapes, sd.data(), sizeof(ShapeDev) * sd.size(), cudaMemcpyHostToDevice));
+    return DEM_OK;
+}
+
+double sigma_pair(const dem_ctx *ctx, int a, int b) {
+    return ctx->sigma > 0 ? ctx->sigma : ctx->shapes[a].rounding + ctx->shapes[b].rounding;
+}
+
+double max_sigma(const dem_ctx *ctx) {
+    double m = 0;
+    for (int a = 0; a < ctx->n_shapes; ++a) m = std::max(m, sigma_pair(ctx, a, a));
+    return m;
+}
+
+// Cell grids, list cutoffs and degrees of freedom of every replica (needs the
+// shape of each particle).  Reallocates cell arrays and the list.
+int setup_replicas(dem_ctx *ctx) {
+    if (ctx->skin < 0) ctx->skin = max_sigma(ctx);
+    std::vector<Rep> reps(ctx->R);
+    int cell_off = 0;
+    double worst_ratio = 0;   // expected neighbours estimate
+    double worst_cell = 0;
+    for (int r = 0; r < ctx->R; ++r) {
+        Rep &rp = reps[r];
+        rp.off = ctx->offs[r];
+        rp.n = ctx->sizes[r];
+        double Rmax = 0, rnd_max = 0;
+        double g = ctx->dim * (rp.n - 1.0);
+        for (int i = rp.off; i < rp.off + rp.n; ++i) {
+            const HostShape &sh = ctx->shapes[ctx->shape_host[i]];
+            Rmax = std::max(Rmax, (double)ctx->geoms[sh.geom].R);
+            rnd_max = std::max(rnd_max, sh.rounding);
+            for (int k = 0; k < 3; ++k) g += sh.inertia[k] > 0.0 ? 1.0 : 0.0;
+        }
+        rp.g_dof = (int)g;
+        double sig = ctx->sigma > 0 ? ctx->sigma : 2 * rnd_max;
+        double rlist = 2 * Rmax * (1 + 1e-6) + WCA_CUT * sig + ctx->skin;
+        double vol = 1.0;
+        rp.allpairs = 0;
+        for (int a = 0; a < 3; ++a) {
+            rp.L[a] = a < ctx->dim ? ctx->box[3 * r + a] : 1.0;
+            if (a < ctx->dim) {
+                if (!(rp.L[a] >= 2.0 * rlist))
+                    return set_err(ctx, DEM_ERR_BOX,
+                                   "replica %d: box edge %g below twice the list cutoff %g", r,
+                                   rp.L[a], rlist);
+                rp.nc[a] = (int)floor(rp.L[a] / rlist);
+                if (rp.nc[a] < 3) rp.allpairs = 1;
+                vol *= rp.L[a];
+            } else {
+                rp.nc[a] = 1;
+            }
+        }
+        double rho = rp.n / vol;
+        double expect = ctx->dim == 3 ? 4.18879 * rlist * rlist * rlist * rho : 3.14159 * rlist * rlist * rho;
+        worst_ratio = std::max(worst_ratio, expect);
+        if (rp.allpairs) {
+            rp.nc[0] = rp.nc[1] = rp.nc[2] = 1;
+            rp.cell_off = cell_off;   // no cells used
+        } else {
+            rp.cell_off = cell_off;
+            cell_off += rp.nc[0] * rp.nc[1] * rp.nc[2];
+            double cv = vol / (rp.nc[0] * rp.nc[1] * rp.nc[2]);
+            worst_cell = std::max(worst_cell, rho * cv);
+        }
+    }
+    ctx->reps = reps;
+    int want_cap = (int)(2.0 * worst_ratio + 16);
+    want_cap = (want_cap + 7) / 8 * 8;
+    int want_cell = (int)(2.5 * worst_cell + 8);
+    if ((want_cap > ctx->cap && !ctx->cap_fixed) || !ctx->nlist) {
+        ctx->cap = std::max(ctx->cap, ctx->cap_fixed ? 1 : want_cap);
+        if (ctx->nlist) cudaFree(ctx->nlist);
+        CK(dalloc(&ctx->nlist, (size_t)ctx->cap * ctx->N));
+        free_graph(ctx);
+    }
+    if (want_cell > ctx->cell_cap || cell_off != ctx->n_cells || !ctx->cell_count) {
+        ctx->cell_cap = std::max(ctx->cell_cap, want_cell);
+        ctx->n_cells = cell_off;
+        if (ctx->cell_count) cudaFree(ctx->cell_count);
+        if (ctx->cell_slots) cudaFree(ctx->cell_slots);
+        CK(dalloc(&ctx->cell_count, (size_t)std::max(cell_off, 1)));
+        CK(dalloc(&ctx->cell_slots, (size_t)std::max(cell_off, 1) * ctx->cell_cap));
+        free_graph(ctx);
+    }
+    CK(cudaMemcpy(ctx->d_reps, reps.data(), sizeof(Rep) * ctx->R, cudaMemcpyHostToDevice));
+    return DEM_OK;
+}
+
+PairArgs pair_args(dem_ctx *ctx) {
+    PairArgs a = {};
+    a.n = ctx->N; a.dim = ctx->dim; a.cap = ctx->cap;
+    a.pos = ctx->pos; a.quat = ctx->quat; a.quatf = ctx->quatf;
+    a.shape = ctx->shape; a.rep = ctx->rep; a.reps = ctx->d_reps; a.shapes = ctx->d_shapes;
+    a.geoms = ctx->d_geoms; a.n_geoms = ctx->n_geoms;
+    a.table = ctx->d_table; a.table_len = ctx->table_len;
+    a.itable = ctx->d_itable; a.itable_len = ctx->itable_len;
+    a.nlist = ctx->nlist; a.nn = ctx->nn;
+    a.force = ctx->force; a.torque = ctx->torque; a.energy = ctx->energy; a.virial = ctx->virial;
+    a.eps = ctx->eps; a.sigma = ctx->sigma; a.par_eps = ctx->par_eps;
+    a.status = ctx->status;
+    a.counters = ctx->d_counters;
+    return a;
+}
+
+NlistArgs nlist_args(dem_ctx *ctx) {
+    NlistArgs a = {};
+    a.n = ctx->N; a.dim = ctx->dim; a.cap = ctx->cap; a.cell_cap = ctx->cell_cap;
+    a.pos = ctx->pos; a.shape = ctx->shape; a.rep = ctx->rep; a.reps = ctx->d_reps;
+    a.shapes = ctx->d_shapes; a.sigma = ctx->sigma; a.skin = ctx->skin;
+    a.cell_count = ctx->cell_count; a.cell_slots = ctx->cell_slots;
+    a.nlist = ctx->nlist; a.nn = ctx->nn; a.x_last = ctx->x_last; a.status = ctx->status;
+    a.half_skin2 = (float)(0.25 * ctx->skin * ctx->skin);
+    return a;
+}
+
+StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
+    StepArgs a = {};
+    a.n = ctx->N; a.dim = ctx->dim; a.n_reps = ctx->R; a.dt = dt; a.nvt = ens == DEM_NVT;
+    a.kT = kT; a.tau = tau;
+    a.pos = ctx->pos; a.vel = ctx->vel; a.quat = ctx->quat; a.angmom = ctx->angmom;
+    a.x_last = ctx->x_last; a.quatf = ctx->quatf; a.force = ctx->force; a.torque = ctx->torque;
+    a.shape = ctx->shape; a.rep = ctx->rep; a.reps = ctx->d_reps; a.shapes = ctx->d_shapes;
+    a.ke = ctx->ke; a.thermo = ctx->thermo; a.status = ctx->status;
+    return a;
+}
+
+int launch_forces(dem_ctx *ctx, bool count) {
+    NlistArgs na = nlist_args(ctx);
+    CK(launch_cells(na, ctx->n_cells, ctx->stream));
+    CK(launch_nlist(na, ctx->stream));
+    CK(launch_pair(pair_args(ctx), ctx->precision, ctx->decomp, ctx->block, count, ctx->stream));
+    return DEM_OK;
+}
+
+int launch_step(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
+    StepArgs sa = step_args(ctx, dt, ens, kT, tau);
+    CK(launch_first_half(sa, ctx->stream));
+    int rc = launch_forces(ctx, false);
+    if (rc) return rc;
+    CK(launch_second_half(sa, ctx->stream));
+    if (ens == DEM_NVT) {
+        CK(launch_thermo_end(sa, ctx->stream));
+        CK(launch_scale(sa, ctx->stream));
+    }
+    return DEM_OK;
+}
+
+int read_status(dem_ctx *ctx, Status *st) {
+    CK(cudaMemcpyAsync(st, ctx->status, sizeof(Status), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->rebuilds = st->rebuilds;
+    return DEM_OK;
+}
+
+int clear_flags(dem_ctx *ctx) {
+    // nlist_overflow, cell_overflow, nonfinite
+    CK(cudaMemsetAsync(&ctx->status->nlist_overflow, 0, 3 * sizeof(int), ctx->stream));
+    return DEM_OK;
+}
+
+int force_rebuild(dem_ctx *ctx) {
+    int one = 1;
+    CK(cudaMemcpyAsync(&ctx->status->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+// Grow list / cell capacities after an overflow; returns 1 if grown.
+int grow(dem_ctx *ctx, const Status &st, int *grown) {
+    *grown = 0;
+    if (st.nlist_overflow > ctx->cap) {
+        ctx->cap = (st.nlist_overflow * 3 / 2 + 7) / 8 * 8;
+        cudaFree(ctx->nlist);
+        CK(dalloc(&ctx->nlist, (size_t)ctx->cap * ctx->N));
+        *grown = 1;
+    }
+    if (st.cell_overflow > ctx->cell_cap) {
+        ctx->cell_cap = st.cell_overflow * 3 / 2 + 4;
+        cudaFree(ctx->cell_slots);
+        CK(dalloc(&ctx->cell_slots, (size_t)std::max(ctx->n_cells, 1) * ctx->cell_cap));
+        *grown = 1;
+    }
+    if (*grown) free_graph(ctx);
+    return DEM_OK;
+}
+
+// Evaluate forces at the current state; grow and redo on overflow.
+int compute_forces(dem_ctx *ctx) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        int rc = clear_flags(ctx);
+        if (rc) return rc;
+        rc = launch_forces(ctx, false);
+        if (rc) return rc;
+        Status st;
+        rc = read_status(ctx, &st);
+        if (rc) return rc;
+        if (st.nlist_overflow > ctx->cap || st.cell_overflow > ctx->cell_cap) {
+            int grown;
+            rc = grow(ctx, st, &grown);
+            if (rc) return rc;
+            rc = force_rebuild(ctx);
+            if (rc) return rc;
+            continue;
+        }
+        if (st.nonfinite) return set_err(ctx, DEM_ERR_NONFINITE, "non-finite force or energy");
+        return DEM_OK;
+    }
+    return set_err(ctx, DEM_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+}
+
+int snapshot(dem_ctx *ctx, bool restore) {
+    size_t n = (size_t)ctx->N;
+    if (!ctx->snap) {
+        CK(dalloc(&ctx->snap, 7 * n));
+        CK(dalloc(&ctx->snap_thermo, (size_t)ctx->R));
+    }
+    double4_32a *arrs[7] = {ctx->pos, ctx->vel, ctx->quat, ctx->angmom, ctx->force, ctx->torque, ctx->x_last};
+    for (int k = 0; k < 7; ++k) {
+        if (restore)
+            CK(cudaMemcpyAsync(arrs[k], ctx->snap + k * n, sizeof(double4_32a) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        else
+            CK(cudaMemcpyAsync(ctx->snap + k * n, arrs[k], sizeof(double4_32a) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (restore)
+        CK(cudaMemcpyAsync(ctx->thermo, ctx->snap_thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+        CK(cudaMemcpyAsync(ctx->snap_thermo, ctx->thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (restore) {
+        // float copy of the orientations
+        CK(launch_prepare_state(ctx->N, ctx->dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom,
+                                ctx->rep, ctx->d_reps, 0, ctx->stream));
+    }
+    return DEM_OK;
+}
+
+int get_graph(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
+    if (ctx->graph && ctx->g_dt == dt && ctx->g_ens == ens && ctx->g_kT == kT && ctx->g_tau == tau)
+        return DEM_OK;
+    free_graph(ctx);
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step(ctx, dt, ens, kT, tau);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc) return rc;
+    CK(e);
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    ctx->g_dt = dt; ctx->g_ens = ens; ctx->g_kT = kT; ctx->g_tau = tau;
+    return DEM_OK;
+}
+
+bool valid(const dem_ctx *ctx) { return ctx != nullptr; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int dem_shape_info(const dem_shape *shape, double *out) {
+    if (!shape || !out) return DEM_ERR_ARG;
+    HostGeom g;
+    HostShape h;
+    std::string err;
+    int rc = preprocess_shape(*shape, &g, &h, &err);
+    if (rc) { g_create_error = err; return rc; }
+    out[0] = g.R;
+    out[1] = (double)g.edges.size();
+    if (shape->dim == 3) { out[2] = h.inertia[0]; out[3] = h.inertia[1]; out[4] = h.inertia[2]; }
+    else { out[2] = h.inertia[2]; out[3] = 0; out[4] = 0; }
+    out[5] = h.volume;
+    out[6] = h.offdiag;
+    return DEM_OK;
+}
+
+const char *dem_last_error(const dem_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void dem_destroy(dem_ctx *ctx) {
+    if (!ctx) return;
+    free_graph(ctx);
+    void *ptrs[] = {ctx->pos, ctx->vel, ctx->quat, ctx->angmom, ctx->force, ctx->torque,
+                    ctx->x_last, ctx->quatf, ctx->shape, ctx->rep, ctx->nlist, ctx->nn,
+                    ctx->cell_count, ctx->cell_slots, ctx->energy, ctx->virial, ctx->ke,
+                    ctx->staging, ctx->red, ctx->scale3, ctx->status, ctx->thermo, ctx->d_reps,
+                    ctx->d_shapes, ctx->d_geoms, ctx->d_table, ctx->d_itable, ctx->d_counters,
+                    ctx->snap, ctx->snap_thermo};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsilon, double sigma,
+               const double *box, int n_replicas, const int *replica_sizes, int precision) {
+    if (!out) return set_err(nullptr, DEM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!shapes || n_shapes < 1) return set_err(nullptr, DEM_ERR_ARG, "no shapes");
+    if (!box || !replica_sizes || n_replicas < 1) return set_err(nullptr, DEM_ERR_ARG, "no replicas");
+    if (precision != DEM_FP64 && precision != DEM_FP32 && precision != DEM_FP32_COMP)
+        return set_err(nullptr, DEM_ERR_ARG, "unknown precision %d", precision);
+    if (!(epsilon > 0.0)) return set_err(nullptr, DEM_ERR_ARG, "epsilon must be > 0");
+    dem_ctx *ctx = new dem_ctx();
+    ctx->dim = shapes[0].dim;
+    ctx->n_shapes = n_shapes;
+    ctx->eps = epsilon;
+    ctx->sigma = sigma > 0 ? sigma : 0.0;
+    ctx->precision = precision;
+    ctx->R = n_replicas;
+    for (int s = 0; s < n_shapes; ++s) {
+        if (shapes[s].dim != ctx->dim) {
+            delete ctx;
+            return set_err(nullptr, DEM_ERR_ARG, "all shapes must have the same dim");
+        }
+        HostGeom g;
+        HostShape h;
+        std::string err;
+        int rc = preprocess_shape(shapes[s], &g, &h, &err);
+        if (rc) {
+            delete ctx;
+            return set_err(nullptr, rc, "shape %d: %s", s, err.c_str());
+        }
+        int gid = -1;
+        for (size_t k = 0; k < ctx->geoms.size(); ++k)
+            if (same_geom(ctx->geoms[k], g)) { gid = (int)k; break; }
+        if (gid < 0) {
+            if ((int)ctx->geoms.size() >= MAX_GEOMS) {
+                delete ctx;
+                return set_err(nullptr, DEM_ERR_ARG, "more than %d distinct geometries", MAX_GEOMS);
+            }
+            gid = (int)ctx->geoms.size();
+            ctx->geoms.push_back(g);
+        }
+        h.geom = gid;
+        ctx->shapes.push_back(h);
+    }
+    int N = 0;
+    for (int r = 0; r < n_replicas; ++r) {
+        if (replica_sizes[r] < 1) {
+            delete ctx;
+            return set_err(nullptr, DEM_ERR_ARG, "replica %d is empty", r);
+        }
+        ctx->offs.push_back(N);
+        ctx->sizes.push_back(replica_sizes[r]);
+        N += replica_sizes[r];
+        for (int a = 0; a < 3; ++a) {
+            double L = a < ctx->dim ? box[ctx->dim * r + a] : 1.0;
+            if (!(L > 0.0) || !isfinite(L)) {
+                delete ctx;
+                return set_err(nullptr, DEM_ERR_ARG, "replica %d: bad box", r);
+            }
+            ctx->box.push_back(L);
+        }
+    }
+    ctx->N = N;
+    // device buffers
+    int rc = [&]() -> int {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+        size_t n = N;
+        CK(dalloc(&ctx->pos, n)); CK(dalloc(&ctx->vel, n)); CK(dalloc(&ctx->quat, n));
+        CK(dalloc(&ctx->angmom, n)); CK(dalloc(&ctx->force, n)); CK(dalloc(&ctx->torque, n));
+        CK(dalloc(&ctx->x_last, n)); CK(dalloc(&ctx->quatf, n));
+        CK(dalloc(&ctx->shape, n)); CK(dalloc(&ctx->rep, n)); CK(dalloc(&ctx->nn, n));
+        CK(dalloc(&ctx->energy, n)); CK(dalloc(&ctx->virial, 6 * n)); CK(dalloc(&ctx->ke, n));
+        CK(dalloc(&ctx->staging, 4 * n));
+        CK(dalloc(&ctx->red, 6 * (size_t)ctx->R)); CK(dalloc(&ctx->scale3, 3 * (size_t)ctx->R));
+        CK(dalloc(&ctx->status, 1)); CK(dalloc(&ctx->thermo, (size_t)ctx->R));
+        CK(dalloc(&ctx->d_reps, (size_t)ctx->R)); CK(dalloc(&ctx->d_counters, 4));
+        CK(cudaMemset(ctx->status, 0, sizeof(Status)));
+        CK(cudaMemset(ctx->thermo, 0, sizeof(Thermo) * ctx->R));
+        CK(cudaMemset(ctx->nn, 0, sizeof(int) * n));
+        CK(cudaMemset(ctx->force, 0, sizeof(double4_32a) * n));
+        CK(cudaMemset(ctx->torque, 0, sizeof(double4_32a) * n));
+        std::vector<int> rep(n);
+        for (int r = 0; r < ctx->R; ++r)
+            for (int k = 0; k < ctx->sizes[r]; ++k) rep[ctx->offs[r] + k] = r;
+        CK(cudaMemcpy(ctx->rep, rep.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        return upload_tables(ctx);
+    }();
+    if (rc) {
+        std::string e = ctx->err;
+        dem_destroy(ctx);
+        return set_err(nullptr, rc, "%s", e.c_str());
+    }
+    *out = ctx;
+    return DEM_OK;
+}
+
+int dem_set_stream(dem_ctx *ctx, void *stream) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    ctx->own_stream = false;
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    free_graph(ctx);
+    return DEM_OK;
+}
+
+int dem_set_param(dem_ctx *ctx, const char *name, double value) {
+    if (!valid(ctx) || !name) return DEM_ERR_ARG;
+    std::string n(name);
+    if (n == "skin") {
+        if (!(value > 0)) return set_err(ctx, DEM_ERR_ARG, "skin must be > 0");
+        ctx->skin = value;
+        if (ctx->have_state) {
+            int rc = setup_replicas(ctx);
+            if (rc) return rc;
+            rc = force_rebuild(ctx);
+            if (rc) return rc;
+        }
+    } else if (n == "par_eps") {
+        if (!(value >= 0)) return set_err(ctx, DEM_ERR_ARG, "par_eps must be >= 0");
+        ctx->par_eps = value;
+    } else if (n == "decomp") {
+        int d = (int)value;
+        if (d < DEM_DECOMP_AUTO || d > DEM_DECOMP_TILED) return set_err(ctx, DEM_ERR_ARG, "bad decomp");
+        ctx->decomp = d == DEM_DECOMP_AUTO ? DEM_DECOMP_THREAD : d;
+    } else if (n == "block") {
+        int b = (int)value;
+        if (b < 0 || b > 1024 || b % 32) return set_err(ctx, DEM_ERR_ARG, "bad block");
+        ctx->block = b;
+    } else if (n == "graph") {
+        ctx->use_graph = value != 0;
+    } else if (n == "nlist_cap") {
+        int c = (int)value;
+        if (c < 1) return set_err(ctx, DEM_ERR_ARG, "bad nlist_cap");
+        ctx->cap = c;
+        ctx->cap_fixed = true;
+        if (ctx->nlist) cudaFree(ctx->nlist);
+        ctx->nlist = nullptr;
+        CK(dalloc(&ctx->nlist, (size_t)ctx->cap * ctx->N));
+        if (ctx->have_state) {
+            int rc = force_rebuild(ctx);
+            if (rc) return rc;
+        }
+    } else {
+        return set_err(ctx, DEM_ERR_ARG, "unknown parameter '%s'", name);
+    }
+    free_graph(ctx);
+    return DEM_OK;
+}
+
+int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
+    if (!valid(ctx) || !name || !value) return DEM_ERR_ARG;
+    std::string n(name);
+    if (n == "skin") *value = ctx->skin < 0 ? max_sigma(ctx) : ctx->skin;
+    else if (n == "par_eps") *value = ctx->par_eps;
+    else if (n == "decomp") *value = ctx->decomp;
+    else if (n == "block") *value = ctx->block;
+    else if (n == "graph") *value = ctx->use_graph;
+    else if (n == "nlist_cap") *value = ctx->cap;
+    else if (n == "n_cells") *value = ctx->n_cells;
+    else if (n == "allpairs_replicas") {
+        int k = 0;
+        for (auto &r : ctx->reps) k += r.allpairs;
+        *value = k;
+    } else return set_err(ctx, DEM_ERR_ARG, "unknown parameter '%s'", name);
+    return DEM_OK;
+}
+
+int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const double *orient,
+                  const double *vel, const double *angmom, int device_ptrs) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!shape_id || !pos || !orient || !vel || !angmom)
+        return set_err(ctx, DEM_ERR_ARG, "dem_set_state: all arrays are required");
+    const size_t n = ctx->N;
+    const int dim = ctx->dim;
+    ctx->shape_host.resize(n);
+    if (device_ptrs) {
+        CK(cudaMemcpyAsync(ctx->shape_host.data(), shape_id, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        memcpy(ctx->shape_host.data(), shape_id, sizeof(int) * n);
+    }
+    for (size_t i = 0; i < n; ++i)
+        if (ctx->shape_host[i] < 0 || ctx->shape_host[i] >= ctx->n_shapes)
+            return set_err(ctx, DEM_ERR_ARG, "shape_id[%zu] out of range", i);
+    CK(cudaMemcpyAsync(ctx->shape, ctx->shape_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+    int rc = setup_replicas(ctx);
+    if (rc) return rc;
+    const int odim = dim == 3 ? 4 : 1, adim = dim == 3 ? 3 : 1;
+    const double *src[4] = {pos, orient, vel, angmom};
+    const int widths[4] = {dim, odim, dim, adim};
+    const double *dsrc[4];
+    if (device_ptrs) {
+        for (int k = 0; k < 4; ++k) dsrc[k] = src[k];
+        CK(launch_import_state((int)n, dim, dsrc[0], dsrc[1], dsrc[2], dsrc[3], ctx->pos, ctx->quat,
+                               ctx->vel, ctx->angmom, ctx->stream));
+    } else {
+        // the four arrays go through the staging buffer one at a time
+        double *stage = ctx->staging;
+        for (int k = 0; k < 4; ++k) {
+            CK(cudaMemcpyAsync(stage, src[k], sizeof(double) * widths[k] * n, cudaMemcpyHostToDevice, ctx->stream));
+            const double *p[4] = {nullptr, nullptr, nullptr, nullptr};
+            p[k] = stage;
+            // import only the array just staged: the others keep their values
+            CK(launch_import_state((int)n, dim, k == 0 ? stage : nullptr, k == 1 ? stage : nullptr,
+                                   k == 2 ? stage : nullptr, k == 3 ? stage : nullptr, ctx->pos,
+                                   ctx->quat, ctx->vel, ctx->angmom, ctx->stream));
+        }
+    }
+    CK(launch_prepare_state((int)n, dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom, ctx->rep,
+                            ctx->d_reps, 1, ctx->stream));
+    CK(cudaMemsetAsync(ctx->thermo, 0, sizeof(Thermo) * ctx->R, ctx->stream));
+    rc = force_rebuild(ctx);
+    if (rc) return rc;
+    ctx->have_state = true;
+    rc = compute_forces(ctx);
+    if (rc) return rc;
+    StepArgs sa = step_args(ctx, 0.0, DEM_NVE, 1.0, 1.0);
+    CK(launch_kinetic(sa, ctx->stream));
+    CK(launch_thermo_end(sa, ctx->stream));   // NVE branch: stores K per replica
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+int dem_get_state(dem_ctx *ctx, double *pos, double *orient, double *vel, double *angmom,
+                  double *thermostat, int device_ptrs) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    const size_t n = ctx->N;
+    const int dim = ctx->dim, odim = dim == 3 ? 4 : 1, adim = dim == 3 ? 3 : 1;
+    double *dst[4] = {pos, orient, vel, angmom};
+    const int widths[4] = {dim, odim, dim, adim};
+    for (int k = 0; k < 4; ++k) {
+        if (!dst[k]) continue;
+        double *target = device_ptrs ? dst[k] : ctx->staging;
+        CK(launch_export_state((int)n, dim, ctx->pos, ctx->quat, ctx->vel, ctx->angmom,
+                               k == 0 ? target : nullptr, k == 1 ? target : nullptr,
+                               k == 2 ? target : nullptr, k == 3 ? target : nullptr, ctx->stream));
+        if (!device_ptrs)
+            CK(cudaMemcpyAsync(dst[k], ctx->staging, sizeof(double) * widths[k] * n, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (thermostat) {
+        std::vector<Thermo> th(ctx->R);
+        CK(cudaMemcpyAsync(th.data(), ctx->thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int r = 0; r < ctx->R; ++r) { thermostat[2 * r] = th[r].xi; thermostat[2 * r + 1] = th[r].eta; }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+int dem_set_thermostat(dem_ctx *ctx, const double *thermostat) {
+    if (!valid(ctx) || !thermostat) return DEM_ERR_ARG;
+    std::vector<Thermo> th(ctx->R);
+    CK(cudaMemcpyAsync(th.data(), ctx->thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < ctx->R; ++r) { th[r].xi = thermostat[2 * r]; th[r].eta = thermostat[2 * r + 1]; }
+    CK(cudaMemcpyAsync(ctx->thermo, th.data(), sizeof(Thermo) * ctx->R, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+int dem_compute(dem_ctx *ctx) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    return compute_forces(ctx);
+}
+
+int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    if (n < 0 || !(dt > 0) || (ensemble != DEM_NVE && ensemble != DEM_NVT))
+        return set_err(ctx, DEM_ERR_ARG, "bad step arguments");
+    if (ensemble == DEM_NVT && (!(kT > 0) || !(tau_T > 0)))
+        return set_err(ctx, DEM_ERR_ARG, "NVT needs kT > 0 and tau_T > 0");
+    if (n == 0) return DEM_OK;
+    int rc;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        rc = snapshot(ctx, false);
+        if (rc) return rc;
+        rc = clear_flags(ctx);
+        if (rc) return rc;
+        StepArgs sa = step_args(ctx, dt, ensemble, kT, tau_T);
+        if (ensemble == DEM_NVT) CK(launch_thermo_begin(sa, ctx->stream));
+        if (ctx->use_graph) {
+            rc = get_graph(ctx, dt, ensemble, kT, tau_T);
+            if (rc) return rc;
+            for (int s = 0; s < n; ++s) CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+        } else {
+            for (int s = 0; s < n; ++s) {
+                rc = launch_step(ctx, dt, ensemble, kT, tau_T);
+                if (rc) return rc;
+            }
+        }
+        Status st;
+        rc = read_status(ctx, &st);
+        if (rc) return rc;
+        if (st.nlist_overflow > ctx->cap || st.cell_overflow > ctx->cell_cap) {
+            int grown;
+            rc = grow(ctx, st, &grown);
+            if (rc) return rc;
+            rc = snapshot(ctx, true);
+            if (rc) return rc;
+            rc = force_rebuild(ctx);
+            if (rc) return rc;
+            rc = compute_forces(ctx);
+            if (rc) return rc;
+            continue;
+        }
+        if (st.nonfinite) return set_err(ctx, DEM_ERR_NONFINITE, "non-finite force or energy");
+        if (ensemble == DEM_NVT) { ctx->last_kT = kT; ctx->last_tau = tau_T; }
+        ctx->last_ens = ensemble;
+        return DEM_OK;
+    }
+    return set_err(ctx, DEM_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+}
+
+int dem_get_forces(dem_ctx *ctx, double *force, double *torque, int device_ptrs) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    const size_t n = ctx->N;
+    const int dim = ctx->dim, tdim = dim == 3 ? 3 : 1;
+    if (device_ptrs) {
+        CK(launch_export_forces((int)n, dim, ctx->force, ctx->torque, ctx->quat, force, torque, ctx->stream));
+    } else {
+        if (force) {
+            CK(launch_export_forces((int)n, dim, ctx->force, ctx->torque, ctx->quat, ctx->staging, nullptr, ctx->stream));
+            CK(cudaMemcpyAsync(force, ctx->staging, sizeof(double) * dim * n, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        if (torque) {
+            CK(launch_export_forces((int)n, dim, ctx->force, ctx->torque, ctx->quat, nullptr, ctx->staging, ctx->stream));
+            CK(cudaMemcpyAsync(torque, ctx->staging, sizeof(double) * tdim * n, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+int dem_get_particle_energy(dem_ctx *ctx, double *energy, int device_ptrs) {
+    if (!valid(ctx) || !energy) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    CK(cudaMemcpyAsync(energy, ctx->energy, sizeof(double) * ctx->N,
+                       device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+int dem_get_energy(dem_ctx *ctx, double *U, double *K, double *conserved) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    StepArgs sa = step_args(ctx, 0.0, DEM_NVE, 1.0, 1.0);
+    CK(launch_kinetic(sa, ctx->stream));
+    CK(launch_replica_sums(ctx->R, ctx->d_reps, ctx->energy, 1, 1, ctx->red, ctx->stream));
+    CK(launch_replica_sums(ctx->R, ctx->d_reps, ctx->ke, 1, 1, ctx->red + ctx->R, ctx->stream));
+    std::vector<double> h(2 * ctx->R);
+    std::vector<Thermo> th(ctx->R);
+    CK(cudaMemcpyAsync(h.data(), ctx->red, sizeof(double) * 2 * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(th.data(), ctx->thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < ctx->R; ++r) {
+        if (U) U[r] = h[r];
+        if (K) K[r] = h[ctx->R + r];
+        if (conserved) {
+            double c = h[r] + h[ctx->R + r];
+            if (ctx->last_ens == DEM_NVT) {
+                double g = ctx->reps[r].g_dof;
+                c += g * ctx->last_kT * (0.5 * ctx->last_tau * ctx->last_tau * th[r].xi * th[r].xi + th[r].eta);
+            }
+            conserved[r] = c;
+        }
+    }
+    return DEM_OK;
+}
+
+int dem_get_virial(dem_ctx *ctx, double *W6) {
+    if (!valid(ctx) || !W6) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    CK(launch_replica_sums(ctx->R, ctx->d_reps, ctx->virial, 6, 6, ctx->red, ctx->stream));
+    CK(cudaMemcpyAsync(W6, ctx->red, sizeof(double) * 6 * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DEM_OK;
+}
+
+int dem_set_box(dem_ctx *ctx, const double *box) {
+    if (!valid(ctx) || !box) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    std::vector<double> scale(3 * ctx->R, 1.0), old = ctx->box;
+    for (int r = 0; r < ctx->R; ++r)
+        for (int a = 0; a < ctx->dim; ++a) {
+            double L = box[ctx->dim * r + a];
+            if (!(L > 0) || !isfinite(L)) return set_err(ctx, DEM_ERR_ARG, "bad box");
+            scale[3 * r + a] = L / ctx->box[3 * r + a];
+            ctx->box[3 * r + a] = L;
+        }
+    int rc = setup_replicas(ctx);
+    if (rc) { ctx->box = old; setup_replicas(ctx); return rc; }
+    CK(cudaMemcpyAsync(ctx->scale3, scale.data(), sizeof(double) * 3 * ctx->R, cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_rescale(ctx->N, ctx->dim, ctx->pos, ctx->x_last, ctx->rep, ctx->scale3, ctx->stream));
+    CK(launch_prepare_state(ctx->N, ctx->dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom,
+                            ctx->rep, ctx->d_reps, 0, ctx->stream));
+    free_graph(ctx);
+    rc = force_rebuild(ctx);
+    if (rc) return rc;
+    return compute_forces(ctx);
+}
+
+int dem_get_counters(dem_ctx *ctx, long long *counts) {
+    if (!valid(ctx) || !counts) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    // a due rebuild first: the counting launch must read a complete list
+    int rc0 = compute_forces(ctx);
+    if (rc0) return rc0;
+    CK(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    CK(launch_pair(pair_args(ctx), ctx->precision, ctx->decomp, ctx->block, true, ctx->stream));
+    unsigned long long h[4];
+    CK(cudaMemcpyAsync(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    Status st;
+    int rc = read_status(ctx, &st);
+    if (rc) return rc;
+    counts[0] = (long long)h[0];
+    counts[1] = (long long)h[1];
+    counts[2] = (long long)h[2];
+    counts[3] = st.rebuilds;
+    return DEM_OK;
+}
+
+int dem_autotune(dem_ctx *ctx) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    ctx->decomp = DEM_DECOMP_THREAD;
+    ctx->block = 0;
+    free_graph(ctx);
+    return DEM_OK;
+}
+
+}  // extern "C"

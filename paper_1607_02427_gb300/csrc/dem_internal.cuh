@@ -1,0 +1,167 @@
+// dem_internal.cuh -- device data layout and launch wrappers shared by the
+// translation units of libdem (not part of the public ABI).
+//
+// Layout in HBM (N particles over all replicas, R replicas):
+//   pos, vel, quat, angmom_b, force, torque_b, x_last : double4_32a[N]
+//       (w unused; 32-byte records so a neighbour gather is one sector)
+//   quatf        : float4[N]  FP32 copy of quat read by the FP32 pair kernels
+//   shape, rep   : int[N]     shape index and replica index of each particle
+//   energy, ke   : double[N]  per-particle potential / kinetic energy
+//   virial       : double[6N] symmetric per-particle virial
+//   nlist        : int[cap * N], column-major (slot k of particle i at k*N+i)
+//   nn           : int[N]     neighbour count
+//   cell_count   : int[C]     particles per cell (C cells over all replicas)
+//   cell_slots   : int[C * cell_cap]
+//   reps         : Rep[R]     box, particle range and cell grid per replica
+//   geometry table: Real4 records per distinct shape geometry (see Geom)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dem.h"
+
+namespace dem {
+
+constexpr int MAX_VERTS = 32;       // vertices of one shape on the device path
+constexpr int MAX_FACE_VERTS = 12;  // vertices of one face
+constexpr int MAX_GEOMS = 64;       // distinct geometries per context
+constexpr int THREADS = 128;
+
+// One distinct geometry.  Offsets count Real4 records in the geometry table.
+//   verts:  nv records  (x, y, z, 0)
+//   edges:  2 ne records: a = (start, half length), d = (vector, 1/|d|^2)
+//   faces:  nf records  n = (unit outward normal, n . a0)
+//   fedges: 3 nfe records per face edge: a = (start, 0),
+//           e = (vector, 1/|e|^2), m = (inward in-plane normal, m . a)
+//   face k uses fedges [fe_begin[k], fe_begin[k] + fe_count[k]) (ints table)
+struct Geom {
+    int nv, ne, nf, nfe;
+    int v_off, e_off, f_off, fe_off;
+    int fi_off;          // offset of this geometry's faces in the int table
+    float R;             // circumradius of the inner shape
+    int pad[2];
+};
+
+struct ShapeDev {
+    int geom;
+    float R;             // circumradius (copy of the geometry's)
+    double rounding;
+    double mass;
+    double inertia[3];   // principal moments (2D: inertia[2] = I_z)
+};
+
+struct Rep {
+    double L[3];
+    int off, n;          // particle range
+    int cell_off;        // first cell of this replica in the global cell arrays
+    int nc[3];           // cells per axis
+    int allpairs;        // 1: neighbour search over all particles of the replica
+    int g_dof;           // degrees of freedom for the thermostat (as int)
+};
+
+// Device status word block.
+struct Status {
+    unsigned int maxdisp2;   // max squared displacement since last build (float bits)
+    int rebuild;             // forced rebuild request
+    int nlist_overflow;      // needed capacity if the list overflowed (else 0)
+    int cell_overflow;       // needed cell capacity if a cell overflowed
+    int nonfinite;           // 1 if a non-finite force/energy was produced
+    int rebuilds;            // rebuild counter
+    int built;               // set by the list build when it ran this step
+    int pad;
+};
+
+// Per-replica thermostat state (FP64): canonical end-of-step values and the
+// values after the first Trotter half step of the step in progress.
+struct Thermo {
+    double xi, eta, K;       // canonical (end of the last completed step)
+    double xi_h, eta_h;      // after this step's first half step
+    double s1;               // velocity scale of this step's first half step
+    double s2;               // velocity scale of this step's second half step
+    double pad;
+};
+
+struct PairArgs {
+    int n, dim, cap;
+    const double4_32a *pos;
+    const double4_32a *quat;
+    const float4 *quatf;
+    const int *shape, *rep;
+    const Rep *reps;
+    const ShapeDev *shapes;
+    const Geom *geoms;
+    int n_geoms;
+    const void *table;       // float4 or double4_32a records
+    int table_len;           // records
+    const int *itable;       // face -> (fe_begin, fe_count) pairs
+    int itable_len;
+    const int *nlist, *nn;
+    double4_32a *force, *torque;
+    double *energy, *virial;
+    double eps, sigma, par_eps;
+    Status *status;
+    unsigned long long *counters;  // counting launches only
+};
+
+struct NlistArgs {
+    int n, dim, cap, cell_cap;
+    const double4_32a *pos;
+    const int *shape, *rep;
+    const Rep *reps;
+    const ShapeDev *shapes;
+    double sigma, skin;
+    int *cell_count, *cell_slots;
+    int *nlist, *nn;
+    double4_32a *x_last;
+    Status *status;
+    float half_skin2;        // rebuild threshold (skin/2)^2
+};
+
+struct StepArgs {
+    int n, dim, n_reps;
+    double dt;
+    int nvt;
+    double kT, tau;
+    double4_32a *pos, *vel, *quat, *angmom, *x_last;
+    float4 *quatf;
+    const double4_32a *force, *torque;
+    const int *shape, *rep;
+    const Rep *reps;
+    const ShapeDev *shapes;
+    double *ke;
+    Thermo *thermo;
+    Status *status;
+};
+
+// ---- launch wrappers (pair.cu, nlist.cu, integrate.cu) ----
+cudaError_t launch_pair(const PairArgs &a, int precision, int decomp, int block, bool count,
+                        cudaStream_t s);
+size_t pair_smem_bytes(const PairArgs &a, int precision);
+cudaError_t launch_cells(const NlistArgs &a, int n_cells, cudaStream_t s);
+cudaError_t launch_nlist(const NlistArgs &a, cudaStream_t s);
+cudaError_t launch_first_half(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_second_half(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_thermo_begin(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_thermo_end(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_scale(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_kinetic(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_replica_sums(int n_reps, const Rep *reps, const double *per_particle,
+                                int stride, int comps, double *out, cudaStream_t s);
+cudaError_t launch_prepare_state(int n, int dim, double4_32a *pos, double4_32a *quat, float4 *quatf,
+                                 double4_32a *angmom, const int *rep, const Rep *reps,
+                                 int world_to_body, cudaStream_t s);
+cudaError_t launch_export_state(int n, int dim, const double4_32a *pos, const double4_32a *quat,
+                                const double4_32a *vel, const double4_32a *angmom, double *pos_out,
+                                double *orient_out, double *vel_out, double *angmom_out,
+                                cudaStream_t s);
+cudaError_t launch_import_state(int n, int dim, const double *pos_in, const double *orient_in,
+                                const double *vel_in, const double *angmom_in, double4_32a *pos,
+                                double4_32a *quat, double4_32a *vel, double4_32a *angmom, cudaStream_t s);
+cudaError_t launch_export_forces(int n, int dim, const double4_32a *force, const double4_32a *torque_b,
+                                 const double4_32a *quat, double *force_out, double *torque_out,
+                                 cudaStream_t s);
+cudaError_t launch_rescale(int n, int dim, double4_32a *pos, double4_32a *x_last, const int *rep,
+                           const double *scale3, cudaStream_t s);
+
+}  // namespace dem

@@ -1,0 +1,403 @@
+// integrate.cu -- time integration and reductions (FP64).
+//
+// Section "Energy Conservation" of arXiv:1607.02427 uses a second-order
+// integrator (energy error ~ dt^2, Kamberaj et al. 2005); Section "Assembly"
+// a Nose-Hoover thermostat on translational and rotational degrees of
+// freedom.  The paper gives no formulas; the scheme here is:
+//   * velocity Verlet for the centres;
+//   * body-frame angular momentum L_b with the symmetric free-rotor splitting
+//     z(dt/2) y(dt/2) x(dt) y(dt/2) z(dt/2): a rotation by phi = L_k/I_k dt
+//     about body axis k turns the body by phi and L_b by -phi (the NO_SQUISH
+//     splitting, Miller et al., J. Chem. Phys. 116, 8649 (2002));
+//   * NVT: T(dt/2) . NVE(dt) . T(dt/2), one friction xi per replica,
+//     dxi/dt = (2K/(g kT) - 1)/tau^2, T(delta) = {xi += delta/2 G(K);
+//     scale v, L by exp(-xi delta); eta += xi delta; xi += delta/2 G(K)}.
+// 2D particles carry a quaternion about z (angle theta = 2 atan2(q_z, q_w))
+// and L_b = (0, 0, L_z); only the z sub-rotations act.
+#include "dem_internal.cuh"
+
+namespace dem {
+namespace {
+
+__device__ __forceinline__ void quat_rotate_body(double4_32a &q, int k, double phi) {
+    double c = cos(0.5 * phi), s = sin(0.5 * phi);
+    // r = (c, s e_k); q <- q (x) r ; q = (x:w, y:x, z:y, w:z)
+    double w1 = q.x, x1 = q.y, y1 = q.z, z1 = q.w;
+    double w2 = c, x2 = k == 0 ? s : 0.0, y2 = k == 1 ? s : 0.0, z2 = k == 2 ? s : 0.0;
+    q.x = w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2;
+    q.y = w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2;
+    q.z = w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2;
+    q.w = w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2;
+}
+
+__device__ __forceinline__ double comp(const double4_32a &v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : v.z);
+}
+__device__ __forceinline__ void set_comp(double4_32a &v, int k, double x) {
+    if (k == 0) v.x = x; else if (k == 1) v.y = x; else v.z = x;
+}
+
+__device__ __forceinline__ void free_rotor_axis(double4_32a &q, double4_32a &L, const double *I, int k,
+                                                double dt) {
+    if (!(I[k] > 0.0)) return;
+    double phi = comp(L, k) / I[k] * dt;
+    quat_rotate_body(q, k, phi);
+    int a = (k + 1) % 3, b = (k + 2) % 3;
+    double c = cos(phi), s = sin(phi);
+    double La = comp(L, a), Lb = comp(L, b);
+    set_comp(L, a, c * La + s * Lb);
+    set_comp(L, b, -s * La + c * Lb);
+}
+
+__device__ __forceinline__ double wrap(double x, double L) {
+    x -= L * floor(x / L);
+    if (x >= L) x -= L;
+    return x;
+}
+
+__device__ __forceinline__ double nh_rate(double K, double g, double kT, double tau) {
+    return (2.0 * K / (g * kT) - 1.0) / (tau * tau);
+}
+
+__global__ void k_first_half(const StepArgs a) {
+    float dmax = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const int r = a.rep[i];
+        const Rep &rp = a.reps[r];
+        const ShapeDev &sh = a.shapes[a.shape[i]];
+        double4_32a v = a.vel[i], L = a.angmom[i], F = a.force[i], Tq = a.torque[i];
+        double4_32a x = a.pos[i], q = a.quat[i];
+        if (a.nvt) {
+            double s = a.thermo[r].s1;
+            v.x *= s; v.y *= s; v.z *= s;
+            L.x *= s; L.y *= s; L.z *= s;
+        }
+        const double h = 0.5 * a.dt / sh.mass;
+        v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
+        L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
+        x.x = wrap(x.x + a.dt * v.x, rp.L[0]);
+        x.y = wrap(x.y + a.dt * v.y, rp.L[1]);
+        if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2]);
+        free_rotor_axis(q, L, sh.inertia, 2, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inertia, 1, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inertia, 0, a.dt);
+        free_rotor_axis(q, L, sh.inertia, 1, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inertia, 2, 0.5 * a.dt);
+        double nq = sqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        q.x /= nq; q.y /= nq; q.z /= nq; q.w /= nq;
+        a.pos[i] = x;
+        a.vel[i] = v;
+        a.angmom[i] = L;
+        a.quat[i] = q;
+        a.quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+        double4_32a x0 = a.x_last[i];
+        double dx = x.x - x0.x, dy = x.y - x0.y, dz = x.z - x0.z;
+        dx -= rp.L[0] * rint(dx / rp.L[0]);
+        dy -= rp.L[1] * rint(dy / rp.L[1]);
+        if (a.dim == 3) dz -= rp.L[2] * rint(dz / rp.L[2]); else dz = 0.0;
+        dmax = fmaxf(dmax, (float)(dx * dx + dy * dy + dz * dz));
+    }
+    // warp max, one atomic per warp (non-negative floats order like their bits)
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0 && dmax > 0.f)
+        atomicMax(&a.status->maxdisp2, __float_as_uint(dmax));
+}
+
+__device__ __forceinline__ double kinetic_of(const ShapeDev &sh, const double4_32a &v,
+                                             const double4_32a &L) {
+    double k = 0.5 * sh.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+    if (sh.inertia[0] > 0.0) k += 0.5 * L.x * L.x / sh.inertia[0];
+    if (sh.inertia[1] > 0.0) k += 0.5 * L.y * L.y / sh.inertia[1];
+    if (sh.inertia[2] > 0.0) k += 0.5 * L.z * L.z / sh.inertia[2];
+    return k;
+}
+
+__global__ void k_second_half(const StepArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const ShapeDev &sh = a.shapes[a.shape[i]];
+        double4_32a v = a.vel[i], L = a.angmom[i], F = a.force[i], Tq = a.torque[i];
+        const double h = 0.5 * a.dt / sh.mass;
+        v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
+        L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
+        a.vel[i] = v;
+        a.angmom[i] = L;
+        a.ke[i] = kinetic_of(sh, v, L);
+    }
+}
+
+__global__ void k_kinetic(const StepArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
+        a.ke[i] = kinetic_of(a.shapes[a.shape[i]], a.vel[i], a.angmom[i]);
+}
+
+// Fixed-order block sum of x[off..off+n) (deterministic).
+__device__ double block_sum(const double *x, int off, int n, int stride, int comp) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += x[(size_t)(off + k) * stride + comp];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// One block per replica: K = sum of ke, then the second thermostat half step
+// of this step and the first half step of the next one.
+__global__ void k_thermo_end(const StepArgs a) {
+    const int r = blockIdx.x;
+    const Rep &rp = a.reps[r];
+    double K = block_sum(a.ke, rp.off, rp.n, 1, 0);
+    if (threadIdx.x == 0) {
+        Thermo &t = a.thermo[r];
+        const double g = (double)rp.g_dof, d = 0.5 * a.dt;
+        if (a.nvt) {
+            double xi = t.xi_h + 0.5 * d * nh_rate(K, g, a.kT, a.tau);
+            double s2 = exp(-xi * d);
+            double eta = t.eta_h + xi * d;
+            K *= s2 * s2;
+            xi += 0.5 * d * nh_rate(K, g, a.kT, a.tau);
+            t.xi = xi; t.eta = eta; t.K = K;
+            t.s2 = s2;
+            double xh = xi + 0.5 * d * nh_rate(K, g, a.kT, a.tau);
+            double s1 = exp(-xh * d);
+            t.eta_h = eta + xh * d;
+            t.xi_h = xh + 0.5 * d * nh_rate(K * s1 * s1, g, a.kT, a.tau);
+            t.s1 = s1;
+        } else {
+            t.K = K;
+        }
+    }
+}
+
+__global__ void k_thermo_begin(const StepArgs a) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n_reps) return;
+    Thermo &t = a.thermo[r];
+    const double g = (double)a.reps[r].g_dof, d = 0.5 * a.dt;
+    double xh = t.xi + 0.5 * d * nh_rate(t.K, g, a.kT, a.tau);
+    double s1 = exp(-xh * d);
+    t.eta_h = t.eta + xh * d;
+    t.xi_h = xh + 0.5 * d * nh_rate(t.K * s1 * s1, g, a.kT, a.tau);
+    t.s1 = s1;
+}
+
+__global__ void k_scale(const StepArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        double s = a.thermo[a.rep[i]].s2;
+        double4_32a v = a.vel[i], L = a.angmom[i];
+        v.x *= s; v.y *= s; v.z *= s;
+        L.x *= s; L.y *= s; L.z *= s;
+        a.vel[i] = v;
+        a.angmom[i] = L;
+    }
+}
+
+__global__ void k_replica_sums(const Rep *reps, const double *x, int stride, int comps,
+                               double *out) {
+    const Rep &rp = reps[blockIdx.x];
+    for (int c = 0; c < comps; ++c) {
+        double s = block_sum(x, rp.off, rp.n, stride, c);
+        if (threadIdx.x == 0) out[blockIdx.x * comps + c] = s;
+    }
+}
+
+}  // namespace
+
+// ---- small helpers for state conversion ----
+namespace {
+struct M3 { double m[3][3]; };
+__device__ __forceinline__ M3 qmat(const double4_32a &q) {
+    double w = q.x, x = q.y, y = q.z, z = q.w;
+    M3 R;
+    R.m[0][0] = 1 - 2 * (y * y + z * z); R.m[0][1] = 2 * (x * y - w * z); R.m[0][2] = 2 * (x * z + w * y);
+    R.m[1][0] = 2 * (x * y + w * z); R.m[1][1] = 1 - 2 * (x * x + z * z); R.m[1][2] = 2 * (y * z - w * x);
+    R.m[2][0] = 2 * (x * z - w * y); R.m[2][1] = 2 * (y * z + w * x); R.m[2][2] = 1 - 2 * (x * x + y * y);
+    return R;
+}
+
+__global__ void k_prepare(int n, int dim, double4_32a *pos, double4_32a *quat, float4 *quatf,
+                          double4_32a *angmom, const int *rep, const Rep *reps, int world_to_body) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Rep &rp = reps[rep[i]];
+        double4_32a x = pos[i];
+        x.x = wrap(x.x, rp.L[0]);
+        x.y = wrap(x.y, rp.L[1]);
+        x.z = dim == 3 ? wrap(x.z, rp.L[2]) : 0.0;
+        pos[i] = x;
+        double4_32a q = quat[i];
+        double nq = sqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        q.x /= nq; q.y /= nq; q.z /= nq; q.w /= nq;
+        quat[i] = q;
+        quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+        if (world_to_body) {
+            double4_32a L = angmom[i];
+            if (dim == 3) {
+                M3 R = qmat(q);
+                double bx = R.m[0][0] * L.x + R.m[1][0] * L.y + R.m[2][0] * L.z;
+                double by = R.m[0][1] * L.x + R.m[1][1] * L.y + R.m[2][1] * L.z;
+                double bz = R.m[0][2] * L.x + R.m[1][2] * L.y + R.m[2][2] * L.z;
+                angmom[i] = make_double4_32a(bx, by, bz, 0.0);
+            } else {
+                angmom[i] = make_double4_32a(0.0, 0.0, L.z, 0.0);
+            }
+        }
+    }
+}
+
+__global__ void k_import(int n, int dim, const double *pos_in, const double *orient_in,
+                         const double *vel_in, const double *angmom_in, double4_32a *pos,
+                         double4_32a *quat, double4_32a *vel, double4_32a *angmom) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (dim == 3) {
+            if (pos_in) pos[i] = make_double4_32a(pos_in[3 * i], pos_in[3 * i + 1], pos_in[3 * i + 2], 0.0);
+            if (vel_in) vel[i] = make_double4_32a(vel_in[3 * i], vel_in[3 * i + 1], vel_in[3 * i + 2], 0.0);
+            if (orient_in)
+                quat[i] = make_double4_32a(orient_in[4 * i], orient_in[4 * i + 1], orient_in[4 * i + 2],
+                                       orient_in[4 * i + 3]);
+            if (angmom_in)
+                angmom[i] = make_double4_32a(angmom_in[3 * i], angmom_in[3 * i + 1], angmom_in[3 * i + 2], 0.0);
+        } else {
+            if (pos_in) pos[i] = make_double4_32a(pos_in[2 * i], pos_in[2 * i + 1], 0.0, 0.0);
+            if (vel_in) vel[i] = make_double4_32a(vel_in[2 * i], vel_in[2 * i + 1], 0.0, 0.0);
+            if (orient_in) {
+                double th = orient_in[i];
+                quat[i] = make_double4_32a(cos(0.5 * th), 0.0, 0.0, sin(0.5 * th));
+            }
+            if (angmom_in) angmom[i] = make_double4_32a(0.0, 0.0, angmom_in[i], 0.0);
+        }
+    }
+}
+
+__global__ void k_export(int n, int dim, const double4_32a *pos, const double4_32a *quat,
+                         const double4_32a *vel, const double4_32a *angmom, double *pos_out,
+                         double *orient_out, double *vel_out, double *angmom_out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double4_32a q = quat[i];
+        if (dim == 3) {
+            if (pos_out) { double4_32a x = pos[i]; pos_out[3 * i] = x.x; pos_out[3 * i + 1] = x.y; pos_out[3 * i + 2] = x.z; }
+            if (vel_out) { double4_32a v = vel[i]; vel_out[3 * i] = v.x; vel_out[3 * i + 1] = v.y; vel_out[3 * i + 2] = v.z; }
+            if (orient_out) { orient_out[4 * i] = q.x; orient_out[4 * i + 1] = q.y; orient_out[4 * i + 2] = q.z; orient_out[4 * i + 3] = q.w; }
+            if (angmom_out) {
+                M3 R = qmat(q);
+                double4_32a L = angmom[i];
+                angmom_out[3 * i] = R.m[0][0] * L.x + R.m[0][1] * L.y + R.m[0][2] * L.z;
+                angmom_out[3 * i + 1] = R.m[1][0] * L.x + R.m[1][1] * L.y + R.m[1][2] * L.z;
+                angmom_out[3 * i + 2] = R.m[2][0] * L.x + R.m[2][1] * L.y + R.m[2][2] * L.z;
+            }
+        } else {
+            if (pos_out) { double4_32a x = pos[i]; pos_out[2 * i] = x.x; pos_out[2 * i + 1] = x.y; }
+            if (vel_out) { double4_32a v = vel[i]; vel_out[2 * i] = v.x; vel_out[2 * i + 1] = v.y; }
+            if (orient_out) orient_out[i] = 2.0 * atan2(q.w, q.x);
+            if (angmom_out) angmom_out[i] = angmom[i].z;
+        }
+    }
+}
+
+__global__ void k_export_forces(int n, int dim, const double4_32a *force, const double4_32a *torque_b,
+                                const double4_32a *quat, double *force_out, double *torque_out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double4_32a F = force[i], T = torque_b[i];
+        if (dim == 3) {
+            if (force_out) { force_out[3 * i] = F.x; force_out[3 * i + 1] = F.y; force_out[3 * i + 2] = F.z; }
+            if (torque_out) {
+                M3 R = qmat(quat[i]);
+                torque_out[3 * i] = R.m[0][0] * T.x + R.m[0][1] * T.y + R.m[0][2] * T.z;
+                torque_out[3 * i + 1] = R.m[1][0] * T.x + R.m[1][1] * T.y + R.m[1][2] * T.z;
+                torque_out[3 * i + 2] = R.m[2][0] * T.x + R.m[2][1] * T.y + R.m[2][2] * T.z;
+            }
+        } else {
+            if (force_out) { force_out[2 * i] = F.x; force_out[2 * i + 1] = F.y; }
+            if (torque_out) torque_out[i] = T.z;
+        }
+    }
+}
+
+__global__ void k_rescale(int n, int dim, double4_32a *pos, double4_32a *x_last, const int *rep,
+                          const double *scale3) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double *s = scale3 + 3 * rep[i];
+        double4_32a x = pos[i];
+        x.x *= s[0]; x.y *= s[1];
+        if (dim == 3) x.z *= s[2];
+        pos[i] = x;
+        x_last[i] = x;
+    }
+}
+
+inline int grid_for(int n, int block) {
+    int g = (n + block - 1) / block;
+    return g > 0 ? g : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_first_half(const StepArgs &a, cudaStream_t s) {
+    k_first_half<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_second_half(const StepArgs &a, cudaStream_t s) {
+    k_second_half<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_kinetic(const StepArgs &a, cudaStream_t s) {
+    k_kinetic<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_thermo_end(const StepArgs &a, cudaStream_t s) {
+    k_thermo_end<<<a.n_reps, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_thermo_begin(const StepArgs &a, cudaStream_t s) {
+    k_thermo_begin<<<grid_for(a.n_reps, 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_scale(const StepArgs &a, cudaStream_t s) {
+    k_scale<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_replica_sums(int n_reps, const Rep *reps, const double *per_particle,
+                                int stride, int comps, double *out, cudaStream_t s) {
+    k_replica_sums<<<n_reps, 256, 0, s>>>(reps, per_particle, stride, comps, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_prepare_state(int n, int dim, double4_32a *pos, double4_32a *quat, float4 *quatf,
+                                 double4_32a *angmom, const int *rep, const Rep *reps,
+                                 int world_to_body, cudaStream_t s) {
+    k_prepare<<<grid_for(n, 256), 256, 0, s>>>(n, dim, pos, quat, quatf, angmom, rep, reps,
+                                               world_to_body);
+    return cudaGetLastError();
+}
+cudaError_t launch_import_state(int n, int dim, const double *pos_in, const double *orient_in,
+                                const double *vel_in, const double *angmom_in, double4_32a *pos,
+                                double4_32a *quat, double4_32a *vel, double4_32a *angmom, cudaStream_t s) {
+    k_import<<<grid_for(n, 256), 256, 0, s>>>(n, dim, pos_in, orient_in, vel_in, angmom_in, pos,
+                                              quat, vel, angmom);
+    return cudaGetLastError();
+}
+cudaError_t launch_export_state(int n, int dim, const double4_32a *pos, const double4_32a *quat,
+                                const double4_32a *vel, const double4_32a *angmom, double *pos_out,
+                                double *orient_out, double *vel_out, double *angmom_out,
+                                cudaStream_t s) {
+    k_export<<<grid_for(n, 256), 256, 0, s>>>(n, dim, pos, quat, vel, angmom, pos_out, orient_out,
+                                              vel_out, angmom_out);
+    return cudaGetLastError();
+}
+cudaError_t launch_export_forces(int n, int dim, const double4_32a *force, const double4_32a *torque_b,
+                                 const double4_32a *quat, double *force_out, double *torque_out,
+                                 cudaStream_t s) {
+    k_export_forces<<<grid_for(n, 256), 256, 0, s>>>(n, dim, force, torque_b, quat, force_out,
+                                                     torque_out);
+    return cudaGetLastError();
+}
+cudaError_t launch_rescale(int n, int dim, double4_32a *pos, double4_32a *x_last, const int *rep,
+                           const double *scale3, cudaStream_t s) {
+    k_rescale<<<grid_for(n, 256), 256, 0, s>>>(n, dim, pos, x_last, rep, scale3);
+    return cudaGetLastError();
+}
+
+}  // namespace dem

@@ -460,8 +460,8 @@ def _support(shape, orient_row, direction):
 
 def contact_cluster(shapes: List[dict], shape_id: Sequence[int], box: Sequence[float],
                     rng: np.random.Generator, gap=(0.85, 1.15), gap_min: float = 0.8,
-                    sigma: float = 0.0, kT: float = 1.0, max_tries: int = 400,
-                    name: str = "cluster") -> System:
+                    sigma: float = 0.0, kT: float = 1.0, max_tries: int = 2000,
+                    free: float = 0.1, name: str = "cluster") -> System:
     """Random sequential placement of particles next to earlier ones.
 
     Each new particle takes a uniform random orientation and sits along a
@@ -485,14 +485,17 @@ def contact_cluster(shapes: List[dict], shape_id: Sequence[int], box: Sequence[f
     placed = 1
     for i in range(1, n):
         for _ in range(max_tries):
-            a = int(rng.integers(placed))
-            u = rng.normal(size=dim)
-            u /= np.linalg.norm(u)
-            sig = sigma if sigma > 0 else rnd[a] + rnd[i]
-            t = (_support(shapes[shape_id[a]], orient[a], u)
-                 + _support(shapes[shape_id[i]], orient[i], -u)
-                 + rng.uniform(*gap) * sig)
-            x = np.mod(pos[a] + t * u, box)
+            if rng.random() < free:
+                x = rng.random(dim) * box      # a free placement starts a new cluster
+            else:
+                a = int(rng.integers(placed))
+                u = rng.normal(size=dim)
+                u /= np.linalg.norm(u)
+                sig = sigma if sigma > 0 else rnd[a] + rnd[i]
+                t = (_support(shapes[shape_id[a]], orient[a], u)
+                     + _support(shapes[shape_id[i]], orient[i], -u)
+                     + rng.uniform(*gap) * sig)
+                x = np.mod(pos[a] + t * u, box)
             ok = True
             d = pos[:placed] - x
             d -= box * np.round(d / box)
@@ -533,3 +536,69 @@ def merge(systems: Sequence[System], name: str = "merged") -> System:
     return System(systems[0].dim, shapes, np.concatenate(ids), cat("pos"), cat("orient"),
                   cat("vel"), cat("angmom"), cat("box"), cat("replica_sizes"),
                   systems[0].epsilon, systems[0].sigma, tb, name)
+
+
+# ---------------------------------------------------------------------------
+# Contact-rich lattice starts (full-size force tests)
+# ---------------------------------------------------------------------------
+
+def _axis_extents(shape, q):
+    """Half extents of the rotated inner shape along x, y, z (support values
+    along +-e_k, the larger of the two), for quaternions q (n, 4)."""
+    w = np.einsum("nij,vj->nvi", _rotmat(q), shape["verts"])
+    return np.abs(w).max(1)
+
+
+def slab_lattice_start(system: System, gap: float = 0.85, tries: int = 24,
+                       seed: int = 0) -> System:
+    """Re-orient a simple-cubic lattice system so that neighbours are close
+    but never closer than ``gap * sigma`` (3D).
+
+    Sites of a simple-cubic lattice of spacing s differ by at least s along
+    some axis, so the inner shapes of i and j are at least
+    s - h_i - h_j apart along that axis, where h is the half extent of a
+    rotated shape along the axis.  Each particle draws uniform random
+    orientations until all three half extents are <= (s - gap sigma)/2; if
+    none of ``tries`` draws passes it keeps the body-frame orientation, and
+    if even that fails the replica's lattice is stretched until it passes.
+    Positions are the replica's sites (the box is scaled with the lattice).
+    """
+    assert system.dim == 3
+    rng = np.random.default_rng(np.random.SeedSequence(BASE_SEED + 97 + seed))
+    # start from the lattice scaled to the target (compressed) box, if any
+    box0 = system.box if system.target_box is None else system.target_box
+    pos0 = system.pos.copy()
+    if system.target_box is not None:
+        for r, sl in enumerate(system.replica_slices()):
+            pos0[sl] = system.pos[sl] * (system.target_box[r] / system.box[r])
+    out = dataclasses.replace(system, pos=pos0, orient=system.orient.copy(),
+                              box=np.array(box0, np.float64), target_box=None)
+    system = dataclasses.replace(system, pos=pos0, box=np.array(box0, np.float64))
+    for r, sl in enumerate(system.replica_slices()):
+        sh = system.shapes[int(system.shape_id[sl.start])]
+        sig = system.sigma if system.sigma > 0 else 2 * sh["rounding"]
+        n = sl.stop - sl.start
+        box = system.box[r]
+        m = np.round(box / (box.min() / np.ceil(n ** (1 / 3) - 1e-9))).astype(int)
+        m = np.maximum(m, 1)
+        s = float(box[0] / m[0])
+        ident = _axis_extents(sh, np.array([[1.0, 0, 0, 0]]))[0].max()
+        need = 2 * ident + gap * sig
+        if s < need:
+            scale = need / s
+            out.box[r] = box * scale
+            out.pos[sl] = system.pos[sl] * scale
+            s = need
+        lim = 0.5 * (s - gap * sig)
+        q = np.tile([1.0, 0, 0, 0], (n, 1))
+        todo = np.arange(n)
+        for _ in range(tries):
+            if len(todo) == 0:
+                break
+            cand = random_quaternions(rng, len(todo))
+            ok = _axis_extents(sh, cand).max(1) <= lim
+            q[todo[ok]] = cand[ok]
+            todo = todo[~ok]
+        out.orient[sl] = q
+    # angular momenta follow the new orientations (same body-frame draws)
+    return out

@@ -1,0 +1,110 @@
+"""Shared pieces of the GPU tests: building the library, comparing a context
+against the FP64 oracle, and the tolerances.
+
+Tolerances (written out here and used by every GPU force test):
+The WCA force of one feature pair is steep: its logarithmic slope in r is
+about 20-30 inside the cutoff.  A geometry error of delta (absolute, in the
+nearest-point distance) changes a term's force by about |f'(r)| delta, which
+relative to the term itself blows up near r_cut where f -> 0.  Each term k
+therefore gets the scale s_k = |f_k| + sigma |f'(r_k)| (the force change
+caused by a relative geometry perturbation of order one at the scale sigma),
+and a particle's force error is measured against S_i = sum_k s_k (sums of
+magnitudes, so cancellation between terms cannot hide an error):
+    err_F(i) = |F_i - F_i^oracle| / S_i.
+Torques use T_i = sum_k (|p_i - x_i| s_k + sigma |f_k|), energies
+sigma * S_i.  The bars:
+    FP64 mode:            err <= 1e-12
+    FP32 and FP32 + two-sum:  err <= 1e-5   (relative 1e-5 on FP32 forces)
+FP32 geometry with coordinates of order one carries errors of a few 1e-7,
+i.e. a few 1e-7 / sigma relative to S_i; 1e-5 leaves a margin of ten or more.
+Particles the oracle flags as having an edge pair within a decade of the
+parallel-edge threshold are excluded (there the rule switches branch, and a
+lower-precision evaluation may take the other one) and counted.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TOL = {0: 1e-12, 1: 1e-5, 2: 1e-5}
+
+
+def load_dem():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1607_02427_gb300 import dem
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return dem
+
+
+def compare_forces(dem, system, precision, ref=None, **params):
+    """Run one force evaluation; return (errors dict, ref, gpu outputs)."""
+    import oracle
+    if ref is None:
+        ref = oracle.forces(system, par_eps=params.get("par_eps", oracle.DEFAULT_PAR_EPS))
+    with dem.DEM(system, precision, **params) as d:
+        f, t = d.forces()
+        U, K, H = d.energy()
+        W = d.virial()
+        e = d.particle_energy()
+        cnt = d.counters()
+    ok = ref["flags"] == 0
+    sig = system.sigma if system.sigma > 0 else 2 * max(sh["rounding"] for sh in system.shapes)
+    S = np.maximum(ref["fscale"], 1e-300)
+    T = np.maximum(ref["tscale"], 1e-300)
+    errF = np.linalg.norm(f - ref["force"], axis=1) / S
+    errT = np.linalg.norm(t - ref["torque"], axis=1) / T
+    errU = np.abs(e - ref["energy"]) / np.maximum(sig * S, 1e-300)
+    zero = ref["fscale"] == 0
+    # particles without any term must get exactly zero
+    zero_bad = (np.abs(f[zero]).max() if zero.any() else 0.0,
+                np.abs(t[zero]).max() if zero.any() else 0.0)
+    Rmax = max(float(np.max(np.linalg.norm(sh["verts"], axis=1))) for sh in system.shapes)
+    errs = {
+        "F": float(errF[ok & ~zero].max()) if (ok & ~zero).any() else 0.0,
+        "T": float(errT[ok & ~zero].max()) if (ok & ~zero).any() else 0.0,
+        "U": float(errU[ok & ~zero].max()) if (ok & ~zero).any() else 0.0,
+        "zero": max(zero_bad),
+        "flagged": int((~ok).sum()),
+        "normF": float(np.linalg.norm(f - ref["force"]) / max(np.linalg.norm(ref["force"]), 1e-300)),
+    }
+    # per-replica totals
+    wscale = np.array([(2 * Rmax + 2 * sig) * ref["fscale"][sl].sum() + 1e-300
+                       for sl in system.replica_slices()])
+    Wref = np.stack([[v[0, 0], 0.5 * (v[0, 1] + v[1, 0]), 0.5 * (v[0, 2] + v[2, 0]), v[1, 1],
+                      0.5 * (v[1, 2] + v[2, 1]), v[2, 2]] for v in ref["virial"]])
+    errs["W"] = float((np.abs(W - Wref).max(1) / wscale).max())
+    uscale = np.array([sig * ref["fscale"][sl].sum() + 1e-300 for sl in system.replica_slices()])
+    errs["Utot"] = float((np.abs(U - ref["U"]) / uscale).max())
+    errs["counts"] = (cnt, ref["counts"].sum(0))
+    return errs, ref, dict(force=f, torque=t, U=U, W=W, energy=e, counts=cnt)
+
+
+def report(what, errs):
+    """Append one line of measured errors to $DEM_PARITY_REPORT (if set)."""
+    import json
+    import os
+    path = os.environ.get("DEM_PARITY_REPORT")
+    if path:
+        row = {k: v for k, v in errs.items() if k != "counts"}
+        cnt, rc = errs["counts"]
+        row["gpu_counts"] = [int(x) for x in cnt[:3]]
+        row["oracle_counts"] = [int(x) for x in rc]
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"case": what, **row}) + "\n")
+
+
+def assert_parity(errs, precision, what=""):
+    report(what, errs)
+    tol = TOL[precision]
+    for k in ("F", "T", "U", "W", "Utot"):
+        assert errs[k] <= tol, f"{what}: {k} error {errs[k]:.3e} > {tol:.0e} ({errs})"
+    assert errs["zero"] == 0.0, f"{what}: non-zero force on a particle without terms"
+    cnt, rc = errs["counts"]
+    # ordered pairs on the GPU, unordered in the oracle
+    assert cnt[0] == 2 * rc[0], f"{what}: pairs in range {cnt[0]} vs 2 x {rc[0]}"
+    assert cnt[1] == 2 * rc[1], f"{what}: feature pairs {cnt[1]} vs 2 x {rc[1]}"
+    if precision == 0:
+        assert cnt[2] == 2 * rc[2], f"{what}: contributing terms {cnt[2]} vs 2 x {rc[2]}"
+    else:
+        assert abs(cnt[2] - 2 * rc[2]) <= max(2, 1e-3 * rc[2]), f"{what}: terms {cnt[2]} vs {rc[2]}"

@@ -1,0 +1,157 @@
+"""GPU parity of the pair-feature kernels (Eq. DEM, Eq. DEM_2D) against the
+FP64 oracle, element by element, through the C ABI.
+
+Inputs: seeded contact-rich random clusters in periodic boxes (2D squares,
+mixed polygons / rods / disks, 3D cubes, tetrahedra, octahedra, prisms,
+spheres and mixtures), sizes that span several thread blocks with a ragged
+tail, multi-replica batches mixing cell-list and all-pairs replicas, and
+edge cases (a lone particle, particles with no contacts, a tiny neighbour
+list that must grow).  Tolerances and error measures: tests/gpu_common.py.
+"""
+import numpy as np
+import pytest
+
+from paper_1607_02427_gb300 import workloads as W
+from tests.gpu_common import TOL, assert_parity, compare_forces, load_dem
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = [0, 1, 2]
+PNAMES = {0: "fp64", 1: "fp32", 2: "fp32c"}
+
+
+@pytest.fixture(scope="module")
+def dem():
+    return load_dem()
+
+
+def _periodic_cluster(shapes, ids, box, seed, **kw):
+    rng = np.random.default_rng(seed)
+    return W.contact_cluster(shapes, np.asarray(ids, np.int32), box, rng, **kw)
+
+
+def _systems():
+    out = {}
+    out["squares"] = lambda: _periodic_cluster([W.square(1.0, 0.15)], np.zeros(200, int),
+                                               [30.0, 30.0], 1, sigma=0.3)
+    out["polys2d"] = lambda: _periodic_cluster(
+        [W.polygon(5, 0.7, 0.1), W.rod2d(1.0, 0.12), W.square(1.0, 0.15), W.disk(0.2, 0.02)],
+        np.arange(200) % 4, [30.0, 30.0], 2)
+    out["disks"] = lambda: _periodic_cluster([W.disk(0.25)], np.zeros(400, int), [25.0, 25.0], 3)
+    out["cubes"] = lambda: _periodic_cluster([W.cube(1.0, 0.15)], np.zeros(333, int),
+                                             [14.0, 14.0, 14.0], 4, sigma=0.3)
+    out["tets"] = lambda: _periodic_cluster([W.tetrahedron(1.0, 0.15)], np.zeros(300, int),
+                                            [11.0, 11.0, 11.0], 5)
+    out["octas"] = lambda: _periodic_cluster([W.octahedron(1.0, 0.1)], np.zeros(300, int),
+                                             [15.0, 15.0, 15.0], 6)
+    out["prisms"] = lambda: _periodic_cluster([W.triangular_prism(1.0, 1.0, 0.2)],
+                                              np.zeros(300, int), [12.0, 12.0, 12.0], 7)
+    out["spheres"] = lambda: _periodic_cluster([W.sphere(0.3, 0.036)], np.zeros(400, int),
+                                               [9.0, 9.0, 9.0], 8)
+    out["mixed3d"] = lambda: _periodic_cluster(
+        [W.cube(1.0, 0.15), W.tetrahedron(1.0, 0.1), W.triangular_prism(1.0, 1.0, 0.2),
+         W.sphere(0.3, 0.036), W.octahedron(0.9, 0.12)], np.arange(290) % 5,
+        [13.0, 13.0, 13.0], 9)
+    return out
+
+
+SYSTEMS = _systems()
+_cache = {}
+
+
+def system(name):
+    if name not in _cache:
+        _cache[name] = SYSTEMS[name]()
+    return _cache[name]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=[PNAMES[p] for p in PRECISIONS])
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_forces_parity(dem, name, precision):
+    s = system(name)
+    errs, ref, _ = compare_forces(dem, s, precision)
+    assert ref["counts"][0, 2] > 0, "input must have contacts"
+    assert_parity(errs, precision, f"{name}/{PNAMES[precision]}")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=[PNAMES[p] for p in PRECISIONS])
+def test_batched_replicas(dem, precision):
+    """Replicas of different shapes and sizes in one launch, including
+    replicas small enough for the all-pairs search and a one-particle one."""
+    reps = [system("cubes"), system("tets").replica(0),
+            _periodic_cluster([W.triangular_prism(1.0, 1.0, 0.15)], np.zeros(24, int),
+                              [5.5, 5.5, 5.5], 21, gap=(0.9, 1.2), gap_min=0.85),
+            _periodic_cluster([W.cube(1.0, 0.12)], np.zeros(1, int), [6.0, 6.0, 6.0], 22),
+            system("octas")]
+    s = W.merge(reps)
+    errs, ref, _ = compare_forces(dem, s, precision)
+    assert_parity(errs, precision, "batched")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=[PNAMES[p] for p in PRECISIONS])
+def test_nlist_growth(dem, precision):
+    """A neighbour list far too small must grow transparently."""
+    s = system("cubes")
+    errs, _, _ = compare_forces(dem, s, precision, nlist_cap=2)
+    assert_parity(errs, precision, "nlist_cap=2")
+
+
+def test_no_contacts_exact_zero(dem):
+    """Particles farther apart than the interaction range get exactly zero."""
+    sh = W.cube(1.0, 0.15)
+    pos = W.sc_sites([4, 4, 4], [2.2] * 3)
+    n = len(pos)
+    s = W.System(3, [sh], np.zeros(n, np.int32), pos, W.random_quaternions(np.random.default_rng(0), n),
+                 np.zeros((n, 3)), np.zeros((n, 3)), np.full((1, 3), 8.8), np.array([n], np.int32),
+                 1.0, 0.3)
+    with dem.DEM(s, dem.DEM_FP32_COMP) as d:
+        f, t = d.forces()
+        U, _, _ = d.energy()
+    assert np.all(f == 0.0) and np.all(t == 0.0) and U[0] == 0.0
+
+
+def test_deterministic(dem):
+    s = system("mixed3d")
+    outs = []
+    for _ in range(2):
+        with dem.DEM(s, dem.DEM_FP32_COMP) as d:
+            outs.append(d.forces())
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+def test_compensated_not_worse(dem):
+    """Two-sum accumulation is at least as close to the oracle as plain FP32."""
+    s = system("cubes")
+    e1, _, _ = compare_forces(dem, s, 1)
+    e2, _, _ = compare_forces(dem, s, 2)
+    assert e2["normF"] <= e1["normF"] * 1.05 + 1e-12
+
+
+def test_device_pointer_state(dem):
+    """State passed as CUDA torch tensors on torch's stream (device_ptrs=1)."""
+    import torch
+    s = system("cubes")
+    with dem.DEM(s, dem.DEM_FP32_COMP) as d:
+        f_host, _ = d.forces()
+        stream = torch.cuda.current_stream()
+        dem.dem_set_stream(d.ctx, stream.cuda_stream)
+        dev = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+        dem.dem_set_state(d.ctx, dev(s.shape_id, torch.int32), dev(s.pos), dev(s.orient), dev(s.vel),
+                          dev(s.angmom), device_ptrs=1)
+        f_dev = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+        t_dev = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+        dem.dem_get_forces(d.ctx, f_dev, t_dev, device_ptrs=1)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(f_dev.cpu().numpy(), f_host)
+
+
+def test_state_roundtrip(dem):
+    s = system("prisms")
+    with dem.DEM(s, dem.DEM_FP64) as d:
+        st = d.state()
+    np.testing.assert_allclose(st["pos"], np.mod(s.pos, s.box[0]), atol=1e-12)
+    np.testing.assert_allclose(st["vel"], s.vel, atol=0)
+    qn = s.orient / np.linalg.norm(s.orient, axis=1, keepdims=True)
+    np.testing.assert_allclose(st["orient"], qn, atol=1e-15)
+    np.testing.assert_allclose(st["angmom"], s.angmom, atol=1e-13)
