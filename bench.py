@@ -1,0 +1,474 @@
+#!/usr/bin/env python3
+"""Particle-steps per second of the rounded-polytope DEM on GB300.
+
+Workload (default): 512 independent replica systems, N_k ~ U{128..2048}
+rounded cubes / tetrahedra / triangular prisms (rounding 0.1-0.2, packing
+fraction 0.30-0.55), NVT at kT = 1, dt = 1e-3, all replicas advanced by
+one captured step graph per step (pair kernel in FP32 with two-sum
+accumulation, state, energies and virials in FP64).
+
+One bench step = one full timestep of every replica: thermostat half
+steps, half kicks, drift and free rotation, neighbour-list rebuild when
+due, the pair-feature kernel, reductions.  The state is prepared first
+(lattice start with bounding spheres one cutoff apart, compression on the
+GPU to each replica's packing fraction, equilibration) and is resident in
+HBM when the timed region starts.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s and FP32-peak fraction, FP32+comp batched vs plain FP64, 1 GB300"
+UNIT = "particle-steps/s"
+
+# GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock.
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+
+# FP32 flops of each counted code path of the pair kernel (FMA = 2, add /
+# mul / reciprocal = 1, compare = 0), hand-counted from csrc/pair.cu and
+# csrc/pair_common.cuh.  Keys are dem_get_counters indices.
+FLOPS_PER_PATH = {
+    0: 90,   # pair setup: j's rotation matrix (30), M = R_i^T R_j (45), dl = R_i^T d (15)
+    3: 23,   # vertex transform into the other frame (18) + reach test (5)
+    4: 6,    # face-plane signed distance
+    5: 6,    # in-plane edge test of a face
+    6: 23,   # point-segment nearest point
+    7: 46,   # edge transform (33) + centre (6) + reach test (7)
+    8: 17,   # edge bounding-sphere test
+    9: 73,   # segment-segment nearest points (Section "Model" parallel rule included)
+    11: 7,   # projection onto the face
+    2: 35,   # WCA term in i's frame (force, torque, energy, sums)
+    12: 15,  # extra rotation of a term evaluated in j's frame
+}
+TWO_SUM_EXTRA = 30   # compensated sums: 6 components x (6 - 1) extra flops per term
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=100)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="batched",
+                   choices=["batched", "cubes", "large", "squares", "octahedra"])
+    p.add_argument("--precision", default="fp32c", choices=["fp64", "fp32", "fp32c"])
+    p.add_argument("--replicas", type=int, default=512)
+    p.add_argument("--compress-steps", type=int, default=3000)
+    p.add_argument("--equil-steps", type=int, default=1000)
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the e2e, FP64 and CPU-baseline measurements")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name, rank, replicas):
+    from paper_1607_02427_gb300 import workloads as W
+    off = 100 * rank
+    if name == "batched":
+        s = W.config_batched(n_replicas=replicas, seed_index=3 + off)
+        return s, dict(dt=1e-3, ensemble="nvt", kT=1.0, tau=0.5)
+    if name == "cubes":
+        return W.config_cubes_4096(seed_index=1 + off), dict(dt=1e-3, ensemble="nvt", kT=1.0, tau=0.5)
+    if name == "large":
+        return W.config_large(seed_index=4 + off), dict(dt=1e-3, ensemble="nvt", kT=1.0, tau=0.5)
+    if name == "octahedra":
+        return W.config_octahedra(seed_index=2 + off), dict(dt=5e-4, ensemble="nve", kT=1.0, tau=0.5)
+    return W.config_squares_2d(seed_index=0 + off), dict(dt=1e-3, ensemble="nve", kT=1.0, tau=0.5)
+
+
+def prepare(dem, system, run, precision, compress_steps, equil_steps):
+    """Context at the target density: compress from the safe lattice start
+    (NVT, geometric box schedule), then equilibrate."""
+    d = dem.DEM(system, precision)
+    ens = dem.DEM_NVT
+    if system.target_box is not None:
+        chunks = 60
+        per = max(1, compress_steps // chunks)
+        start, target = system.box.copy(), system.target_box.copy()
+        for k in range(1, chunks + 1):
+            d.set_box(start * (target / start) ** (k / chunks))
+            d.step(per, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+    if equil_steps:
+        d.step(equil_steps, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+    return d
+
+
+# ---------------------------------------------------------------------------
+# Clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.tmp:
+            return None
+        self.tmp.flush()
+        rows = [r.strip().split(",") for r in open(self.tmp.name) if r.strip()]
+        os.unlink(self.tmp.name)
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Roofline
+# ---------------------------------------------------------------------------
+
+def algorithmic_flops(counts, comp):
+    f = sum(FLOPS_PER_PATH[k] * int(counts[k]) for k in FLOPS_PER_PATH)
+    if comp:
+        f += TWO_SUM_EXTRA * int(counts[2])
+    return f
+
+
+def pair_source_hash():
+    h = hashlib.sha256()
+    for name in ("pair.cu", "pair_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1607_02427_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, precision):
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(f"{workload}/{precision}")
+    if not ent or ent.get("source_hash") != pair_source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline (the FP64 oracle, as it stands)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(system, target_particles=3000, max_step_s=None, run=None):
+    """A bounded sample of the workload: its first replicas (all three shapes)
+    at their target density, contact-rich lattice start (generator-made).
+    With ``max_step_s``, replicas are added while one oracle step of the
+    sample stays within that many seconds."""
+    import oracle
+    from paper_1607_02427_gb300 import workloads as W
+    take, n, cost = [], 0, 0.0
+    for k in range(system.n_replicas):
+        rep = system.replica(k)
+        rep = W.slab_lattice_start(rep) if rep.dim == 3 else rep
+        if max_step_s is not None:
+            t0 = time.perf_counter()
+            oracle.run(rep, 1, run["dt"], ensemble=run["ensemble"], kT=run["kT"], tau=run["tau"])
+            c = time.perf_counter() - t0
+            if take and cost + c > max_step_s:
+                if k >= 8:
+                    break
+                continue
+            cost += c
+        take.append(rep)
+        n += rep.n
+        if max_step_s is None and n >= target_particles and k >= 2:
+            break
+        if max_step_s is not None and (cost >= 0.8 * max_step_s or k >= 8):
+            break
+    return (W.merge(take) if len(take) > 1 else take[0]), len(take)
+
+
+def time_oracle(system, run, seconds, steps=None):
+    import oracle
+    oracle.build()
+    sample, nrep = oracle_sample(system)
+    ens = run["ensemble"]
+    t0 = time.perf_counter()
+    oracle.run(sample, 1, run["dt"], ensemble=ens, kT=run["kT"], tau=run["tau"])
+    one = time.perf_counter() - t0
+    if steps is None:
+        steps = max(1, int(seconds / max(2.0 * one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.run(sample, steps, run["dt"], ensemble=ens, kT=run["kT"], tau=run["tau"])
+    dt = time.perf_counter() - t0
+    return {"value": sample.n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nrep} replicas ({sample.n} particles, first replicas of the workload, "
+                      f"generator-made start at target density), {steps} FP64 steps, "
+                      f"single thread, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# Main
+# ---------------------------------------------------------------------------
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if a.impl == "reference":
+        return reference_arm(a, world, rank)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_1607_02427_gb300 import dem
+
+    system, run = make_workload(a.workload, rank, a.replicas)
+    prec = dem.PRECISIONS[a.precision]
+    ens = dem.DEM_NVT if run["ensemble"] == "nvt" else dem.DEM_NVE
+    d = prepare(dem, system, run, prec, a.compress_steps, a.equil_steps)
+    stream = torch.cuda.current_stream()
+    dem.dem_set_stream(d.ctx, stream.cuda_stream)
+
+    # warm-up
+    d.step(a.warmup, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+    d.set_param("profile", 1)
+    d.step(1, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])   # capture the profiled graph
+    d.set_param("profile", 1)                                      # reset the totals
+    l0 = d.get_param("launches")
+
+    # timed region
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("dem_timed")
+        e0.record(stream)
+        d.step(a.steps, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = int(d.get_param("launches") - l0)
+    pair_ms = d.get_param("pair_ms_total") / max(1.0, d.get_param("pair_launches"))
+    d.set_param("profile", 0)
+    t_max = ms
+    n_total = system.n
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        nt = torch.tensor([float(system.n)], device="cuda")
+        dist.all_reduce(nt)
+        n_total = int(nt.item())
+    value = n_total * a.steps / (t_max / 1e3)
+
+    counts = d.counters()
+    flops = algorithmic_flops(counts, prec == dem.DEM_FP32_COMP)
+    achieved = flops / (pair_ms / 1e3) / 1e12
+    clocks = clk.summary()
+
+    extras = {}
+    if not a.no_extras:
+        extras = measure_extras(a, dem, d, system, run, ens, prec, torch)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_extras:
+        cpu = time_oracle(system, run, a.cpu_seconds)
+
+    if rank != 0:
+        d.close()
+        return
+    pair_fpe = int(counts[1])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec != dem.DEM_FP64 else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": system.name, "replicas": system.n_replicas, "particles": system.n,
+            "precision": {0: "fp64", 1: "fp32", 2: "fp32 pair kernel, two-sum sums, fp64 state"}[prec],
+            "ensemble": run["ensemble"], "dt": run["dt"], "graph": True,
+            "l2": "inputs larger than L2 (per-step working set > 129 MB)",
+            "parallelism": f"replicas x{world}",
+        },
+        "roofline": {
+            "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ncu_traffic(a.workload, a.precision),
+            "kernel": "pair-feature kernel (k_pair_thread)",
+            "kernel_ms": pair_ms, "kernel_share_of_step": pair_ms / (t_max / a.steps),
+            "flops_per_launch": flops, "feature_pairs_per_launch": pair_fpe,
+            "feature_pairs_per_s": pair_fpe / (pair_ms / 1e3),
+            "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max clock",
+        },
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if "e2e" in extras:
+        line["e2e"] = extras.pop("e2e")
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if extras:
+        line["comparison"] = extras
+    print(json.dumps(line))
+    d.close()
+
+
+def measure_extras(a, dem, d, system, run, ens, prec, torch):
+    """End-to-end through the C ABI with host buffers, and the FP64 paths."""
+    out = {}
+    st = d.state()
+    n, dim = system.n, system.dim
+    pin = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x), dtype=dt).pin_memory()
+    h_sid = pin(system.shape_id, torch.int32)
+    h_pos, h_or = pin(st["pos"], torch.float64), pin(st["orient"], torch.float64)
+    h_vel, h_am = pin(st["vel"], torch.float64), pin(st["angmom"], torch.float64)
+    k_e2e = max(3, min(20, a.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        dem.dem_set_state(d.ctx, h_sid, h_pos, h_or, h_vel, h_am, device_ptrs=0)
+        dem.dem_step(d.ctx, 1, run["dt"], ens, run["kT"], run["tau"])
+        U, K, H = d.energy()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    out["e2e"] = {"value": n * k_e2e / t_e2e, "unit": UNIT,
+                  "h2d_bytes_per_step": int(4 * n + 8 * n * (2 * dim + (4 if dim == 3 else 1)
+                                                            + (3 if dim == 3 else 1))),
+                  "d2h_bytes_per_step": int(3 * 8 * system.n_replicas),
+                  "steps": k_e2e,
+                  "what": "per step: dem_set_state from pinned host memory, dem_step(1), "
+                          "dem_get_energy to host"}
+    # the same state in the other precisions, batched (graph)
+    for name, p in (("fp64_batched", dem.DEM_FP64), ("fp32_batched", dem.DEM_FP32)):
+        if p == prec:
+            continue
+        sysc = _with_state(system, st)
+        with dem.DEM(sysc, p) as d2:
+            k = 20 if p == dem.DEM_FP64 else 200
+            d2.step(3, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d2.step(k, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+            torch.cuda.synchronize()
+            out[name] = {"value": n * k / (time.perf_counter() - t0), "unit": UNIT, "steps": k}
+    # plain FP64 single-system path: one context per replica, launch by launch
+    if system.n_replicas > 1:
+        sample = list(range(0, system.n_replicas, max(1, system.n_replicas // 24)))[:24]
+        full = _with_state(system, st)
+        k = 5
+        tot_n, tot_t = 0, 0.0
+        for r in sample:
+            sub = full.replica(r)
+            with dem.DEM(sub, dem.DEM_FP64, graph=0) as d3:
+                d3.step(1, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                d3.step(k, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+                torch.cuda.synchronize()
+                tot_t += time.perf_counter() - t0
+                tot_n += sub.n * k
+        out["fp64_single_system"] = {"value": tot_n / tot_t, "unit": UNIT,
+                                     "sample": f"{len(sample)} replicas one at a time, {k} steps each, no graph"}
+    return out
+
+
+def _with_state(system, st):
+    import dataclasses
+    return dataclasses.replace(system, pos=st["pos"], orient=st["orient"], vel=st["vel"],
+                               angmom=st["angmom"], box=system.target_box
+                               if system.target_box is not None else system.box,
+                               target_box=None)
+
+
+def reference_arm(a, world, rank):
+    """The FP64 CPU oracle on a bounded sample of the workload, per step."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    system, run = make_workload(a.workload, 0, a.replicas)
+    # each step a bounded sample: the whole run within about two minutes
+    budget = 120.0 / max(1, a.steps + a.warmup)
+    sample, nrep = oracle_sample(system, max_step_s=budget, run=run)
+    for _ in range(a.warmup):
+        oracle.run(sample, 1, run["dt"], ensemble=run["ensemble"], kT=run["kT"], tau=run["tau"])
+    t0 = time.perf_counter()
+    steps = a.steps
+    state = sample
+    oracle.run(state, steps, run["dt"], ensemble=run["ensemble"], kT=run["kT"], tau=run["tau"])
+    dt = time.perf_counter() - t0
+    value = sample.n * steps / dt
+    desc = (f"{nrep} replicas ({sample.n} particles) of {system.name}, FP64 oracle, "
+            f"single thread, {steps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": steps, "warmup": a.warmup,
+            "ms_per_step": dt * 1e3 / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": system.name, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

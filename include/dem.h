@@ -203,6 +203,14 @@ int dem_set_box(dem_ctx *ctx, const double *box);
  *   "block"       threads per block of the pair kernel (0 = default)
  *   "graph"       1 = replay each step as a captured CUDA graph (default 1)
  *   "nlist_cap"   neighbour slots per particle (grown automatically)
+ *   "profile"     1 = time every pair-kernel launch of dem_step with a pair
+ *                 of CUDA events on the context's stream (inside the
+ *                 captured graph too); setting it resets the totals
+ * Read-only (dem_get_param):
+ *   "pair_ms_total"  summed pair-kernel time of the profiled steps (ms)
+ *   "pair_launches"  number of profiled pair-kernel launches
+ *   "launches"       kernel launches issued by this context so far
+ *   "n_cells", "allpairs_replicas"  cell-list layout
  * Setting an unknown name or an invalid value returns DEM_ERR_ARG. */
 int dem_set_param(dem_ctx *ctx, const char *name, double value);
 int dem_get_param(dem_ctx *ctx, const char *name, double *value);
@@ -212,11 +220,25 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value);
  * every choice up to floating-point summation order. */
 int dem_autotune(dem_ctx *ctx);
 
-/* Work counters of the last force evaluation (host array of 4 long longs):
- * [0] ordered particle pairs within the bounding-sphere range,
- * [1] feature pairs of those ordered pairs (the work Eq. DEM defines),
- * [2] feature pairs with r < r_cut, [3] neighbour-list rebuilds so far.
- * Counting runs a separate instrumented evaluation (not the timed path). */
+/* Work counters of one force evaluation at the current state (host array of
+ * DEM_N_COUNTERS long longs).  The pair kernel evaluates every ordered pair
+ * (i, j) of the full neighbour list in i's body frame and skips, exactly,
+ * feature pairs whose bounding spheres are farther apart than r_cut:
+ *  [0] ordered particle pairs within the bounding-sphere range
+ *  [1] feature pairs Eq. DEM / Eq. DEM_2D assigns to those pairs
+ *  [2] feature pairs with r < r_cut (WCA terms evaluated)
+ *  [3] vertex transforms into the other particle's frame (+ reach test)
+ *  [4] vertex-face plane tests      [5] in-plane edge tests of faces
+ *  [6] point-segment nearest points [7] edge transforms (+ reach test)
+ *  [8] edge bounding-sphere tests   [9] segment-segment nearest points
+ *  [10] neighbour-list entries scanned
+ *  [11] vertex-face projections inside the face
+ *  [12] terms evaluated in j's frame (vertex(i)-face(j), vertex(i)-edge(j))
+ *  [13] neighbour-list rebuilds so far  [14] kernel launches so far
+ *  [15] 0
+ * Entries [0]-[12] come from a separate instrumented evaluation at the
+ * current state (the evaluation used by dem_step is not instrumented). */
+#define DEM_N_COUNTERS 16
 int dem_get_counters(dem_ctx *ctx, long long *counts);
 
 /* Use this CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream()).

@@ -288,6 +288,17 @@ struct dem_ctx {
     Thermo *snap_thermo = nullptr;
     bool have_state = false;
     long long rebuilds = 0;
+    // kernel launches issued (a graph replay counts each of its kernels)
+    long long launches = 0;
+    int kernels_per_step = 0;
+    // CUDA-event timing of the pair kernel inside the stepped run
+    bool profile = false;
+    cudaEvent_t cap_ev[2] = {nullptr, nullptr};
+    cudaGraph_t graph_src = nullptr;
+    cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms = 0.0;
+    long long prof_n = 0;
     std::string err;
 };
 
@@ -319,7 +330,10 @@ template <class T> cudaError_t dalloc(T **p, size_t count) {
 
 void free_graph(dem_ctx *ctx) {
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->graph_src) cudaGraphDestroy(ctx->graph_src);
     ctx->graph = nullptr;
+    ctx->graph_src = nullptr;
+    ctx->ev_node[0] = ctx->ev_node[1] = nullptr;
     ctx->g_ens = -1;
 }
 
@@ -532,19 +546,27 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     return a;
 }
 
-int launch_forces(dem_ctx *ctx, bool count) {
+// List build (if due) and the pair kernel; e0/e1 (optional) bracket the pair
+// kernel with CUDA events on the context's stream.
+int launch_forces(dem_ctx *ctx, bool count, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
     NlistArgs na = nlist_args(ctx);
     CK(launch_cells(na, ctx->n_cells, ctx->stream));
     CK(launch_nlist(na, ctx->stream));
+    // external records: under stream capture they become event-record nodes
+    if (e0) CK(cudaEventRecordWithFlags(e0, ctx->stream, cudaEventRecordExternal));
     CK(launch_pair(pair_args(ctx), ctx->precision, ctx->decomp, ctx->block, count, ctx->stream));
+    if (e1) CK(cudaEventRecordWithFlags(e1, ctx->stream, cudaEventRecordExternal));
+    ctx->launches += 3;
     return DEM_OK;
 }
 
-int launch_step(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
+int launch_step(dem_ctx *ctx, double dt, int ens, double kT, double tau,
+                cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
     StepArgs sa = step_args(ctx, dt, ens, kT, tau);
     CK(launch_first_half(sa, ctx->stream));
-    int rc = launch_forces(ctx, false);
+    int rc = launch_forces(ctx, false, e0, e1);
     if (rc) return rc;
+    ctx->launches += ens == DEM_NVT ? 4 : 2;
     CK(launch_second_half(sa, ctx->stream));
     if (ens == DEM_NVT) {
         CK(launch_thermo_end(sa, ctx->stream));
@@ -641,20 +663,60 @@ int snapshot(dem_ctx *ctx, bool restore) {
     return DEM_OK;
 }
 
+// Capture one step as a CUDA graph (re-captured when the step parameters,
+// buffers or the profiling switch change).  With profiling on, the graph
+// carries two event-record nodes around the pair kernel; before every replay
+// they are pointed at a fresh pair of events.
 int get_graph(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
-    if (ctx->graph && ctx->g_dt == dt && ctx->g_ens == ens && ctx->g_kT == kT && ctx->g_tau == tau)
+    if (ctx->graph && ctx->g_dt == dt && ctx->g_ens == ens && ctx->g_kT == kT &&
+        ctx->g_tau == tau && (ctx->ev_node[0] != nullptr) == ctx->profile)
         return DEM_OK;
     free_graph(ctx);
+    if (ctx->profile && !ctx->cap_ev[0]) {
+        CK(cudaEventCreate(&ctx->cap_ev[0]));
+        CK(cudaEventCreate(&ctx->cap_ev[1]));
+    }
     cudaGraph_t g;
+    long long l0 = ctx->launches;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = launch_step(ctx, dt, ens, kT, tau);
+    int rc = ctx->profile ? launch_step(ctx, dt, ens, kT, tau, ctx->cap_ev[0], ctx->cap_ev[1])
+                          : launch_step(ctx, dt, ens, kT, tau);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->launches = l0;
     if (rc) return rc;
     CK(e);
+    size_t nn = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    int kernels = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nd, &t));
+        if (t == cudaGraphNodeTypeKernel) ++kernels;
+        if (t == cudaGraphNodeTypeEventRecord) {
+            cudaEvent_t ev;
+            CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            if (ev == ctx->cap_ev[0]) ctx->ev_node[0] = nd;
+            if (ev == ctx->cap_ev[1]) ctx->ev_node[1] = nd;
+        }
+    }
+    ctx->kernels_per_step = kernels;
     e = cudaGraphInstantiate(&ctx->graph, g, 0);
-    cudaGraphDestroy(g);
+    ctx->graph_src = g;
     CK(e);
+    if (ctx->profile && (!ctx->ev_node[0] || !ctx->ev_node[1]))
+        return set_err(ctx, DEM_ERR_CUDA, "profiling events missing from the captured step");
     ctx->g_dt = dt; ctx->g_ens = ens; ctx->g_kT = kT; ctx->g_tau = tau;
+    return DEM_OK;
+}
+
+int ensure_events(dem_ctx *ctx, size_t n) {
+    while (ctx->ev_pool.size() < n) {
+        cudaEvent_t ev;
+        CK(cudaEventCreate(&ev));
+        ctx->ev_pool.push_back(ev);
+    }
     return DEM_OK;
 }
 
@@ -698,6 +760,9 @@ void dem_destroy(dem_ctx *ctx) {
                     ctx->snap, ctx->snap_thermo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
+    for (auto ev : ctx->cap_ev)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -777,7 +842,7 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
         CK(dalloc(&ctx->staging, 4 * n));
         CK(dalloc(&ctx->red, 6 * (size_t)ctx->R)); CK(dalloc(&ctx->scale3, 3 * (size_t)ctx->R));
         CK(dalloc(&ctx->status, 1)); CK(dalloc(&ctx->thermo, (size_t)ctx->R));
-        CK(dalloc(&ctx->d_reps, (size_t)ctx->R)); CK(dalloc(&ctx->d_counters, 4));
+        CK(dalloc(&ctx->d_reps, (size_t)ctx->R)); CK(dalloc(&ctx->d_counters, DEM_N_COUNTERS));
         CK(cudaMemset(ctx->status, 0, sizeof(Status)));
         CK(cudaMemset(ctx->thermo, 0, sizeof(Thermo) * ctx->R));
         CK(cudaMemset(ctx->nn, 0, sizeof(int) * n));
@@ -838,6 +903,10 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
         ctx->block = b;
     } else if (n == "graph") {
         ctx->use_graph = value != 0;
+    } else if (n == "profile") {
+        ctx->profile = value != 0;
+        ctx->prof_ms = 0.0;
+        ctx->prof_n = 0;
     } else if (n == "nlist_cap") {
         int c = (int)value;
         if (c < 1) return set_err(ctx, DEM_ERR_ARG, "bad nlist_cap");
@@ -865,6 +934,10 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
     else if (n == "decomp") *value = ctx->decomp;
     else if (n == "block") *value = ctx->block;
     else if (n == "graph") *value = ctx->use_graph;
+    else if (n == "profile") *value = ctx->profile;
+    else if (n == "pair_ms_total") *value = ctx->prof_ms;
+    else if (n == "pair_launches") *value = (double)ctx->prof_n;
+    else if (n == "launches") *value = (double)ctx->launches;
     else if (n == "nlist_cap") *value = ctx->cap;
     else if (n == "n_cells") *value = ctx->n_cells;
     else if (n == "allpairs_replicas") {
@@ -991,19 +1064,41 @@ int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau
         if (rc) return rc;
         StepArgs sa = step_args(ctx, dt, ensemble, kT, tau_T);
         if (ensemble == DEM_NVT) CK(launch_thermo_begin(sa, ctx->stream));
+        if (ensemble == DEM_NVT) ctx->launches += 1;
+        if (ctx->profile) {
+            rc = ensure_events(ctx, 2 * (size_t)n);
+            if (rc) return rc;
+        }
         if (ctx->use_graph) {
             rc = get_graph(ctx, dt, ensemble, kT, tau_T);
             if (rc) return rc;
-            for (int s = 0; s < n; ++s) CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+            for (int s = 0; s < n; ++s) {
+                if (ctx->profile) {
+                    CK(cudaGraphExecEventRecordNodeSetEvent(ctx->graph, ctx->ev_node[0], ctx->ev_pool[2 * s]));
+                    CK(cudaGraphExecEventRecordNodeSetEvent(ctx->graph, ctx->ev_node[1], ctx->ev_pool[2 * s + 1]));
+                }
+                CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+            }
+            ctx->launches += (long long)n * ctx->kernels_per_step;
         } else {
             for (int s = 0; s < n; ++s) {
-                rc = launch_step(ctx, dt, ensemble, kT, tau_T);
+                rc = ctx->profile ? launch_step(ctx, dt, ensemble, kT, tau_T, ctx->ev_pool[2 * s],
+                                                ctx->ev_pool[2 * s + 1])
+                                  : launch_step(ctx, dt, ensemble, kT, tau_T);
                 if (rc) return rc;
             }
         }
         Status st;
         rc = read_status(ctx, &st);
         if (rc) return rc;
+        if (ctx->profile) {
+            for (int s = 0; s < n; ++s) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ctx->ev_pool[2 * s], ctx->ev_pool[2 * s + 1]));
+                ctx->prof_ms += ms;
+            }
+            ctx->prof_n += n;
+        }
         if (st.nlist_overflow > ctx->cap || st.cell_overflow > ctx->cell_cap) {
             int grown;
             rc = grow(ctx, st, &grown);
@@ -1119,17 +1214,17 @@ int dem_get_counters(dem_ctx *ctx, long long *counts) {
     // a due rebuild first: the counting launch must read a complete list
     int rc0 = compute_forces(ctx);
     if (rc0) return rc0;
-    CK(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_counters, 0, DEM_N_COUNTERS * sizeof(unsigned long long), ctx->stream));
     CK(launch_pair(pair_args(ctx), ctx->precision, ctx->decomp, ctx->block, true, ctx->stream));
-    unsigned long long h[4];
+    unsigned long long h[DEM_N_COUNTERS];
     CK(cudaMemcpyAsync(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     Status st;
     int rc = read_status(ctx, &st);
     if (rc) return rc;
-    counts[0] = (long long)h[0];
-    counts[1] = (long long)h[1];
-    counts[2] = (long long)h[2];
-    counts[3] = st.rebuilds;
+    for (int k = 0; k < DEM_N_COUNTERS; ++k) counts[k] = (long long)h[k];
+    counts[13] = st.rebuilds;
+    counts[14] = ctx->launches;
+    counts[15] = 0;
     return DEM_OK;
 }
 

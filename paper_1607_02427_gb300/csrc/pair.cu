@@ -84,12 +84,12 @@ template <> __device__ __forceinline__ M33<double> orientation<double>(const Pai
 // All terms of the ordered pair (i, j) (i's geometry gi, j's gj), evaluated
 // in i's frame, accumulated into S.  Returns the number of feature pairs
 // the definition (Eq. DEM / Eq. DEM_2D) assigns to the pair.
-template <class T, bool COMP, int DIM>
+template <class T, bool COMP, int DIM, bool COUNT>
 __device__ __forceinline__ unsigned int pair_terms(const typename R4T<T>::type *tab,
                                                    const int *itab, const Geom &gi,
                                                    const Geom &gj, const M33<T> &M, V3<T> dl,
                                                    T rc, T sig2, T eps, T par_eps,
-                                                   Sums<T, COMP> &S) {
+                                                   Sums<T, COMP> &S, PathCount *pc) {
     using R4 = typename R4T<T>::type;
     const T rc2 = rc * rc;
     if (gi.nv == 1 && gj.nv == 1) {             // sphere / disk limit: central WCA
@@ -105,13 +105,16 @@ __device__ __forceinline__ unsigned int pair_terms(const typename R4T<T>::type *
         // V_j x E_i (Eq. DEM_2D, second sum), in i's frame
         for (int b = 0; b < gj.nv; ++b) {
             V3<T> p = dl + mul(M, xyz<T>(tab[gj.v_off + b]));
+            bump<COUNT>(pc, C_VTX);
             if (!(dot(p, p) < reach_i * reach_i)) continue;
             for (int e = 0; e < gi.ne; ++e) {
                 R4 ea = tab[gi.e_off + 2 * e], ed = tab[gi.e_off + 2 * e + 1];
                 V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
                 V3<T> c = A + D * T(0.5) - p;
                 T lim = ea.w + rc;
+                bump<COUNT>(pc, C_SPHERE);
                 if (!(dot(c, c) < lim * lim)) continue;
+                bump<COUNT>(pc, C_PTSEG);
                 T t = clamp01(dot(p - A, D) * ed.w);
                 V3<T> q = A + D * t;
                 V3<T> rv = q - p;
@@ -123,18 +126,24 @@ __device__ __forceinline__ unsigned int pair_terms(const typename R4T<T>::type *
         for (int a_ = 0; a_ < gi.nv; ++a_) {
             V3<T> u = xyz<T>(tab[gi.v_off + a_]);
             V3<T> p = mul_t(M, u - dl);
+            bump<COUNT>(pc, C_VTX);
             if (!(dot(p, p) < reach_j * reach_j)) continue;
             for (int e = 0; e < gj.ne; ++e) {
                 R4 ea = tab[gj.e_off + 2 * e], ed = tab[gj.e_off + 2 * e + 1];
                 V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
                 V3<T> c = A + D * T(0.5) - p;
                 T lim = ea.w + rc;
+                bump<COUNT>(pc, C_SPHERE);
                 if (!(dot(c, c) < lim * lim)) continue;
+                bump<COUNT>(pc, C_PTSEG);
                 T t = clamp01(dot(p - A, D) * ed.w);
                 V3<T> q = A + D * t;
                 V3<T> rv = p - q;
                 T r2 = dot(rv, rv);
-                if (r2 < rc2) wca_term_jframe(S, M, u, rv, r2, sig2, eps);
+                if (r2 < rc2) {
+                    bump<COUNT>(pc, C_JTERMS);
+                    wca_term_jframe(S, M, u, rv, r2, sig2, eps);
+                }
             }
         }
         return (unsigned)(gi.nv * gj.ne + gj.nv * gi.ne);
@@ -142,11 +151,12 @@ __device__ __forceinline__ unsigned int pair_terms(const typename R4T<T>::type *
     // 3D.  V_j x F_i (Eq. DEM, third sum), in i's frame
     for (int b = 0; b < gj.nv; ++b) {
         V3<T> p = dl + mul(M, xyz<T>(tab[gj.v_off + b]));
+        bump<COUNT>(pc, C_VTX);
         if (!(dot(p, p) < reach_i * reach_i)) continue;
         for (int f = 0; f < gi.nf; ++f) {
             V3<T> q;
             T r2;
-            if (!face_nearest<T>(tab, itab, gi.f_off + f, gi.fi_off + 2 * f, p, rc, &q, &r2))
+            if (!face_nearest<T, COUNT>(tab, itab, gi.f_off + f, gi.fi_off + 2 * f, p, rc, &q, &r2, pc))
                 continue;
             if (r2 < rc2) wca_term(S, q, q - p, r2, sig2, eps);
         }
@@ -155,13 +165,17 @@ __device__ __forceinline__ unsigned int pair_terms(const typename R4T<T>::type *
     for (int a_ = 0; a_ < gi.nv; ++a_) {
         V3<T> u = xyz<T>(tab[gi.v_off + a_]);
         V3<T> p = mul_t(M, u - dl);
+        bump<COUNT>(pc, C_VTX);
         if (!(dot(p, p) < reach_j * reach_j)) continue;
         for (int f = 0; f < gj.nf; ++f) {
             V3<T> q;
             T r2;
-            if (!face_nearest<T>(tab, itab, gj.f_off + f, gj.fi_off + 2 * f, p, rc, &q, &r2))
+            if (!face_nearest<T, COUNT>(tab, itab, gj.f_off + f, gj.fi_off + 2 * f, p, rc, &q, &r2, pc))
                 continue;
-            if (r2 < rc2) wca_term_jframe(S, M, u, p - q, r2, sig2, eps);
+            if (r2 < rc2) {
+                bump<COUNT>(pc, C_JTERMS);
+                wca_term_jframe(S, M, u, p - q, r2, sig2, eps);
+            }
         }
     }
     // E_i x E_j (Eq. DEM, first sum), in i's frame
@@ -171,13 +185,16 @@ __device__ __forceinline__ unsigned int pair_terms(const typename R4T<T>::type *
         V3<T> D2 = mul(M, xyz<T>(bd));
         V3<T> C2 = A2 + D2 * T(0.5);
         T reach = reach_i + ba.w;
+        bump<COUNT>(pc, C_EDGE);
         if (!(dot(C2, C2) < reach * reach)) continue;
         for (int ea = 0; ea < gi.ne; ++ea) {
             R4 aa = tab[gi.e_off + 2 * ea], ad = tab[gi.e_off + 2 * ea + 1];
             V3<T> A1 = xyz<T>(aa), D1 = xyz<T>(ad);
             V3<T> dc = A1 + D1 * T(0.5) - C2;
             T lim = aa.w + ba.w + rc;
+            bump<COUNT>(pc, C_SPHERE);
             if (!(dot(dc, dc) < lim * lim)) continue;
+            bump<COUNT>(pc, C_SEGSEG);
             V3<T> P1, P2;
             segment_nearest<T>(A1, D1, ad.w, A2, D2, bd.w, par_eps, &P1, &P2);
             V3<T> rv = P1 - P2;
@@ -241,7 +258,9 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
     }
     const T eps = (T)a.eps;
     const T par_eps = (T)a.par_eps;
-    unsigned long long c_pairs = 0, c_fpe = 0, c_terms = 0;
+    PathCount pc;
+    if constexpr (COUNT)
+        for (int k = 0; k < NCOUNT; ++k) pc.v[k] = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const int si = a.shape[i];
         const ShapeDev &shi = a.shapes[si];
@@ -259,6 +278,7 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
         for (int k = 0; k < nn; ++k) {
             const int j = a.nlist[(size_t)k * a.n + i];
             PairGeom pg;
+            bump<COUNT>(&pc, C_NEIGH);
             if (!pair_in_range(a, j, xi, gi.R, rnd_i, rp, &pg)) continue;
             const M33<T> Rj = orientation<T>(a, j);
             const M33<T> M = mul_tn(Ri, Rj);
@@ -267,19 +287,18 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
             const T rc = (T)(WCA_CUT * pg.sig);
             S.fp = v3<T>(T(0), T(0), T(0));
             unsigned before = S.nterm;
-            unsigned nf = pair_terms<T, COMP, DIM>(tab, itab, gi, geo[pg.gj], M, dl, rc, sig * sig,
-                                                   eps, par_eps, S);
+            unsigned nf = pair_terms<T, COMP, DIM, COUNT>(tab, itab, gi, geo[pg.gj], M, dl, rc,
+                                                          sig * sig, eps, par_eps, S, &pc);
             if (S.nterm != before) pair_virial(Rd, pg, S, W);
-            if (COUNT) { c_pairs++; c_fpe += nf; }
+            bump<COUNT>(&pc, C_PAIRS);
+            bump<COUNT>(&pc, C_FPE, nf);
         }
-        if (COUNT) c_terms += S.nterm;
+        bump<COUNT>(&pc, C_TERMS, S.nterm);
         store_particle(a, i, S, W);
     }
-    if (COUNT) {
-        atomicAdd(a.counters + 0, c_pairs);
-        atomicAdd(a.counters + 1, c_fpe);
-        atomicAdd(a.counters + 2, c_terms);
-    }
+    if constexpr (COUNT)
+        for (int k = 0; k < NCOUNT; ++k)
+            if (pc.v[k]) atomicAdd(a.counters + k, (unsigned long long)pc.v[k]);
 }
 
 template <class T, bool COMP, int DIM>

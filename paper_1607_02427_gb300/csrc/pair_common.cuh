@@ -169,21 +169,51 @@ __device__ __forceinline__ void wca_term_jframe(Sums<T, COMP> &S, const M33<T> &
 // in-plane edge tests >= 0) q is the projection; else q is the nearest
 // point on the edges whose test fails (the nearest boundary point of a
 // convex polygon lies on such an edge).
-template <class T, class R4>
+// Work counters of a counting launch (see dem_get_counters).
+enum {
+    C_PAIRS = 0,       // ordered pairs within the bounding-sphere range
+    C_FPE = 1,         // feature pairs Eq. DEM / Eq. DEM_2D assigns to them
+    C_TERMS = 2,       // terms with r < r_cut (WCA evaluated)
+    C_VTX = 3,         // vertex transforms (+ reach test)
+    C_PLANE = 4,       // face-plane tests
+    C_INPLANE = 5,     // in-plane edge tests of faces
+    C_PTSEG = 6,       // point-segment nearest points
+    C_EDGE = 7,        // edge transforms (+ reach test)
+    C_SPHERE = 8,      // edge bounding-sphere tests
+    C_SEGSEG = 9,      // segment-segment nearest points
+    C_NEIGH = 10,      // neighbour-list entries scanned
+    C_INSIDE = 11,     // vertex-face projections inside the face
+    C_JTERMS = 12,     // terms evaluated in j's frame
+    NCOUNT = 16
+};
+struct PathCount {
+    unsigned int v[NCOUNT];
+};
+template <bool COUNT>
+__device__ __forceinline__ void bump(PathCount *pc, int k, unsigned int n = 1) {
+    if constexpr (COUNT) pc->v[k] += n;
+}
+
+
+template <class T, bool COUNT, class R4>
 __device__ __forceinline__ bool face_nearest(const R4 *tab, const int *itab, int face_rec,
-                                             int face_int, V3<T> p, T rc, V3<T> *q, T *r2) {
+                                             int face_int, V3<T> p, T rc, V3<T> *q, T *r2,
+                                             PathCount *pc) {
     R4 nf = tab[face_rec];
     T h = nf.x * p.x + nf.y * p.y + nf.z * p.z - nf.w;
+    bump<COUNT>(pc, C_PLANE);
     if (!(fabs(h) < rc)) return false;
     int fe = itab[face_int], cnt = itab[face_int + 1];
     bool inside = true;
     T best = T(3.0e38);
     V3<T> bq = p;
+    bump<COUNT>(pc, C_INPLANE, (unsigned)cnt);
     for (int k = 0; k < cnt; ++k) {
         R4 m = tab[fe + 3 * k + 2];
         T s = m.x * p.x + m.y * p.y + m.z * p.z - m.w;
         if (s < T(0)) {
             inside = false;
+            bump<COUNT>(pc, C_PTSEG);
             R4 a = tab[fe + 3 * k], e = tab[fe + 3 * k + 1];
             V3<T> A = xyz<T>(a), E = xyz<T>(e);
             T t = clamp01(dot(p - A, E) * e.w);
@@ -194,6 +224,7 @@ __device__ __forceinline__ bool face_nearest(const R4 *tab, const int *itab, int
         }
     }
     if (inside) {
+        bump<COUNT>(pc, C_INSIDE);
         *q = p - xyz<T>(nf) * h;
         *r2 = h * h;
     } else {

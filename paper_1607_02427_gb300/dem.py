@@ -170,9 +170,11 @@ def dem_create(shapes: Sequence[dict], epsilon: float, sigma: float, box, replic
 
 def dem_set_state(ctx, shape_id, pos, orient, vel, angmom, device_ptrs: int = 0):
     lib = load()
-    if device_ptrs:
-        return _check(lib.dem_set_state(ctx, _ptr(shape_id), _ptr(pos), _ptr(orient), _ptr(vel),
-                                        _ptr(angmom), 1), ctx)
+    arrays = (shape_id, pos, orient, vel, angmom)
+    if device_ptrs or all(hasattr(a, "data_ptr") for a in arrays):
+        # CUDA tensors (device_ptrs=1), or host torch tensors (e.g. pinned
+        # memory) passed as they are: int32 / float64, contiguous
+        return _check(lib.dem_set_state(ctx, *[_ptr(a) for a in arrays], int(device_ptrs)), ctx)
     arrs = [_host(shape_id, np.int32)] + [_host(a, np.float64) for a in (pos, orient, vel, angmom)]
     return _check(lib.dem_set_state(ctx, *[_ptr(a) for a in arrs], 0), ctx)
 
@@ -241,7 +243,7 @@ def dem_autotune(ctx):
 
 
 def dem_get_counters(ctx) -> np.ndarray:
-    c = np.zeros(4, np.int64)
+    c = np.zeros(16, np.int64)
     _check(load().dem_get_counters(ctx, c.ctypes.data_as(C.POINTER(C.c_longlong))), ctx)
     return c
 
