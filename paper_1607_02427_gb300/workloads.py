@@ -485,7 +485,7 @@ def contact_cluster(shapes: List[dict], shape_id: Sequence[int], box: Sequence[f
     placed = 1
     for i in range(1, n):
         for _ in range(max_tries):
-            if rng.random() < free:
+            if free > 0 and rng.random() < free:
                 x = rng.random(dim) * box      # a free placement starts a new cluster
             else:
                 a = int(rng.integers(placed))

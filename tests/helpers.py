@@ -47,7 +47,7 @@ def open_cluster(shapes, shape_id, seed, gap=(0.85, 1.15), gap_min=0.8, box=400.
     rng = np.random.default_rng(seed)
     dim = shapes[0]["dim"]
     s = W.contact_cluster(shapes, shape_id, [box] * dim, rng, gap=gap, gap_min=gap_min,
-                          sigma=sigma, kT=kT)
+                          sigma=sigma, kT=kT, free=0.0)
     d = s.pos - s.pos[0]
     d -= box * np.round(d / box)
     s.pos = d - d.mean(0) + box / 2
