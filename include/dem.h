@@ -252,8 +252,45 @@ int dem_set_stream(dem_ctx *ctx, void *stream);
  * out[6] largest off-diagonal inertia element (0 in principal axes). */
 int dem_shape_info(const dem_shape *shape, double *out);
 
+/* Forces without any device allocation.  The paper has no counterpart: this
+ * is a library convenience for callers that cannot call cudaMalloc, such as
+ * code inside a framework whose pool allocator owns all device memory, a
+ * process already at its device-memory limit, or a real-time loop that must
+ * not take the device-wide synchronisation cudaMalloc and cudaFree can cause.
+ * It computes, for ONE periodic system, the forces, torques and per-particle
+ * energies dem_compute would, holding every intermediate array (packed
+ * state, geometry tables, neighbour list, status) in one static device array
+ * of the library: about 8.3 MiB, reserved on every GPU that loads libdem until
+ * the process exits.
+ *   shapes, n_shapes, epsilon, sigma, precision   as for dem_create (host)
+ *   box        dim box lengths (host); each edge at least twice the
+ *              interaction range 2 R_max + r_cut, else DEM_ERR_BOX
+ *   n          1 <= n <= DEM_NOALLOC_MAX_N, else DEM_ERR_ARG
+ *   shape_id   device, n ints;  pos device, n*dim;  orient device, n*4
+ *              quaternions (3D) or n angles (2D)
+ *   force      device, n*dim (world frame), written
+ *   torque     device, 3D n*3 (world frame) or 2D n, written
+ *   energy     device, n (half of each pair's energy per particle) or NULL
+ *   stream     cudaStream_t to run on; NULL is the default stream
+ * Neighbours are searched over all pairs (cost ~ n^2: meant for small
+ * systems); a particle with more than DEM_NOALLOC_MAX_NEIGHBOURS partners in
+ * range gives DEM_ERR_NLIST_OVERFLOW, since no memory can be added.  The call
+ * returns after its stream has finished the work.  The first call on each
+ * device looks up the static array's address with that device current; make
+ * that first call before any stream capture.  Every call on a device shares
+ * the one array, which keeps the last call's contents (each call clears what
+ * must start at zero); calls that overlap on the GPU (from other threads or
+ * streams) race, so the caller must serialise them.  Errors are reported by
+ * dem_last_error(NULL). */
+#define DEM_NOALLOC_MAX_N 16384
+#define DEM_NOALLOC_MAX_NEIGHBOURS 64
+int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double epsilon, double sigma,
+                       const double *box, int n, const int *shape_id, const double *pos,
+                       const double *orient, int precision, double *force, double *torque,
+                       double *energy, void *stream);
+
 /* One-line description of the last error of ctx (or of the last failed
- * dem_create when ctx is NULL). */
+ * dem_create or dem_forces_noalloc when ctx is NULL). */
 const char *dem_last_error(const dem_ctx *ctx);
 
 void dem_destroy(dem_ctx *ctx);

@@ -238,6 +238,104 @@ bool same_geom(const HostGeom &a, const HostGeom &b) {
 
 }  // namespace
 
+// The message dem_last_error(NULL) returns, for entry points without a context.
+void dem::set_global_error(const std::string &msg) { g_create_error = msg; }
+
+// Host copies of the geometry tables (same layout as a context's), for the
+// entry point that evaluates forces without a context (noalloc.cu).
+int dem::make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t,
+                          std::string *err) {
+    std::vector<HostGeom> geoms;
+    std::vector<HostShape> hs;
+    for (int s = 0; s < n_shapes; ++s) {
+        HostGeom g;
+        HostShape h;
+        int rc = preprocess_shape(shapes[s], &g, &h, err);
+        if (rc) return rc;
+        if (shapes[s].dim != shapes[0].dim) { *err = "all shapes must have the same dim"; return DEM_ERR_ARG; }
+        int gid = -1;
+        for (size_t k = 0; k < geoms.size(); ++k)
+            if (same_geom(geoms[k], g)) { gid = (int)k; break; }
+        if (gid < 0) {
+            if ((int)geoms.size() >= MAX_GEOMS) { *err = "too many distinct geometries"; return DEM_ERR_ARG; }
+            gid = (int)geoms.size();
+            geoms.push_back(g);
+        }
+        h.geom = gid;
+        hs.push_back(h);
+    }
+    t->dim = shapes[0].dim;
+    t->td.clear(); t->itab.clear(); t->geoms.clear(); t->shapes.clear();
+    t->Rmax = 0; t->rnd_max = 0;
+    for (auto &g : geoms) {
+        Geom G = {};
+        G.nv = (int)(g.v.size() / 3);
+        G.ne = (int)g.edges.size();
+        G.nf = (int)g.faces.size();
+        G.R = (float)(g.R * (1.0 + 1e-6) + 1e-7);
+        t->Rmax = std::max(t->Rmax, (double)G.R);
+        G.v_off = (int)t->td.size();
+        for (int k = 0; k < G.nv; ++k)
+            t->td.push_back(make_double4_32a(g.v[3 * k], g.v[3 * k + 1], g.v[3 * k + 2], 0.0));
+        G.e_off = (int)t->td.size();
+        for (auto &e : g.edges) {
+            D3 a = d3(&g.v[3 * e.first]), b = d3(&g.v[3 * e.second]);
+            D3 d = sub(b, a);
+            double ln = norm(d);
+            t->td.push_back(make_double4_32a(a.x, a.y, a.z, 0.5 * ln * (1.0 + 1e-5) + 1e-6));
+            t->td.push_back(make_double4_32a(d.x, d.y, d.z, 1.0 / (ln * ln)));
+        }
+        G.f_off = (int)t->td.size();
+        std::vector<D3> normals;
+        for (auto &loop : g.faces) {
+            size_t m = loop.size();
+            D3 n = {0, 0, 0};
+            for (size_t k = 0; k < m; ++k)
+                n = add(n, crossp(d3(&g.v[3 * loop[k]]), d3(&g.v[3 * loop[(k + 1) % m]])));
+            n = scl(n, 1.0 / norm(n));
+            normals.push_back(n);
+            t->td.push_back(make_double4_32a(n.x, n.y, n.z, dotp(n, d3(&g.v[3 * loop[0]]))));
+        }
+        G.fe_off = (int)t->td.size();
+        G.fi_off = (int)t->itab.size();
+        int nfe = 0;
+        for (size_t f = 0; f < g.faces.size(); ++f) {
+            auto &loop = g.faces[f];
+            size_t m = loop.size();
+            t->itab.push_back((int)t->td.size());
+            t->itab.push_back((int)m);
+            for (size_t k = 0; k < m; ++k) {
+                D3 a = d3(&g.v[3 * loop[k]]), b = d3(&g.v[3 * loop[(k + 1) % m]]);
+                D3 e = sub(b, a);
+                D3 mm = crossp(normals[f], e);
+                mm = scl(mm, 1.0 / norm(mm));
+                t->td.push_back(make_double4_32a(a.x, a.y, a.z, 0.0));
+                t->td.push_back(make_double4_32a(e.x, e.y, e.z, 1.0 / dotp(e, e)));
+                t->td.push_back(make_double4_32a(mm.x, mm.y, mm.z, dotp(mm, a)));
+                ++nfe;
+            }
+        }
+        G.nfe = nfe;
+        t->geoms.push_back(G);
+    }
+    if (t->itab.empty()) { t->itab.push_back(0); t->itab.push_back(0); }
+    t->tf.resize(t->td.size());
+    for (size_t k = 0; k < t->td.size(); ++k)
+        t->tf[k] = make_float4((float)t->td[k].x, (float)t->td[k].y, (float)t->td[k].z,
+                               (float)t->td[k].w);
+    for (auto &h : hs) {
+        ShapeDev sd = {};
+        sd.geom = h.geom;
+        sd.R = t->geoms[h.geom].R;
+        sd.rounding = h.rounding;
+        sd.mass = h.mass;
+        for (int k = 0; k < 3; ++k) sd.inertia[k] = h.inertia[k];
+        t->rnd_max = std::max(t->rnd_max, h.rounding);
+        t->shapes.push_back(sd);
+    }
+    return DEM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------

@@ -19,6 +19,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 #include "dem.h"
 
 namespace dem {
@@ -163,5 +166,19 @@ cudaError_t launch_export_forces(int n, int dim, const double4_32a *force, const
                                  cudaStream_t s);
 cudaError_t launch_rescale(int n, int dim, double4_32a *pos, double4_32a *x_last, const int *rep,
                            const double *scale3, cudaStream_t s);
+
+// Geometry tables of a shape set built on the host, in the layout the pair
+// kernels read (api.cu).
+struct HostTables {
+    int dim = 3;
+    std::vector<float4> tf;
+    std::vector<double4_32a> td;
+    std::vector<int> itab;
+    std::vector<Geom> geoms;
+    std::vector<ShapeDev> shapes;
+    double Rmax = 0, rnd_max = 0;
+};
+int make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t, std::string *err);
+void set_global_error(const std::string &msg);
 
 }  // namespace dem

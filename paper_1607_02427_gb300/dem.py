@@ -37,7 +37,9 @@ EXPORTS = ["dem_create", "dem_set_state", "dem_get_state", "dem_set_thermostat",
            "dem_compute", "dem_get_forces", "dem_get_energy", "dem_get_particle_energy",
            "dem_get_virial", "dem_set_box", "dem_set_param", "dem_get_param", "dem_autotune",
            "dem_get_counters", "dem_set_stream", "dem_shape_info", "dem_last_error",
-           "dem_destroy"]
+           "dem_destroy", "dem_forces_noalloc"]
+DEM_NOALLOC_MAX_N = 16384
+DEM_NOALLOC_MAX_NEIGHBOURS = 64
 
 
 class DemError(RuntimeError):
@@ -86,6 +88,8 @@ def load():
         "dem_set_stream": [vp, vp],
         "dem_shape_info": [C.POINTER(dem_shape), dp],
         "dem_destroy": [vp],
+        "dem_forces_noalloc": [C.POINTER(dem_shape), C.c_int, C.c_double, C.c_double, dp,
+                               C.c_int, vp, vp, vp, C.c_int, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -256,6 +260,27 @@ def dem_set_stream(ctx, stream_handle: Optional[int]):
 def dem_destroy(ctx):
     if ctx:
         load().dem_destroy(ctx)
+
+
+def dem_forces_noalloc(shapes: Sequence[dict], epsilon: float, sigma: float, box, shape_id,
+                       pos, orient, precision: int, force, torque, energy=None,
+                       stream_handle: Optional[int] = None):
+    """Forces of one system with no device allocation (see dem.h).  shape_id,
+    pos, orient, force, torque and energy are CUDA tensors."""
+    lib = load()
+    arr = (dem_shape * len(shapes))()
+    keep = []
+    for k, sh in enumerate(shapes):
+        s, kk = make_shape(sh)
+        arr[k] = s
+        keep += kk
+    b = _host(np.asarray(box, np.float64).ravel(), np.float64)
+    n = int(shape_id.shape[0])
+    return _check(lib.dem_forces_noalloc(arr, len(shapes), float(epsilon), float(sigma),
+                                         b.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                         _ptr(shape_id), _ptr(pos), _ptr(orient), int(precision),
+                                         _ptr(force), _ptr(torque), _ptr(energy),
+                                         C.c_void_p(stream_handle) if stream_handle else None))
 
 
 class DEM:
