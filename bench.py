@@ -75,6 +75,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the e2e, FP64 and CPU-baseline measurements")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--decomp", default="auto", choices=["auto", "thread", "warp"])
     return p.parse_args()
 
 
@@ -283,6 +284,15 @@ def main():
     d = prepare(dem, system, run, prec, a.compress_steps, a.equil_steps)
     stream = torch.cuda.current_stream()
     dem.dem_set_stream(d.ctx, stream.cuda_stream)
+    if a.decomp == "auto":
+        dem.dem_autotune(d.ctx)
+    else:
+        d.set_param("decomp", {"thread": 1, "warp": 2}[a.decomp])
+    decomp_name = {1: "thread", 2: "warp", 3: "tiled"}[int(d.get_param("decomp"))]
+    tune = {}
+    if a.decomp == "auto":
+        for k, nm in enumerate(["thread64", "thread128", "warp128"]):
+            tune[nm] = d.get_param(f"autotune_ms_{k}")
 
     # warm-up
     d.step(a.warmup, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
@@ -346,13 +356,15 @@ def main():
             "workload": system.name, "replicas": system.n_replicas, "particles": system.n,
             "precision": {0: "fp64", 1: "fp32", 2: "fp32 pair kernel, two-sum sums, fp64 state"}[prec],
             "ensemble": run["ensemble"], "dt": run["dt"], "graph": True,
+            "decomposition": decomp_name,
             "l2": "inputs larger than L2 (per-step working set > 129 MB)",
             "parallelism": f"replicas x{world}",
         },
         "roofline": {
             "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ncu_traffic(a.workload, a.precision),
-            "kernel": "pair-feature kernel (k_pair_thread)",
+            "kernel": f"pair-feature kernel (decomposition {decomp_name})",
+            "autotune_ms": tune,
             "kernel_ms": pair_ms, "kernel_share_of_step": pair_ms / (t_max / a.steps),
             "flops_per_launch": flops, "feature_pairs_per_launch": pair_fpe,
             "feature_pairs_per_s": pair_fpe / (pair_ms / 1e3),

@@ -216,8 +216,11 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value);
 int dem_get_param(dem_ctx *ctx, const char *name, double *value);
 
 /* Run every pair-kernel decomposition and block size on the current state
- * and keep the fastest (timed with CUDA events).  Results are identical for
- * every choice up to floating-point summation order. */
+ * and keep the fastest (timed with CUDA events on the context's stream).
+ * Candidates, in order: THREAD with 64 and 128 threads per block, WARP;
+ * their mean times are readable as parameters "autotune_ms_0", ... .
+ * Results are identical for every choice up to floating-point summation
+ * order; the chosen one is the "decomp" and "block" parameters. */
 int dem_autotune(dem_ctx *ctx);
 
 /* Work counters of one force evaluation at the current state (host array of
@@ -260,7 +263,7 @@ int dem_shape_info(const dem_shape *shape, double *out);
  * It computes, for ONE periodic system, the forces, torques and per-particle
  * energies dem_compute would, holding every intermediate array (packed
  * state, geometry tables, neighbour list, status) in one static device array
- * of the library: about 8.3 MiB, reserved on every GPU that loads libdem until
+ * of the library: about 20 MiB, reserved on every GPU that loads libdem until
  * the process exits.
  *   shapes, n_shapes, epsilon, sigma, precision   as for dem_create (host)
  *   box        dim box lengths (host); each edge at least twice the

@@ -328,6 +328,7 @@ int dem::make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t,
         sd.geom = h.geom;
         sd.R = t->geoms[h.geom].R;
         sd.rounding = h.rounding;
+        sd.rounding_f = (float)h.rounding;
         sd.mass = h.mass;
         for (int k = 0; k < 3; ++k) sd.inertia[k] = h.inertia[k];
         t->rnd_max = std::max(t->rnd_max, h.rounding);
@@ -366,7 +367,8 @@ struct dem_ctx {
     double4_32a *pos = nullptr, *vel = nullptr, *quat = nullptr, *angmom = nullptr;
     double4_32a *force = nullptr, *torque = nullptr, *x_last = nullptr;
     float4 *quatf = nullptr;
-    int *shape = nullptr, *rep = nullptr, *nlist = nullptr, *nn = nullptr;
+    int *shape = nullptr, *rep = nullptr, *nn = nullptr;
+    float4 *nlist = nullptr, *delta = nullptr;
     int *cell_count = nullptr, *cell_slots = nullptr;
     double *energy = nullptr, *virial = nullptr, *ke = nullptr;
     double *staging = nullptr;        // N * 4 doubles
@@ -397,6 +399,7 @@ struct dem_ctx {
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms = 0.0;
     long long prof_n = 0;
+    std::vector<float> tune_ms;   // pair-kernel ms of each autotuner candidate
     std::string err;
 };
 
@@ -513,6 +516,7 @@ int upload_tables(dem_ctx *ctx) {
         sd[s].geom = ctx->shapes[s].geom;
         sd[s].R = gd[ctx->shapes[s].geom].R;
         sd[s].rounding = ctx->shapes[s].rounding;
+        sd[s].rounding_f = (float)ctx->shapes[s].rounding;
         sd[s].mass = ctx->shapes[s].mass;
         for (int k = 0; k < 3; ++k) sd[s].inertia[k] = ctx->shapes[s].inertia[k];
     }
@@ -614,7 +618,7 @@ PairArgs pair_args(dem_ctx *ctx) {
     a.geoms = ctx->d_geoms; a.n_geoms = ctx->n_geoms;
     a.table = ctx->d_table; a.table_len = ctx->table_len;
     a.itable = ctx->d_itable; a.itable_len = ctx->itable_len;
-    a.nlist = ctx->nlist; a.nn = ctx->nn;
+    a.nlist = ctx->nlist; a.nn = ctx->nn; a.delta = ctx->delta;
     a.force = ctx->force; a.torque = ctx->torque; a.energy = ctx->energy; a.virial = ctx->virial;
     a.eps = ctx->eps; a.sigma = ctx->sigma; a.par_eps = ctx->par_eps;
     a.status = ctx->status;
@@ -629,6 +633,7 @@ NlistArgs nlist_args(dem_ctx *ctx) {
     a.shapes = ctx->d_shapes; a.sigma = ctx->sigma; a.skin = ctx->skin;
     a.cell_count = ctx->cell_count; a.cell_slots = ctx->cell_slots;
     a.nlist = ctx->nlist; a.nn = ctx->nn; a.x_last = ctx->x_last; a.status = ctx->status;
+    a.delta = ctx->delta;
     a.half_skin2 = (float)(0.25 * ctx->skin * ctx->skin);
     return a;
 }
@@ -638,7 +643,8 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     a.n = ctx->N; a.dim = ctx->dim; a.n_reps = ctx->R; a.dt = dt; a.nvt = ens == DEM_NVT;
     a.kT = kT; a.tau = tau;
     a.pos = ctx->pos; a.vel = ctx->vel; a.quat = ctx->quat; a.angmom = ctx->angmom;
-    a.x_last = ctx->x_last; a.quatf = ctx->quatf; a.force = ctx->force; a.torque = ctx->torque;
+    a.x_last = ctx->x_last; a.quatf = ctx->quatf; a.delta = ctx->delta;
+    a.force = ctx->force; a.torque = ctx->torque;
     a.shape = ctx->shape; a.rep = ctx->rep; a.reps = ctx->d_reps; a.shapes = ctx->d_shapes;
     a.ke = ctx->ke; a.thermo = ctx->thermo; a.status = ctx->status;
     return a;
@@ -851,7 +857,7 @@ void dem_destroy(dem_ctx *ctx) {
     if (!ctx) return;
     free_graph(ctx);
     void *ptrs[] = {ctx->pos, ctx->vel, ctx->quat, ctx->angmom, ctx->force, ctx->torque,
-                    ctx->x_last, ctx->quatf, ctx->shape, ctx->rep, ctx->nlist, ctx->nn,
+                    ctx->x_last, ctx->quatf, ctx->delta, ctx->shape, ctx->rep, ctx->nlist, ctx->nn,
                     ctx->cell_count, ctx->cell_slots, ctx->energy, ctx->virial, ctx->ke,
                     ctx->staging, ctx->red, ctx->scale3, ctx->status, ctx->thermo, ctx->d_reps,
                     ctx->d_shapes, ctx->d_geoms, ctx->d_table, ctx->d_itable, ctx->d_counters,
@@ -934,7 +940,8 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
         size_t n = N;
         CK(dalloc(&ctx->pos, n)); CK(dalloc(&ctx->vel, n)); CK(dalloc(&ctx->quat, n));
         CK(dalloc(&ctx->angmom, n)); CK(dalloc(&ctx->force, n)); CK(dalloc(&ctx->torque, n));
-        CK(dalloc(&ctx->x_last, n)); CK(dalloc(&ctx->quatf, n));
+        CK(dalloc(&ctx->x_last, n)); CK(dalloc(&ctx->quatf, n)); CK(dalloc(&ctx->delta, n));
+        CK(cudaMemset(ctx->delta, 0, sizeof(float4) * n));
         CK(dalloc(&ctx->shape, n)); CK(dalloc(&ctx->rep, n)); CK(dalloc(&ctx->nn, n));
         CK(dalloc(&ctx->energy, n)); CK(dalloc(&ctx->virial, 6 * n)); CK(dalloc(&ctx->ke, n));
         CK(dalloc(&ctx->staging, 4 * n));
@@ -1036,6 +1043,11 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
     else if (n == "pair_ms_total") *value = ctx->prof_ms;
     else if (n == "pair_launches") *value = (double)ctx->prof_n;
     else if (n == "launches") *value = (double)ctx->launches;
+    else if (n.rfind("autotune_ms_", 0) == 0) {
+        size_t k = (size_t)atoi(n.c_str() + 12);
+        if (k >= ctx->tune_ms.size()) return set_err(ctx, DEM_ERR_ARG, "no such autotune result");
+        *value = ctx->tune_ms[k];
+    }
     else if (n == "nlist_cap") *value = ctx->cap;
     else if (n == "n_cells") *value = ctx->n_cells;
     else if (n == "allpairs_replicas") {
@@ -1329,10 +1341,40 @@ int dem_get_counters(dem_ctx *ctx, long long *counts) {
 int dem_autotune(dem_ctx *ctx) {
     if (!valid(ctx)) return DEM_ERR_ARG;
     if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
-    ctx->decomp = DEM_DECOMP_THREAD;
-    ctx->block = 0;
+    int rc = compute_forces(ctx);   // the list is current before timing
+    if (rc) return rc;
+    struct Cand { int decomp, block; };
+    const Cand cands[] = {{DEM_DECOMP_THREAD, 64}, {DEM_DECOMP_THREAD, 128},
+                          {DEM_DECOMP_WARP, 128}};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 3.0e38f;
+    Cand pick = cands[0];
+    ctx->tune_ms.clear();
+    for (const Cand &c : cands) {
+        PairArgs pa = pair_args(ctx);
+        CK(launch_pair(pa, ctx->precision, c.decomp, c.block, false, ctx->stream));   // warm-up
+        CK(cudaEventRecord(e0, ctx->stream));
+        const int reps = 3;
+        for (int r = 0; r < reps; ++r)
+            CK(launch_pair(pa, ctx->precision, c.decomp, c.block, false, ctx->stream));
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= reps;
+        ctx->tune_ms.push_back(ms);
+        if (ms < best) { best = ms; pick = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->launches += 4 * (long long)(sizeof(cands) / sizeof(cands[0]));
+    ctx->decomp = pick.decomp;
+    ctx->block = pick.block;
     free_graph(ctx);
-    return DEM_OK;
+    // the last timed launch left the forces of the current state in place
+    return compute_forces(ctx);
 }
 
 }  // extern "C"

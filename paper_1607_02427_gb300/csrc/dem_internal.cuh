@@ -8,7 +8,11 @@
 //   shape, rep   : int[N]     shape index and replica index of each particle
 //   energy, ke   : double[N]  per-particle potential / kinetic energy
 //   virial       : double[6N] symmetric per-particle virial
-//   nlist        : int[cap * N], column-major (slot k of particle i at k*N+i)
+//   nlist        : float4[cap * N], column-major (slot k of particle i at
+//                  k*N+i): x, y, z = x_j - x_i (minimum image, FP32) when the
+//                  list was built, w = the bits of the int j
+//   delta        : float4[N]  x_i - x_i(list build) (minimum image, FP32), so
+//                  that x_j - x_i = d0 + delta_j - delta_i between builds
 //   nn           : int[N]     neighbour count
 //   cell_count   : int[C]     particles per cell (C cells over all replicas)
 //   cell_slots   : int[C * cell_cap]
@@ -52,6 +56,8 @@ struct ShapeDev {
     double rounding;
     double mass;
     double inertia[3];   // principal moments (2D: inertia[2] = I_z)
+    float rounding_f;    // FP32 copy of rounding for the FP32 kernels
+    float pad;
 };
 
 struct Rep {
@@ -99,7 +105,9 @@ struct PairArgs {
     int table_len;           // records
     const int *itable;       // face -> (fe_begin, fe_count) pairs
     int itable_len;
-    const int *nlist, *nn;
+    const float4 *nlist;
+    const int *nn;
+    const float4 *delta;
     double4_32a *force, *torque;
     double *energy, *virial;
     double eps, sigma, par_eps;
@@ -115,8 +123,10 @@ struct NlistArgs {
     const ShapeDev *shapes;
     double sigma, skin;
     int *cell_count, *cell_slots;
-    int *nlist, *nn;
+    float4 *nlist;
+    int *nn;
     double4_32a *x_last;
+    float4 *delta;
     Status *status;
     float half_skin2;        // rebuild threshold (skin/2)^2
 };
@@ -127,7 +137,7 @@ struct StepArgs {
     int nvt;
     double kT, tau;
     double4_32a *pos, *vel, *quat, *angmom, *x_last;
-    float4 *quatf;
+    float4 *quatf, *delta;
     const double4_32a *force, *torque;
     const int *shape, *rep;
     const Rep *reps;

@@ -19,8 +19,7 @@
 namespace dem {
 namespace {
 
-__device__ __forceinline__ void quat_rotate_body(double4_32a &q, int k, double phi) {
-    double c = cos(0.5 * phi), s = sin(0.5 * phi);
+__device__ __forceinline__ void quat_rotate_body(double4_32a &q, int k, double c, double s) {
     // r = (c, s e_k); q <- q (x) r ; q = (x:w, y:x, z:y, w:z)
     double w1 = q.x, x1 = q.y, y1 = q.z, z1 = q.w;
     double w2 = c, x2 = k == 0 ? s : 0.0, y2 = k == 1 ? s : 0.0, z2 = k == 2 ? s : 0.0;
@@ -37,13 +36,18 @@ __device__ __forceinline__ void set_comp(double4_32a &v, int k, double x) {
     if (k == 0) v.x = x; else if (k == 1) v.y = x; else v.z = x;
 }
 
+// One sincos of phi/2 serves both the quaternion (half angle) and the
+// angular momentum (cos phi = 1 - 2 s^2, sin phi = 2 s c): FP64
+// transcendentals are expensive on this part.
 __device__ __forceinline__ void free_rotor_axis(double4_32a &q, double4_32a &L, const double *I, int k,
                                                 double dt) {
     if (!(I[k] > 0.0)) return;
     double phi = comp(L, k) / I[k] * dt;
-    quat_rotate_body(q, k, phi);
+    double sh, ch;
+    sincos(0.5 * phi, &sh, &ch);
+    quat_rotate_body(q, k, ch, sh);
     int a = (k + 1) % 3, b = (k + 2) % 3;
-    double c = cos(phi), s = sin(phi);
+    double c = 1.0 - 2.0 * sh * sh, s = 2.0 * sh * ch;
     double La = comp(L, a), Lb = comp(L, b);
     set_comp(L, a, c * La + s * Lb);
     set_comp(L, b, -s * La + c * Lb);
@@ -96,6 +100,7 @@ __global__ void k_first_half(const StepArgs a) {
         dy -= rp.L[1] * rint(dy / rp.L[1]);
         if (a.dim == 3) dz -= rp.L[2] * rint(dz / rp.L[2]); else dz = 0.0;
         dmax = fmaxf(dmax, (float)(dx * dx + dy * dy + dz * dz));
+        a.delta[i] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
     }
     // warp max, one atomic per warp (non-negative floats order like their bits)
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));

@@ -13,6 +13,10 @@
 // particles of the replica instead of the 27-cell (9 in 2D) stencil.
 // Neighbour indices are sorted so that the pair kernels sum in a fixed
 // order regardless of the order in which atomics filled the cells.
+// Each entry also carries x_j - x_i at build time (minimum image taken here in
+// FP64, then rounded to FP32); the integrator keeps each particle's FP32
+// displacement since the build, so the FP32 pair kernels form
+// x_j - x_i = d0 + delta_j - delta_i without FP64 arithmetic.
 #include "dem_internal.cuh"
 
 namespace dem {
@@ -58,7 +62,9 @@ __device__ __forceinline__ void consider(const NlistArgs &a, int i, int j, doubl
     double sig = a.sigma > 0.0 ? a.sigma : rnd_i + sj.rounding;
     double lim = Ri + (double)sj.R + WCA_CUT * sig + a.skin;
     if (dx * dx + dy * dy + dz * dz < lim * lim) {
-        if (*count < a.cap) a.nlist[(size_t)(*count) * a.n + i] = j;
+        if (*count < a.cap)
+            a.nlist[(size_t)(*count) * a.n + i] =
+                make_float4((float)dx, (float)dy, (float)dz, __int_as_float(j));
         (*count)++;
     }
 }
@@ -103,9 +109,9 @@ __global__ void k_nlist(const NlistArgs a) {
         }
         // insertion sort of the column (ascending j)
         for (int p = 1; p < count; ++p) {
-            int v = a.nlist[(size_t)p * a.n + i];
+            float4 v = a.nlist[(size_t)p * a.n + i];
             int q = p - 1;
-            while (q >= 0 && a.nlist[(size_t)q * a.n + i] > v) {
+            while (q >= 0 && __float_as_int(a.nlist[(size_t)q * a.n + i].w) > __float_as_int(v.w)) {
                 a.nlist[(size_t)(q + 1) * a.n + i] = a.nlist[(size_t)q * a.n + i];
                 --q;
             }
@@ -113,6 +119,7 @@ __global__ void k_nlist(const NlistArgs a) {
         }
         a.nn[i] = count;
         a.x_last[i] = xi;
+        a.delta[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 

@@ -9,7 +9,7 @@
 // synchronisation cudaMalloc and cudaFree can cause.  They can still get
 // forces from this entry point.
 //
-// The static array is about 8.3 MiB and is reserved on every GPU that loads
+// The static array is about 20 MiB and is reserved on every GPU that loads
 // the library, until the process exits.  All calls on a device share it and
 // it keeps the last call's contents, so each call clears what must start at
 // zero (the status word, the replica index of every particle), and calls
@@ -43,8 +43,9 @@ constexpr size_t OFF_VIRIAL = OFF_ENERGY + align256(sizeof(double) * MAX_N);
 constexpr size_t OFF_SHAPE = OFF_VIRIAL + align256(6 * sizeof(double) * MAX_N);
 constexpr size_t OFF_REP = OFF_SHAPE + align256(sizeof(int) * MAX_N);
 constexpr size_t OFF_NN = OFF_REP + align256(sizeof(int) * MAX_N);
-constexpr size_t OFF_NLIST = OFF_NN + align256(sizeof(int) * MAX_N);
-constexpr size_t OFF_TABLE = OFF_NLIST + align256(sizeof(int) * (size_t)MAX_N * CAP);
+constexpr size_t OFF_DELTA = OFF_NN + align256(sizeof(int) * MAX_N);
+constexpr size_t OFF_NLIST = OFF_DELTA + align256(sizeof(float4) * MAX_N);
+constexpr size_t OFF_TABLE = OFF_NLIST + align256(sizeof(float4) * (size_t)MAX_N * CAP);
 constexpr size_t OFF_GEOMS = OFF_TABLE + align256(TABLE_BYTES);
 constexpr size_t OFF_ITAB = OFF_GEOMS + align256(sizeof(Geom) * MAX_GEOMS);
 constexpr size_t OFF_SHAPES = OFF_ITAB + align256(sizeof(int) * MAX_ITAB);
@@ -143,7 +144,8 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     int *shp = reinterpret_cast<int *>(b + OFF_SHAPE);
     int *rep = reinterpret_cast<int *>(b + OFF_REP);
     int *nn = reinterpret_cast<int *>(b + OFF_NN);
-    int *nlist = reinterpret_cast<int *>(b + OFF_NLIST);
+    float4 *delta = reinterpret_cast<float4 *>(b + OFF_DELTA);
+    float4 *nlist = reinterpret_cast<float4 *>(b + OFF_NLIST);
     void *table = b + OFF_TABLE;
     Geom *geoms = reinterpret_cast<Geom *>(b + OFF_GEOMS);
     int *itab = reinterpret_cast<int *>(b + OFF_ITAB);
@@ -185,6 +187,7 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     na.sigma = sigma > 0 ? sigma : 0.0; na.skin = 0.0;
     na.cell_count = nullptr; na.cell_slots = nullptr;
     na.nlist = nlist; na.nn = nn; na.x_last = xlast; na.status = status; na.half_skin2 = 0.f;
+    na.delta = delta;
     NA_CK(launch_nlist(na, st));
     PairArgs pa = {};
     pa.n = n; pa.dim = dim; pa.cap = CAP;
@@ -193,7 +196,7 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     pa.geoms = geoms; pa.n_geoms = (int)t.geoms.size();
     pa.table = table; pa.table_len = (int)t.td.size();
     pa.itable = itab; pa.itable_len = (int)t.itab.size();
-    pa.nlist = nlist; pa.nn = nn;
+    pa.nlist = nlist; pa.nn = nn; pa.delta = delta;
     pa.force = force4; pa.torque = torque4; pa.energy = en; pa.virial = vir;
     pa.eps = epsilon; pa.sigma = sigma > 0 ? sigma : 0.0; pa.par_eps = 1e-6;
     pa.status = status; pa.counters = nullptr;

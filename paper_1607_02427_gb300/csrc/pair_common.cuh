@@ -89,6 +89,9 @@ template <class T, bool COMP> struct Acc {
     T s;
     __device__ __forceinline__ void zero() { s = T(0); }
     __device__ __forceinline__ void add(T x) { s += x; }
+    // merge another lane's accumulator (os, oc); oc is unused without two-sum
+    __device__ __forceinline__ void merge(T os, T) { s += os; }
+    __device__ __forceinline__ T comp() const { return T(0); }
     __device__ __forceinline__ double get() const { return (double)s; }
 };
 template <> struct Acc<float, true> {
@@ -101,74 +104,66 @@ template <> struct Acc<float, true> {
         s = t;
         c = __fadd_rn(c, e);
     }
+    // two-sum of the leading parts, the trailing parts added to the error
+    __device__ __forceinline__ void merge(float os, float oc) {
+        float t = __fadd_rn(s, os);
+        float bp = __fsub_rn(t, s);
+        float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(os, bp));
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, oc), e);
+    }
+    __device__ __forceinline__ float comp() const { return c; }
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
-// Per-particle accumulators of one owner i.
+// Per-particle accumulators of one owner i: force and torque in i's body
+// frame, energy, and the symmetric body-frame virial (xx, xy, xz, yy, yz, zz).
 template <class T, bool COMP> struct Sums {
-    Acc<T, COMP> f[3], t[3];
-    double u;
-    V3<T> fp;            // force of the current pair (virial)
-    unsigned int nterm;  // contributing terms (counting launches)
+    Acc<T, COMP> f[3], t[3], u, w[6];
+    unsigned int nterm;  // terms evaluated (counting launches)
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int k = 0; k < 3; ++k) { f[k].zero(); t[k].zero(); }
-        u = 0.0;
-        fp = v3<T>(T(0), T(0), T(0));
+        u.zero();
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k].zero();
         nterm = 0;
     }
 };
 
-struct PairConst {
-    float eps;
-    double epsd;
-};
-
-// One WCA term (Eq. LJ, Eq. WCA) with nearest points p_i, p_j in i's frame:
-// pi = p_i - x_i (lever arm), rv = p_i - p_j, r2 = |rv|^2 < r_cut^2.
-// Force on i: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 * rv;  U = 4 eps ((s/r)^12 -
-// (s/r)^6) + eps (the shift removes U_LJ(r_cut) = -eps).
-template <class T, bool COMP>
-__device__ __forceinline__ void wca_term(Sums<T, COMP> &S, V3<T> pi, V3<T> rv, T r2, T sig2,
-                                         T eps) {
+// WCA of one feature pair (Eq. LJ, Eq. WCA) at squared nearest-point distance
+// r2 < r_cut^2: returns w with the force on i equal to w (p_i - p_j), and
+// *U = 4 eps ((s/r)^12 - (s/r)^6) + eps (the shift removes U_LJ(r_cut) = -eps).
+template <class T>
+__device__ __forceinline__ T wca_factor(T r2, T sig2, T eps, T *U) {
     T ir2 = T(1) / r2;
     T s2 = sig2 * ir2;
     T s6 = s2 * s2 * s2;
     T s12 = s6 * s6;
-    T w = T(24) * eps * (T(2) * s12 - s6) * ir2;
-    V3<T> f = rv * w;
-    V3<T> tq = cross(pi, f);
-    S.f[0].add(f.x); S.f[1].add(f.y); S.f[2].add(f.z);
-    S.t[0].add(tq.x); S.t[1].add(tq.y); S.t[2].add(tq.z);
-    S.fp = S.fp + f;
-    S.u += 0.5 * (double)(T(4) * eps * (s12 - s6) + eps);
-    S.nterm++;
+    *U = T(4) * eps * (s12 - s6) + eps;
+    return T(24) * eps * (T(2) * s12 - s6) * ir2;
 }
-// Same, for a term whose geometry was evaluated in j's frame: rvj = p_i - p_j
-// in j's frame; the force is mapped to i's frame with M; pi in i's frame.
+
+// Accumulate one term: force f on i and lever arm pi = p_i - x_i, both in
+// i's frame; half the energy; the body-frame virial 1/2 sym((-dl) (x) f)
+// with dl = x_j - x_i in i's frame (the world virial is R_i W R_i^T).
 template <class T, bool COMP>
-__device__ __forceinline__ void wca_term_jframe(Sums<T, COMP> &S, const M33<T> &M, V3<T> pi,
-                                                V3<T> rvj, T r2, T sig2, T eps) {
-    T ir2 = T(1) / r2;
-    T s2 = sig2 * ir2;
-    T s6 = s2 * s2 * s2;
-    T s12 = s6 * s6;
-    T w = T(24) * eps * (T(2) * s12 - s6) * ir2;
-    V3<T> f = mul(M, rvj * w);
+__device__ __forceinline__ void add_term_body(Sums<T, COMP> &S, V3<T> pi, V3<T> f, V3<T> dl,
+                                              T U) {
     V3<T> tq = cross(pi, f);
     S.f[0].add(f.x); S.f[1].add(f.y); S.f[2].add(f.z);
     S.t[0].add(tq.x); S.t[1].add(tq.y); S.t[2].add(tq.z);
-    S.fp = S.fp + f;
-    S.u += 0.5 * (double)(T(4) * eps * (s12 - s6) + eps);
+    S.u.add(T(0.5) * U);
+    const T x = -dl.x, y = -dl.y, z = -dl.z;
+    S.w[0].add(T(0.5) * x * f.x);
+    S.w[1].add(T(0.25) * (x * f.y + y * f.x));
+    S.w[2].add(T(0.25) * (x * f.z + z * f.x));
+    S.w[3].add(T(0.5) * y * f.y);
+    S.w[4].add(T(0.25) * (y * f.z + z * f.y));
+    S.w[5].add(T(0.5) * z * f.z);
     S.nterm++;
 }
 
-// Nearest point q on a convex face to p (both in the face owner's frame).
-// Returns false when |signed plane distance| >= rc: then r* >= rc and the
-// term is exactly zero.  Otherwise *r2 = |p - q|^2.  Inside the face (all
-// in-plane edge tests >= 0) q is the projection; else q is the nearest
-// point on the edges whose test fails (the nearest boundary point of a
-// convex polygon lies on such an edge).
 // Work counters of a counting launch (see dem_get_counters).
 enum {
     C_PAIRS = 0,       // ordered pairs within the bounding-sphere range
@@ -194,7 +189,12 @@ __device__ __forceinline__ void bump(PathCount *pc, int k, unsigned int n = 1) {
     if constexpr (COUNT) pc->v[k] += n;
 }
 
-
+// Nearest point q on a convex face to p (both in the face owner's frame).
+// Returns false when |signed plane distance| >= rc: then r* >= rc and the
+// term is exactly zero.  Otherwise *r2 = |p - q|^2.  Inside the face (all
+// in-plane edge tests >= 0) q is the projection; else q is the nearest
+// point on the edges whose test fails (the nearest boundary point of a
+// convex polygon lies on such an edge).
 template <class T, bool COUNT, class R4>
 __device__ __forceinline__ bool face_nearest(const R4 *tab, const int *itab, int face_rec,
                                              int face_int, V3<T> p, T rc, V3<T> *q, T *r2,

@@ -65,17 +65,47 @@ def system(name):
     return _cache[name]
 
 
+DECOMPS = {"thread": 1, "warp": 2}
+
+
+@pytest.mark.parametrize("decomp", list(DECOMPS))
 @pytest.mark.parametrize("precision", PRECISIONS, ids=[PNAMES[p] for p in PRECISIONS])
 @pytest.mark.parametrize("name", list(SYSTEMS))
-def test_forces_parity(dem, name, precision):
+def test_forces_parity(dem, name, precision, decomp):
     s = system(name)
-    errs, ref, _ = compare_forces(dem, s, precision)
+    errs, ref, _ = compare_forces(dem, s, precision, decomp=DECOMPS[decomp])
     assert ref["counts"][0, 2] > 0, "input must have contacts"
-    assert_parity(errs, precision, f"{name}/{PNAMES[precision]}")
+    assert_parity(errs, precision, f"{name}/{PNAMES[precision]}/{decomp}")
 
 
+@pytest.mark.parametrize("name", ["cubes", "mixed3d", "polys2d"])
+def test_decompositions_same_work(dem, name):
+    """Both decompositions run the same culls on the same items: every work
+    counter agrees exactly (FP64 mode, so no test sits at a rounding edge)."""
+    s = system(name)
+    cnt = []
+    for dec in DECOMPS.values():
+        with dem.DEM(s, dem.DEM_FP64, decomp=dec) as d:
+            cnt.append(d.counters()[:13])
+    np.testing.assert_array_equal(cnt[0], cnt[1])
+
+
+def test_autotune_keeps_results(dem):
+    s = system("cubes")
+    with dem.DEM(s, dem.DEM_FP32_COMP) as d:
+        f0, _ = d.forces()
+        dem.dem_autotune(d.ctx)
+        assert d.get_param("decomp") in (1.0, 2.0)
+        assert d.get_param("autotune_ms_2") > 0
+        f1, _ = d.forces()
+        d.step(5, 1e-3, dem.DEM_NVE)
+    scale = np.abs(f0).max()
+    assert np.abs(f1 - f0).max() <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("decomp", list(DECOMPS))
 @pytest.mark.parametrize("precision", PRECISIONS, ids=[PNAMES[p] for p in PRECISIONS])
-def test_batched_replicas(dem, precision):
+def test_batched_replicas(dem, precision, decomp):
     """Replicas of different shapes and sizes in one launch, including
     replicas small enough for the all-pairs search and a one-particle one."""
     reps = [system("cubes"), system("tets").replica(0),
@@ -84,8 +114,8 @@ def test_batched_replicas(dem, precision):
             _periodic_cluster([W.cube(1.0, 0.12)], np.zeros(1, int), [6.0, 6.0, 6.0], 22),
             system("octas")]
     s = W.merge(reps)
-    errs, ref, _ = compare_forces(dem, s, precision)
-    assert_parity(errs, precision, "batched")
+    errs, ref, _ = compare_forces(dem, s, precision, decomp=DECOMPS[decomp])
+    assert_parity(errs, precision, f"batched/{decomp}")
 
 
 @pytest.mark.parametrize("precision", PRECISIONS, ids=[PNAMES[p] for p in PRECISIONS])
