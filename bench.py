@@ -45,18 +45,28 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 # mul / reciprocal = 1, compare = 0), hand-counted from csrc/pair.cu and
 # csrc/pair_common.cuh.  Keys are dem_get_counters indices.
 FLOPS_PER_PATH = {
-    0: 90,   # pair setup: j's rotation matrix (30), M = R_i^T R_j (45), dl = R_i^T d (15)
+    10: 15,  # list entry: separation d0 + delta_j - delta_i (6) + range test (9)
+    0: 123,  # in-range pair: j's rotation matrix (30), M = R_i^T R_j (45),
+             # dl = R_i^T d (15), sigma terms (2), centre-line axis in both
+             # frames (26) and the separating-axis bounds (5)
+    16: 5,   # vertex projection onto the centre line
     3: 23,   # vertex transform into the other frame (18) + reach test (5)
     4: 6,    # face-plane signed distance
     5: 6,    # in-plane edge test of a face
     6: 23,   # point-segment nearest point
     7: 46,   # edge transform (33) + centre (6) + reach test (7)
     8: 17,   # edge bounding-sphere test
+    17: 24,  # carrier-line distance test (cross product, two dots, compare)
     9: 73,   # segment-segment nearest points (Section "Model" parallel rule included)
     11: 7,   # projection onto the face
     2: 35,   # WCA term in i's frame (force, torque, energy, sums)
     12: 15,  # extra rotation of a term evaluated in j's frame
 }
+WORK_COUNTERS = {0: "pairs", 1: "feature_pairs", 2: "terms", 3: "vertex_transforms",
+                 4: "plane_tests", 5: "inplane_tests", 6: "point_segment",
+                 7: "edge_transforms", 8: "edge_sphere_tests", 9: "segment_segment",
+                 10: "list_entries", 11: "inside", 12: "jframe_terms",
+                 15: "active_pairs", 16: "sat_projections", 17: "line_tests"}
 TWO_SUM_EXTRA = 30   # compensated sums: 6 components x (6 - 1) extra flops per term
 
 
@@ -367,6 +377,7 @@ def main():
             "autotune_ms": tune,
             "kernel_ms": pair_ms, "kernel_share_of_step": pair_ms / (t_max / a.steps),
             "flops_per_launch": flops, "feature_pairs_per_launch": pair_fpe,
+            "work_counters": {name: int(counts[k]) for k, name in WORK_COUNTERS.items()},
             "feature_pairs_per_s": pair_fpe / (pair_ms / 1e3),
             "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max clock",
         },

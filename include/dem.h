@@ -78,11 +78,12 @@ extern "C" {
 /* ---- pair-kernel decompositions (parameter "decomp") ---- */
 #define DEM_DECOMP_AUTO 0    /* chosen by dem_autotune (default: THREAD)        */
 #define DEM_DECOMP_THREAD 1  /* one thread walks all neighbours of particle i   */
-#define DEM_DECOMP_WARP 2    /* one warp per particle i; lanes split the
-                                (neighbour, feature) work; warp-shuffle sums   */
-#define DEM_DECOMP_TILED 3   /* one warp per ordered pair (i, j); lanes take i's
-                                features as in Section "Algorithm"; a segmented
-                                sum over i's neighbours                        */
+#define DEM_DECOMP_WARP 2    /* one warp per 32 particles: the lanes scan their
+                                list entries, queue the pairs that pass the
+                                culls, and evaluate 32 queued pairs at a time,
+                                one per lane; each particle's lane sums its
+                                pairs in queue order                           */
+#define DEM_DECOMP_TILED 3   /* reserved                                        */
 
 typedef struct dem_ctx dem_ctx;   /* opaque; owned by the library */
 
@@ -102,7 +103,9 @@ typedef struct dem_ctx dem_ctx;   /* opaque; owned by the library */
  *   mass           > 0
  *   inertia        3D: 3 principal moments, 2D: 1 (I_z); NULL derives them
  *                  for a uniform-density inner solid of the given mass.
- * The inner shape must be convex.  3D edges are derived from the faces. */
+ * The inner shape must be convex.  3D edges are derived from the faces.  A
+ * shape has at most 32 vertices, 32 edges, 32 faces and 12 vertices per
+ * face. */
 typedef struct dem_shape {
     int dim;
     int n_verts;
@@ -238,10 +241,13 @@ int dem_autotune(dem_ctx *ctx);
  *  [11] vertex-face projections inside the face
  *  [12] terms evaluated in j's frame (vertex(i)-face(j), vertex(i)-edge(j))
  *  [13] neighbour-list rebuilds so far  [14] kernel launches so far
- *  [15] 0
- * Entries [0]-[12] come from a separate instrumented evaluation at the
- * current state (the evaluation used by dem_step is not instrumented). */
-#define DEM_N_COUNTERS 16
+ *  [15] pairs that pass the separating-axis test along the centre line
+ *  [16] vertex projections of that test  [17] carrier-line distance tests
+ *  [18], [19] 0
+ * Entries other than [13] and [14] come from a separate instrumented
+ * evaluation at the current state (the evaluation used by dem_step is not
+ * instrumented). */
+#define DEM_N_COUNTERS 20
 int dem_get_counters(dem_ctx *ctx, long long *counts);
 
 /* Use this CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream()).

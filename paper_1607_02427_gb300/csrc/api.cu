@@ -142,7 +142,8 @@ static int preprocess_shape(const dem_shape &s, HostGeom *g, HostShape *h, std::
                     if (std::find(g->edges.begin(), g->edges.end(), e) == g->edges.end())
                         g->edges.push_back(e);
                 }
-            if ((int)g->edges.size() > 3 * MAX_VERTS) return fail("too many edges");
+            if ((int)g->edges.size() > MAX_EDGES) return fail("more than %d edges", MAX_EDGES);
+            if ((int)g->faces.size() > MAX_FACES) return fail("more than %d faces", MAX_FACES);
             // faces planar, convex, counter-clockwise seen from outside
             D3 vc = {0, 0, 0};
             for (int k = 0; k < nv; ++k) vc = add(vc, d3(&g->v[3 * k]));
@@ -241,30 +242,14 @@ bool same_geom(const HostGeom &a, const HostGeom &b) {
 // The message dem_last_error(NULL) returns, for entry points without a context.
 void dem::set_global_error(const std::string &msg) { g_create_error = msg; }
 
-// Host copies of the geometry tables (same layout as a context's), for the
-// entry point that evaluates forces without a context (noalloc.cu).
-int dem::make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t,
-                          std::string *err) {
-    std::vector<HostGeom> geoms;
-    std::vector<HostShape> hs;
-    for (int s = 0; s < n_shapes; ++s) {
-        HostGeom g;
-        HostShape h;
-        int rc = preprocess_shape(shapes[s], &g, &h, err);
-        if (rc) return rc;
-        if (shapes[s].dim != shapes[0].dim) { *err = "all shapes must have the same dim"; return DEM_ERR_ARG; }
-        int gid = -1;
-        for (size_t k = 0; k < geoms.size(); ++k)
-            if (same_geom(geoms[k], g)) { gid = (int)k; break; }
-        if (gid < 0) {
-            if ((int)geoms.size() >= MAX_GEOMS) { *err = "too many distinct geometries"; return DEM_ERR_ARG; }
-            gid = (int)geoms.size();
-            geoms.push_back(g);
-        }
-        h.geom = gid;
-        hs.push_back(h);
-    }
-    t->dim = shapes[0].dim;
+namespace {
+
+// Geometry tables in the layout the pair kernels read (see Geom): FP64
+// records and their FP32 copies, the int table (face ranges, and the vertex
+// membership masks of every edge and face used by the separating-axis
+// culls), and the per-shape records.
+void build_tables(const std::vector<HostGeom> &geoms, const std::vector<HostShape> &hs,
+                  HostTables *t) {
     t->td.clear(); t->itab.clear(); t->geoms.clear(); t->shapes.clear();
     t->Rmax = 0; t->rnd_max = 0;
     for (auto &g : geoms) {
@@ -272,6 +257,7 @@ int dem::make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t,
         G.nv = (int)(g.v.size() / 3);
         G.ne = (int)g.edges.size();
         G.nf = (int)g.faces.size();
+        // conservative (slightly enlarged) radii for the exact culls
         G.R = (float)(g.R * (1.0 + 1e-6) + 1e-7);
         t->Rmax = std::max(t->Rmax, (double)G.R);
         G.v_off = (int)t->td.size();
@@ -316,6 +302,15 @@ int dem::make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t,
             }
         }
         G.nfe = nfe;
+        // vertex membership masks: bit k set when vertex k bounds the edge/face
+        G.em_off = (int)t->itab.size();
+        for (auto &e : g.edges) t->itab.push_back((int)((1u << e.first) | (1u << e.second)));
+        G.fm_off = (int)t->itab.size();
+        for (auto &loop : g.faces) {
+            unsigned m = 0;
+            for (int v : loop) m |= 1u << v;
+            t->itab.push_back((int)m);
+        }
         t->geoms.push_back(G);
     }
     if (t->itab.empty()) { t->itab.push_back(0); t->itab.push_back(0); }
@@ -334,6 +329,35 @@ int dem::make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t,
         t->rnd_max = std::max(t->rnd_max, h.rounding);
         t->shapes.push_back(sd);
     }
+}
+
+}  // namespace
+
+// Host copies of the geometry tables (same layout as a context's), for the
+// entry point that evaluates forces without a context (noalloc.cu).
+int dem::make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t,
+                          std::string *err) {
+    std::vector<HostGeom> geoms;
+    std::vector<HostShape> hs;
+    for (int s = 0; s < n_shapes; ++s) {
+        HostGeom g;
+        HostShape h;
+        int rc = preprocess_shape(shapes[s], &g, &h, err);
+        if (rc) return rc;
+        if (shapes[s].dim != shapes[0].dim) { *err = "all shapes must have the same dim"; return DEM_ERR_ARG; }
+        int gid = -1;
+        for (size_t k = 0; k < geoms.size(); ++k)
+            if (same_geom(geoms[k], g)) { gid = (int)k; break; }
+        if (gid < 0) {
+            if ((int)geoms.size() >= MAX_GEOMS) { *err = "too many distinct geometries"; return DEM_ERR_ARG; }
+            gid = (int)geoms.size();
+            geoms.push_back(g);
+        }
+        h.geom = gid;
+        hs.push_back(h);
+    }
+    t->dim = shapes[0].dim;
+    build_tables(geoms, hs, t);
     return DEM_OK;
 }
 
@@ -440,88 +464,25 @@ void free_graph(dem_ctx *ctx) {
 
 // Upload geometry tables (FP64 and FP32 copies) and per-shape records.
 int upload_tables(dem_ctx *ctx) {
-    std::vector<double4_32a> tab;
-    std::vector<int> itab;
-    std::vector<Geom> gd;
-    for (auto &g : ctx->geoms) {
-        Geom G = {};
-        G.nv = (int)(g.v.size() / 3);
-        G.ne = (int)g.edges.size();
-        G.nf = (int)g.faces.size();
-        // conservative (slightly enlarged) radii for the exact culls
-        G.R = (float)(g.R * (1.0 + 1e-6) + 1e-7);
-        G.v_off = (int)tab.size();
-        for (int k = 0; k < G.nv; ++k) tab.push_back(make_double4_32a(g.v[3 * k], g.v[3 * k + 1], g.v[3 * k + 2], 0.0));
-        G.e_off = (int)tab.size();
-        for (auto &e : g.edges) {
-            D3 a = d3(&g.v[3 * e.first]), b = d3(&g.v[3 * e.second]);
-            D3 d = sub(b, a);
-            double ln = norm(d);
-            tab.push_back(make_double4_32a(a.x, a.y, a.z, 0.5 * ln * (1.0 + 1e-5) + 1e-6));
-            tab.push_back(make_double4_32a(d.x, d.y, d.z, 1.0 / (ln * ln)));
-        }
-        G.f_off = (int)tab.size();
-        std::vector<D3> normals;
-        for (auto &loop : g.faces) {
-            size_t m = loop.size();
-            D3 n = {0, 0, 0};
-            for (size_t k = 0; k < m; ++k)
-                n = add(n, crossp(d3(&g.v[3 * loop[k]]), d3(&g.v[3 * loop[(k + 1) % m]])));
-            n = scl(n, 1.0 / norm(n));
-            normals.push_back(n);
-            tab.push_back(make_double4_32a(n.x, n.y, n.z, dotp(n, d3(&g.v[3 * loop[0]]))));
-        }
-        G.fe_off = (int)tab.size();
-        G.fi_off = (int)itab.size();
-        int nfe = 0;
-        for (size_t f = 0; f < g.faces.size(); ++f) {
-            auto &loop = g.faces[f];
-            size_t m = loop.size();
-            itab.push_back((int)tab.size());
-            itab.push_back((int)m);
-            for (size_t k = 0; k < m; ++k) {
-                D3 a = d3(&g.v[3 * loop[k]]), b = d3(&g.v[3 * loop[(k + 1) % m]]);
-                D3 e = sub(b, a);
-                D3 mm = crossp(normals[f], e);
-                mm = scl(mm, 1.0 / norm(mm));
-                tab.push_back(make_double4_32a(a.x, a.y, a.z, 0.0));
-                tab.push_back(make_double4_32a(e.x, e.y, e.z, 1.0 / dotp(e, e)));
-                tab.push_back(make_double4_32a(mm.x, mm.y, mm.z, dotp(mm, a)));
-                ++nfe;
-            }
-        }
-        G.nfe = nfe;
-        gd.push_back(G);
-    }
-    if (itab.empty()) { itab.push_back(0); itab.push_back(0); }
-    ctx->table_len = (int)tab.size();
-    ctx->itable_len = (int)itab.size();
-    ctx->n_geoms = (int)gd.size();
-    CK(dalloc(&ctx->d_geoms, gd.size()));
-    CK(cudaMemcpy(ctx->d_geoms, gd.data(), sizeof(Geom) * gd.size(), cudaMemcpyHostToDevice));
-    CK(dalloc(&ctx->d_itable, itab.size()));
-    CK(cudaMemcpy(ctx->d_itable, itab.data(), sizeof(int) * itab.size(), cudaMemcpyHostToDevice));
+    HostTables t;
+    t.dim = ctx->dim;
+    build_tables(ctx->geoms, ctx->shapes, &t);
+    ctx->table_len = (int)t.td.size();
+    ctx->itable_len = (int)t.itab.size();
+    ctx->n_geoms = (int)t.geoms.size();
+    CK(dalloc(&ctx->d_geoms, t.geoms.size()));
+    CK(cudaMemcpy(ctx->d_geoms, t.geoms.data(), sizeof(Geom) * t.geoms.size(), cudaMemcpyHostToDevice));
+    CK(dalloc(&ctx->d_itable, t.itab.size()));
+    CK(cudaMemcpy(ctx->d_itable, t.itab.data(), sizeof(int) * t.itab.size(), cudaMemcpyHostToDevice));
     if (ctx->precision == DEM_FP64) {
-        CK(dalloc((double4_32a **)&ctx->d_table, tab.size()));
-        CK(cudaMemcpy(ctx->d_table, tab.data(), sizeof(double4_32a) * tab.size(), cudaMemcpyHostToDevice));
+        CK(dalloc((double4_32a **)&ctx->d_table, t.td.size()));
+        CK(cudaMemcpy(ctx->d_table, t.td.data(), sizeof(double4_32a) * t.td.size(), cudaMemcpyHostToDevice));
     } else {
-        std::vector<float4> tf(tab.size());
-        for (size_t k = 0; k < tab.size(); ++k)
-            tf[k] = make_float4((float)tab[k].x, (float)tab[k].y, (float)tab[k].z, (float)tab[k].w);
-        CK(dalloc((float4 **)&ctx->d_table, tf.size()));
-        CK(cudaMemcpy(ctx->d_table, tf.data(), sizeof(float4) * tf.size(), cudaMemcpyHostToDevice));
+        CK(dalloc((float4 **)&ctx->d_table, t.tf.size()));
+        CK(cudaMemcpy(ctx->d_table, t.tf.data(), sizeof(float4) * t.tf.size(), cudaMemcpyHostToDevice));
     }
-    std::vector<ShapeDev> sd(ctx->shapes.size());
-    for (size_t s = 0; s < sd.size(); ++s) {
-        sd[s].geom = ctx->shapes[s].geom;
-        sd[s].R = gd[ctx->shapes[s].geom].R;
-        sd[s].rounding = ctx->shapes[s].rounding;
-        sd[s].rounding_f = (float)ctx->shapes[s].rounding;
-        sd[s].mass = ctx->shapes[s].mass;
-        for (int k = 0; k < 3; ++k) sd[s].inertia[k] = ctx->shapes[s].inertia[k];
-    }
-    CK(dalloc(&ctx->d_shapes, sd.size()));
-    CK(cudaMemcpy(ctx->d_shapes, sd.data(), sizeof(ShapeDev) * sd.size(), cudaMemcpyHostToDevice));
+    CK(dalloc(&ctx->d_shapes, t.shapes.size()));
+    CK(cudaMemcpy(ctx->d_shapes, t.shapes.data(), sizeof(ShapeDev) * t.shapes.size(), cudaMemcpyHostToDevice));
     return DEM_OK;
 }
 
@@ -1334,7 +1295,6 @@ int dem_get_counters(dem_ctx *ctx, long long *counts) {
     for (int k = 0; k < DEM_N_COUNTERS; ++k) counts[k] = (long long)h[k];
     counts[13] = st.rebuilds;
     counts[14] = ctx->launches;
-    counts[15] = 0;
     return DEM_OK;
 }
 

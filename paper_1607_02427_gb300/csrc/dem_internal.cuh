@@ -30,7 +30,9 @@
 
 namespace dem {
 
-constexpr int MAX_VERTS = 32;       // vertices of one shape on the device path
+constexpr int MAX_VERTS = 32;       // vertices of one shape (bit masks of 32)
+constexpr int MAX_EDGES = 32;       // edges of one shape (bit masks of 32)
+constexpr int MAX_FACES = 32;       // faces of one shape (bit masks of 32)
 constexpr int MAX_FACE_VERTS = 12;  // vertices of one face
 constexpr int MAX_GEOMS = 64;       // distinct geometries per context
 constexpr int THREADS = 128;
@@ -42,12 +44,14 @@ constexpr int THREADS = 128;
 //   fedges: 3 nfe records per face edge: a = (start, 0),
 //           e = (vector, 1/|e|^2), m = (inward in-plane normal, m . a)
 //   face k uses fedges [fe_begin[k], fe_begin[k] + fe_count[k]) (ints table)
+//   int table also: a 32-bit mask of the vertices of each edge and each face
 struct Geom {
     int nv, ne, nf, nfe;
     int v_off, e_off, f_off, fe_off;
     int fi_off;          // offset of this geometry's faces in the int table
     float R;             // circumradius of the inner shape
-    int pad[2];
+    int em_off;          // int table: vertex-membership mask of each edge
+    int fm_off;          // int table: vertex-membership mask of each face
 };
 
 struct ShapeDev {

@@ -6,11 +6,11 @@
 // Work decomposition (owner computes over a full neighbour list; only
 // particle i's sums are written, so no atomics and a fixed summation order):
 //   THREAD  one thread per particle i walks its neighbours j.
-//   WARP    one warp per particle i; the pair setups of 32 list entries are
-//           made by 32 lanes, then the (neighbour, vertex) and (neighbour,
-//           edge) work items and, after the cheap culls, the surviving
-//           (vertex, face) and (edge, edge) tests are spread evenly over the
-//           lanes with warp scans; shuffle trees combine the lane sums.
+//   WARP    one warp per 32 particles, one lane per active pair: the lanes
+//           scan the list entries of the 32 particles, the pairs that pass
+//           the culls below are queued in ballot order, 32 queued pairs are
+//           evaluated at a time (one per lane), and each particle's lane
+//           adds its pairs' partial sums in queue order.
 //
 // Separation.  FP32 modes: x_j - x_i = d0 + delta_j - delta_i, where d0 is
 // the FP32 minimum-image separation stored in the list entry when the list
@@ -19,12 +19,21 @@
 // on this part).  FP64 mode: x_j - x_i from the FP64 positions, minimum image
 // by comparison with half the box.
 //
-// Exact culls (each skips only terms that are zero because r* >= r_cut):
+// Culls (each skips only terms that are zero because every point pair of
+// the two features is at least r_cut apart):
 //   pair:    |x_ij| >= R_i + R_j + r_cut         (all features lie within R)
+//   pair:    separating axis along u = x_ij / |x_ij|: |x_ij| - h_i - h_j >=
+//            r_cut, with h_i, h_j the supports of the inner shapes towards
+//            each other (projections of the vertices on u)
+//   feature: a feature of i whose largest projection on u is at most
+//            |x_ij| - h_j - r_cut cannot reach j (likewise for j); vertex
+//            masks come from the projections, edge and face masks from the
+//            vertex-membership masks of the geometry table
 //   vertex:  |p - x_owner| >= R_owner + r_cut    (p cannot reach any face)
 //   edge:    |c_e - x_i| >= R_i + h_e + r_cut    (the edge cannot reach i)
 //   face:    |signed plane distance| >= r_cut
 //   edges:   |c_1 - c_2| >= h_1 + h_2 + r_cut    (edge bounding spheres)
+//   edges:   distance of the two carrier lines >= r_cut
 #include <type_traits>
 
 #include "pair_common.cuh"
@@ -58,6 +67,7 @@ template <class T> struct Owner {
     double4_32a x;       // FP64 mode
     T R, rnd;
     T sig_all;           // the one sigma of all pairs, or 0 (sigma_ij = r_i + r_j)
+    int geom;
     const Rep *rp;
 };
 
@@ -119,6 +129,7 @@ __device__ __forceinline__ Owner<T> make_owner(const PairArgs &a, int i, const S
     Owner<T> o;
     o.rp = &a.reps[a.rep[i]];
     o.R = (T)gi.R;
+    o.geom = shi.geom;
     o.sig_all = a.sigma > 0.0 ? (T)a.sigma : T(0);
     if constexpr (std::is_same<T, float>::value) {
         o.delta = a.delta[i];
@@ -130,20 +141,284 @@ __device__ __forceinline__ Owner<T> make_owner(const PairArgs &a, int i, const S
     return o;
 }
 
-// Totals of particle i: force rotated to the world frame, torque in the
-// body frame, energy, virial rotated to the world frame (R W R^T), all in T;
-// out = {F(3), tau(3), U, W(6)}.
-template <class T, bool COMP>
-__device__ __forceinline__ void totals(const Sums<T, COMP> &S, const M33<T> &R, T out[13]) {
-    T tot[13];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        tot[k] = S.f[k].s + S.f[k].comp();
-        tot[3 + k] = S.t[k].s + S.t[k].comp();
+template <class T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+
+// ---------------------------------------------------------------------------
+// Pair setup: separating axis along the centre line and the feature masks
+// ---------------------------------------------------------------------------
+template <class T> struct PairWork {
+    M33<T> M;            // R_i^T R_j
+    V3<T> dl;            // x_j - x_i in i's frame
+    T rc, sig2;
+    int gj;
+    unsigned vim, vjm;   // vertices of i / of j that can reach the other
+    unsigned eim, ejm;   // edges
+    unsigned fim, fjm;   // faces
+};
+
+__device__ __forceinline__ unsigned low_bits(int n) { return n >= 32 ? FULL : ((1u << n) - 1u); }
+
+// Mask of the features (edges or faces) with a vertex in vmask.
+__device__ __forceinline__ unsigned feature_mask(const int *mtab, int n, unsigned vmask) {
+    unsigned m = 0;
+    for (int k = 0; k < n; ++k)
+        if ((unsigned)mtab[k] & vmask) m |= 1u << k;
+    return m;
+}
+
+// Returns false when the pair is separated along its centre line by at least
+// r_cut (all of its terms are zero).
+template <class T, bool COUNT>
+__device__ __forceinline__ bool pair_setup(const typename R4T<T>::type *tab, const int *itab,
+                                           const Geom &gi, const Geom &gj, PairWork<T> *w,
+                                           PathCount *pc) {
+    w->vim = low_bits(gi.nv);
+    w->vjm = low_bits(gj.nv);
+    w->eim = low_bits(gi.ne);
+    w->ejm = low_bits(gj.ne);
+    w->fim = low_bits(gi.nf);
+    w->fjm = low_bits(gj.nf);
+    const T d2 = dot(w->dl, w->dl);
+    if (gi.nv == 1 && gj.nv == 1) return true;           // sphere limit: one term
+    if (!(d2 > T(0))) return true;                         // coincident centres
+    const T inv = rsqrt_t(d2);
+    const T dn = d2 * inv;                                 // |x_ij|
+    const V3<T> u = w->dl * inv;                           // i's frame
+    const V3<T> uj = mul_t(w->M, u);                       // the same axis in j's frame
+    // support of j towards i: max over j's vertices of -(v . uj)
+    T hj = T(-3.0e38);
+    for (int k = 0; k < gj.nv; ++k) hj = fmax(hj, -dot(xyz<T>(tab[gj.v_off + k]), uj));
+    // support of i towards j, and i's vertices that reach j's slab
+    const T lo_i = dn - hj - w->rc;
+    T hi = T(-3.0e38);
+    unsigned vim = 0;
+    for (int k = 0; k < gi.nv; ++k) {
+        const T p = dot(xyz<T>(tab[gi.v_off + k]), u);
+        hi = fmax(hi, p);
+        if (p > lo_i) vim |= 1u << k;
     }
-    tot[6] = S.u.s + S.u.comp();
+    bump<COUNT>(pc, C_PROJ, (unsigned)(gi.nv + 2 * gj.nv));
+    if (!(dn - hi - hj < w->rc)) return false;
+    const T hi_j = hi + w->rc - dn;                        // j's vertices: v . uj < hi_j
+    unsigned vjm = 0;
+    for (int k = 0; k < gj.nv; ++k)
+        if (dot(xyz<T>(tab[gj.v_off + k]), uj) < hi_j) vjm |= 1u << k;
+    w->vim = vim;
+    w->vjm = vjm;
+    w->eim = feature_mask(itab + gi.em_off, gi.ne, vim);
+    w->ejm = feature_mask(itab + gj.em_off, gj.ne, vjm);
+    w->fim = feature_mask(itab + gi.fm_off, gi.nf, vim);
+    w->fjm = feature_mask(itab + gj.fm_off, gj.nf, vjm);
+    return true;
+}
+
+// The 13 values of one term: force f and torque pi x f in i's frame, half
+// the energy, the body-frame virial 1/2 sym((-dl) (x) f).
+template <class T>
+__device__ __forceinline__ void term_values(V3<T> pi, V3<T> f, V3<T> dl, T U, T *v) {
+    const V3<T> tq = cross(pi, f);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z;
+    v[3] = tq.x; v[4] = tq.y; v[5] = tq.z;
+    v[6] = T(0.5) * U;
+    const T x = -dl.x, y = -dl.y, z = -dl.z;
+    v[7] = T(0.5) * x * f.x;
+    v[8] = T(0.25) * (x * f.y + y * f.x);
+    v[9] = T(0.25) * (x * f.z + z * f.x);
+    v[10] = T(0.5) * y * f.y;
+    v[11] = T(0.25) * (y * f.z + z * f.y);
+    v[12] = T(0.5) * z * f.z;
+}
+
+// Sinks of the terms: the particle's compensated sums, or a pair's partial.
+template <class T, bool COMP> struct SumSink {
+    Acc<T, COMP> v[13];
+    __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) tot[7 + k] = S.w[k].s + S.w[k].comp();
+        for (int k = 0; k < 13; ++k) v[k].zero();
+    }
+    __device__ __forceinline__ void add(const T *x) {
+#pragma unroll
+        for (int k = 0; k < 13; ++k) v[k].add(x[k]);
+    }
+    __device__ __forceinline__ T total(int k) const { return v[k].s + v[k].comp(); }
+};
+template <class T> struct PartSink {
+    T v[13];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < 13; ++k) v[k] = T(0);
+    }
+    __device__ __forceinline__ void add(const T *x) {
+#pragma unroll
+        for (int k = 0; k < 13; ++k) v[k] += x[k];
+    }
+};
+
+// All terms of an active pair (Eq. DEM / Eq. DEM_2D restricted to the
+// masked features, which carry every non-zero term), in i's frame.
+template <class T, int DIM, bool COUNT, class Sink>
+__device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, const int *itab,
+                                          const Geom &gi, const Geom &gj, const PairWork<T> &w,
+                                          T eps, T par_eps, Sink &sink, PathCount *pc) {
+    using R4 = typename R4T<T>::type;
+    const T rc = w.rc, rc2 = rc * rc;
+    const V3<T> dl = w.dl;
+    T U, wf, tv[13];
+    if (gi.nv == 1 && gj.nv == 1) {             // sphere / disk limit: central WCA
+        const V3<T> pi = xyz<T>(tab[gi.v_off]);
+        const V3<T> rv = pi - (dl + mul(w.M, xyz<T>(tab[gj.v_off])));
+        const T r2 = dot(rv, rv);
+        if (r2 < rc2) {
+            wf = wca_factor(r2, w.sig2, eps, &U);
+            term_values(pi, rv * wf, dl, U, tv);
+            sink.add(tv);
+            bump<COUNT>(pc, C_TERMS);
+        }
+        return;
+    }
+    const T reach_i = T(gi.R) + rc, reach_j = T(gj.R) + rc;
+    // vertex of j against the faces (2D: edges) of i, in i's frame
+    for (unsigned mb = w.vjm; mb; mb &= mb - 1u) {
+        const int b = __ffs(mb) - 1;
+        const V3<T> p = dl + mul(w.M, xyz<T>(tab[gj.v_off + b]));
+        bump<COUNT>(pc, C_VTX);
+        if (!(dot(p, p) < reach_i * reach_i)) continue;
+        if constexpr (DIM == 3) {
+            for (unsigned mf = w.fim; mf; mf &= mf - 1u) {
+                const int f = __ffs(mf) - 1;
+                V3<T> q;
+                T r2;
+                if (!face_nearest<T, COUNT>(tab, itab, gi.f_off + f, gi.fi_off + 2 * f, p, rc, &q, &r2, pc))
+                    continue;
+                if (r2 < rc2) {
+                    wf = wca_factor(r2, w.sig2, eps, &U);
+                    term_values(q, (q - p) * wf, dl, U, tv);
+                    sink.add(tv);
+                    bump<COUNT>(pc, C_TERMS);
+                }
+            }
+        } else {
+            for (unsigned me = w.eim; me; me &= me - 1u) {
+                const int e = __ffs(me) - 1;
+                const R4 ea = tab[gi.e_off + 2 * e], ed = tab[gi.e_off + 2 * e + 1];
+                const V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
+                const V3<T> c = A + D * T(0.5) - p;
+                const T lim = ea.w + rc;
+                bump<COUNT>(pc, C_SPHERE);
+                if (!(dot(c, c) < lim * lim)) continue;
+                bump<COUNT>(pc, C_PTSEG);
+                const V3<T> q = A + D * clamp01(dot(p - A, D) * ed.w);
+                const V3<T> rv = q - p;
+                const T r2 = dot(rv, rv);
+                if (r2 < rc2) {
+                    wf = wca_factor(r2, w.sig2, eps, &U);
+                    term_values(q, rv * wf, dl, U, tv);
+                    sink.add(tv);
+                    bump<COUNT>(pc, C_TERMS);
+                }
+            }
+        }
+    }
+    // vertex of i against the faces (2D: edges) of j, in j's frame
+    for (unsigned ma = w.vim; ma; ma &= ma - 1u) {
+        const int ai = __ffs(ma) - 1;
+        const V3<T> u = xyz<T>(tab[gi.v_off + ai]);
+        const V3<T> p = mul_t(w.M, u - dl);
+        bump<COUNT>(pc, C_VTX);
+        if (!(dot(p, p) < reach_j * reach_j)) continue;
+        if constexpr (DIM == 3) {
+            for (unsigned mf = w.fjm; mf; mf &= mf - 1u) {
+                const int f = __ffs(mf) - 1;
+                V3<T> q;
+                T r2;
+                if (!face_nearest<T, COUNT>(tab, itab, gj.f_off + f, gj.fi_off + 2 * f, p, rc, &q, &r2, pc))
+                    continue;
+                if (r2 < rc2) {
+                    wf = wca_factor(r2, w.sig2, eps, &U);
+                    term_values(u, mul(w.M, (p - q) * wf), dl, U, tv);
+                    sink.add(tv);
+                    bump<COUNT>(pc, C_TERMS);
+                    bump<COUNT>(pc, C_JTERMS);
+                }
+            }
+        } else {
+            for (unsigned me = w.ejm; me; me &= me - 1u) {
+                const int e = __ffs(me) - 1;
+                const R4 ea = tab[gj.e_off + 2 * e], ed = tab[gj.e_off + 2 * e + 1];
+                const V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
+                const V3<T> c = A + D * T(0.5) - p;
+                const T lim = ea.w + rc;
+                bump<COUNT>(pc, C_SPHERE);
+                if (!(dot(c, c) < lim * lim)) continue;
+                bump<COUNT>(pc, C_PTSEG);
+                const V3<T> q = A + D * clamp01(dot(p - A, D) * ed.w);
+                const V3<T> rv = p - q;
+                const T r2 = dot(rv, rv);
+                if (r2 < rc2) {
+                    wf = wca_factor(r2, w.sig2, eps, &U);
+                    term_values(u, mul(w.M, rv * wf), dl, U, tv);
+                    sink.add(tv);
+                    bump<COUNT>(pc, C_TERMS);
+                    bump<COUNT>(pc, C_JTERMS);
+                }
+            }
+        }
+    }
+    if constexpr (DIM == 3) {
+        // edges of j against the edges of i, in i's frame
+        const unsigned eim = w.eim;
+        for (unsigned mb = eim ? w.ejm : 0u; mb; mb &= mb - 1u) {
+            const int eb = __ffs(mb) - 1;
+            const R4 ba = tab[gj.e_off + 2 * eb], bd = tab[gj.e_off + 2 * eb + 1];
+            const V3<T> A2 = dl + mul(w.M, xyz<T>(ba));
+            const V3<T> D2 = mul(w.M, xyz<T>(bd));
+            const V3<T> C2 = A2 + D2 * T(0.5);
+            const T reach = reach_i + ba.w;
+            bump<COUNT>(pc, C_EDGE);
+            if (!(dot(C2, C2) < reach * reach)) continue;
+            for (unsigned ma = eim; ma; ma &= ma - 1u) {
+                const int ea = __ffs(ma) - 1;
+                const R4 aa = tab[gi.e_off + 2 * ea], ad = tab[gi.e_off + 2 * ea + 1];
+                const V3<T> A1 = xyz<T>(aa), D1 = xyz<T>(ad);
+                const V3<T> dc = A1 + D1 * T(0.5) - C2;
+                const T lim = aa.w + ba.w + rc;
+                bump<COUNT>(pc, C_SPHERE);
+                if (!(dot(dc, dc) < lim * lim)) continue;
+                // carrier lines farther apart than r_cut: the segments are too
+                const V3<T> nrm = cross(D1, D2);
+                const T n2 = dot(nrm, nrm);
+                const T sep = dot(A2 - A1, nrm);
+                bump<COUNT>(pc, C_LINE);
+                if (sep * sep >= rc2 * n2 && n2 > par_eps * dot(D1, D1) * dot(D2, D2)) continue;
+                bump<COUNT>(pc, C_SEGSEG);
+                V3<T> P1, P2;
+                segment_nearest<T>(A1, D1, ad.w, A2, D2, bd.w, par_eps, &P1, &P2);
+                const V3<T> rv = P1 - P2;
+                const T r2 = dot(rv, rv);
+                if (r2 < rc2) {
+                    wf = wca_factor(r2, w.sig2, eps, &U);
+                    term_values(P1, rv * wf, dl, U, tv);
+                    sink.add(tv);
+                    bump<COUNT>(pc, C_TERMS);
+                }
+            }
+        }
+    }
+}
+
+// Number of feature pairs Eq. DEM / Eq. DEM_2D assigns to a pair.
+__device__ __forceinline__ unsigned defined_feature_pairs(int dim, const Geom &gi, const Geom &gj) {
+    if (gi.nv == 1 && gj.nv == 1) return 1u;
+    if (dim == 2) return (unsigned)(gi.nv * gj.ne + gj.nv * gi.ne);
+    return (unsigned)(gi.ne * gj.ne + gi.nv * gj.nf + gj.nv * gi.nf);
+}
+
+// World-frame outputs of particle i from its body-frame totals:
+// out = {F (rotated), tau (body), U, W (R W R^T)}.
+template <class T>
+__device__ __forceinline__ void world_outputs(const T *tot, const M33<T> &R, T *out) {
     const V3<T> fw = mul(R, v3<T>(tot[0], tot[1], tot[2]));
     out[0] = fw.x; out[1] = fw.y; out[2] = fw.z;
     out[3] = tot[3]; out[4] = tot[4]; out[5] = tot[5];
@@ -155,159 +430,39 @@ __device__ __forceinline__ void totals(const Sums<T, COMP> &S, const M33<T> &R, 
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             RB[r][c] = R.m[r][0] * B[0][c] + R.m[r][1] * B[1][c] + R.m[r][2] * B[2][c];
-    const int idx[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    out[7] = RB[0][0] * R.m[0][0] + RB[0][1] * R.m[0][1] + RB[0][2] * R.m[0][2];
+    out[8] = RB[0][0] * R.m[1][0] + RB[0][1] * R.m[1][1] + RB[0][2] * R.m[1][2];
+    out[9] = RB[0][0] * R.m[2][0] + RB[0][1] * R.m[2][1] + RB[0][2] * R.m[2][2];
+    out[10] = RB[1][0] * R.m[1][0] + RB[1][1] * R.m[1][1] + RB[1][2] * R.m[1][2];
+    out[11] = RB[1][0] * R.m[2][0] + RB[1][1] * R.m[2][1] + RB[1][2] * R.m[2][2];
+    out[12] = RB[2][0] * R.m[2][0] + RB[2][1] * R.m[2][1] + RB[2][2] * R.m[2][2];
+}
+
+__device__ __forceinline__ void store_outputs(const PairArgs &a, int i, const double *v) {
+    double *f = reinterpret_cast<double *>(a.force + i);
+    double *t = reinterpret_cast<double *>(a.torque + i);
+    f[0] = v[0]; f[1] = v[1]; f[2] = v[2];
+    t[0] = v[3]; t[1] = v[4]; t[2] = v[5];
+    a.energy[i] = v[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const int r = idx[k][0], c = idx[k][1];
-        out[7 + k] = RB[r][0] * R.m[c][0] + RB[r][1] * R.m[c][1] + RB[r][2] * R.m[c][2];
-    }
+    for (int k = 0; k < 6; ++k) a.virial[6 * (size_t)i + k] = v[7 + k];
+    double chk = 0.0;
+#pragma unroll
+    for (int k = 0; k < 13; ++k) chk += v[k];
+    if (!isfinite(chk)) atomicExch(&a.status->nonfinite, 1);
 }
 
-// Store value k of the 13 totals of particle i.
-__device__ __forceinline__ void store_value(const PairArgs &a, int i, int k, double v) {
-    if (k < 3) reinterpret_cast<double *>(a.force + i)[k] = v;
-    else if (k < 6) reinterpret_cast<double *>(a.torque + i)[k - 3] = v;
-    else if (k == 6) a.energy[i] = v;
-    else a.virial[6 * (size_t)i + (k - 7)] = v;
-    if (!isfinite(v)) atomicExch(&a.status->nonfinite, 1);
-}
-
-// All terms of the ordered pair (i, j) (i's geometry gi, j's gj), evaluated
-// in i's frame, accumulated into S.  Returns the number of feature pairs
-// the definition (Eq. DEM / Eq. DEM_2D) assigns to the pair.
-template <class T, bool COMP, int DIM, bool COUNT>
-__device__ __forceinline__ unsigned int pair_terms(const typename R4T<T>::type *tab,
-                                                   const int *itab, const Geom &gi,
-                                                   const Geom &gj, const M33<T> &M, V3<T> dl,
-                                                   T rc, T sig2, T eps, T par_eps,
-                                                   Sums<T, COMP> &S, PathCount *pc) {
-    using R4 = typename R4T<T>::type;
-    const T rc2 = rc * rc;
-    T U, wf;
-    if (gi.nv == 1 && gj.nv == 1) {             // sphere / disk limit: central WCA
-        V3<T> pi = xyz<T>(tab[gi.v_off]);
-        V3<T> pj = dl + mul(M, xyz<T>(tab[gj.v_off]));
-        V3<T> rv = pi - pj;
-        T r2 = dot(rv, rv);
-        if (r2 < rc2) {
-            wf = wca_factor(r2, sig2, eps, &U);
-            add_term_body(S, pi, rv * wf, dl, U);
-        }
-        return 1u;
-    }
-    const T reach_i = T(gi.R) + rc, reach_j = T(gj.R) + rc;
-    if constexpr (DIM == 2) {
-        // V_j x E_i (Eq. DEM_2D, second sum), in i's frame
-        for (int b = 0; b < gj.nv; ++b) {
-            V3<T> p = dl + mul(M, xyz<T>(tab[gj.v_off + b]));
-            bump<COUNT>(pc, C_VTX);
-            if (!(dot(p, p) < reach_i * reach_i)) continue;
-            for (int e = 0; e < gi.ne; ++e) {
-                R4 ea = tab[gi.e_off + 2 * e], ed = tab[gi.e_off + 2 * e + 1];
-                V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
-                V3<T> c = A + D * T(0.5) - p;
-                T lim = ea.w + rc;
-                bump<COUNT>(pc, C_SPHERE);
-                if (!(dot(c, c) < lim * lim)) continue;
-                bump<COUNT>(pc, C_PTSEG);
-                V3<T> q = A + D * clamp01(dot(p - A, D) * ed.w);
-                V3<T> rv = q - p;
-                T r2 = dot(rv, rv);
-                if (r2 < rc2) {
-                    wf = wca_factor(r2, sig2, eps, &U);
-                    add_term_body(S, q, rv * wf, dl, U);
-                }
-            }
-        }
-        // V_i x E_j (Eq. DEM_2D, first sum), in j's frame
-        for (int a_ = 0; a_ < gi.nv; ++a_) {
-            V3<T> u = xyz<T>(tab[gi.v_off + a_]);
-            V3<T> p = mul_t(M, u - dl);
-            bump<COUNT>(pc, C_VTX);
-            if (!(dot(p, p) < reach_j * reach_j)) continue;
-            for (int e = 0; e < gj.ne; ++e) {
-                R4 ea = tab[gj.e_off + 2 * e], ed = tab[gj.e_off + 2 * e + 1];
-                V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
-                V3<T> c = A + D * T(0.5) - p;
-                T lim = ea.w + rc;
-                bump<COUNT>(pc, C_SPHERE);
-                if (!(dot(c, c) < lim * lim)) continue;
-                bump<COUNT>(pc, C_PTSEG);
-                V3<T> q = A + D * clamp01(dot(p - A, D) * ed.w);
-                V3<T> rv = p - q;
-                T r2 = dot(rv, rv);
-                if (r2 < rc2) {
-                    bump<COUNT>(pc, C_JTERMS);
-                    wf = wca_factor(r2, sig2, eps, &U);
-                    add_term_body(S, u, mul(M, rv * wf), dl, U);
-                }
-            }
-        }
-        return (unsigned)(gi.nv * gj.ne + gj.nv * gi.ne);
-    } else {
-        // 3D.  V_j x F_i (Eq. DEM, third sum), in i's frame
-        for (int b = 0; b < gj.nv; ++b) {
-            V3<T> p = dl + mul(M, xyz<T>(tab[gj.v_off + b]));
-            bump<COUNT>(pc, C_VTX);
-            if (!(dot(p, p) < reach_i * reach_i)) continue;
-            for (int f = 0; f < gi.nf; ++f) {
-                V3<T> q;
-                T r2;
-                if (!face_nearest<T, COUNT>(tab, itab, gi.f_off + f, gi.fi_off + 2 * f, p, rc, &q, &r2, pc))
-                    continue;
-                if (r2 < rc2) {
-                    wf = wca_factor(r2, sig2, eps, &U);
-                    add_term_body(S, q, (q - p) * wf, dl, U);
-                }
-            }
-        }
-        // V_i x F_j (Eq. DEM, second sum), in j's frame
-        for (int a_ = 0; a_ < gi.nv; ++a_) {
-            V3<T> u = xyz<T>(tab[gi.v_off + a_]);
-            V3<T> p = mul_t(M, u - dl);
-            bump<COUNT>(pc, C_VTX);
-            if (!(dot(p, p) < reach_j * reach_j)) continue;
-            for (int f = 0; f < gj.nf; ++f) {
-                V3<T> q;
-                T r2;
-                if (!face_nearest<T, COUNT>(tab, itab, gj.f_off + f, gj.fi_off + 2 * f, p, rc, &q, &r2, pc))
-                    continue;
-                if (r2 < rc2) {
-                    bump<COUNT>(pc, C_JTERMS);
-                    wf = wca_factor(r2, sig2, eps, &U);
-                    add_term_body(S, u, mul(M, (p - q) * wf), dl, U);
-                }
-            }
-        }
-        // E_i x E_j (Eq. DEM, first sum), in i's frame
-        for (int eb = 0; eb < (gi.ne > 0 ? gj.ne : 0); ++eb) {
-            R4 ba = tab[gj.e_off + 2 * eb], bd = tab[gj.e_off + 2 * eb + 1];
-            V3<T> A2 = dl + mul(M, xyz<T>(ba));
-            V3<T> D2 = mul(M, xyz<T>(bd));
-            V3<T> C2 = A2 + D2 * T(0.5);
-            T reach = reach_i + ba.w;
-            bump<COUNT>(pc, C_EDGE);
-            if (!(dot(C2, C2) < reach * reach)) continue;
-            for (int ea = 0; ea < gi.ne; ++ea) {
-                R4 aa = tab[gi.e_off + 2 * ea], ad = tab[gi.e_off + 2 * ea + 1];
-                V3<T> A1 = xyz<T>(aa), D1 = xyz<T>(ad);
-                V3<T> dc = A1 + D1 * T(0.5) - C2;
-                T lim = aa.w + ba.w + rc;
-                bump<COUNT>(pc, C_SPHERE);
-                if (!(dot(dc, dc) < lim * lim)) continue;
-                bump<COUNT>(pc, C_SEGSEG);
-                V3<T> P1, P2;
-                segment_nearest<T>(A1, D1, ad.w, A2, D2, bd.w, par_eps, &P1, &P2);
-                V3<T> rv = P1 - P2;
-                T r2 = dot(rv, rv);
-                if (r2 < rc2) {
-                    wf = wca_factor(r2, sig2, eps, &U);
-                    add_term_body(S, P1, rv * wf, dl, U);
-                }
-            }
-        }
-        return (unsigned)(gi.ne * gj.ne + gi.nv * gj.nf + gj.nv * gi.nf);
-    }
+template <class T, bool COMP>
+__device__ __forceinline__ void finish_particle(const PairArgs &a, int i, const SumSink<T, COMP> &S,
+                                                const M33<T> &R) {
+    T tot[13], out[13];
+#pragma unroll
+    for (int k = 0; k < 13; ++k) tot[k] = S.total(k);
+    world_outputs(tot, R, out);
+    double v[13];
+#pragma unroll
+    for (int k = 0; k < 13; ++k) v[k] = (double)out[k];
+    store_outputs(a, i, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,7 +492,7 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
         const Geom gi = geo[shi.geom];
         const Owner<T> own = make_owner<T>(a, i, shi, gi);
         const M33<T> Ri = orientation<T>(a, i);
-        Sums<T, COMP> S;
+        SumSink<T, COMP> S;
         S.zero();
         const int nn = a.nn[i];
         for (int k = 0; k < nn; ++k) {
@@ -346,20 +501,20 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
             int j;
             bump<COUNT>(&pc, C_NEIGH);
             if (!in_range<T>(a, e, own, &j, &pg)) continue;
-            const M33<T> Rj = orientation<T>(a, j);
-            const M33<T> M = mul_tn(Ri, Rj);
-            const V3<T> dl = mul_t(Ri, pg.d);
-            const T rc = (T)WCA_CUT * pg.sig;
-            unsigned nf = pair_terms<T, COMP, DIM, COUNT>(tab, itab, gi, geo[pg.gj], M, dl, rc,
-                                                          pg.sig * pg.sig, eps, par_eps, S, &pc);
+            const Geom &gj = geo[pg.gj];
             bump<COUNT>(&pc, C_PAIRS);
-            bump<COUNT>(&pc, C_FPE, nf);
+            bump<COUNT>(&pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
+            PairWork<T> w;
+            w.M = mul_tn(Ri, orientation<T>(a, j));
+            w.dl = mul_t(Ri, pg.d);
+            w.rc = (T)WCA_CUT * pg.sig;
+            w.sig2 = pg.sig * pg.sig;
+            w.gj = pg.gj;
+            if (!pair_setup<T, COUNT>(tab, itab, gi, gj, &w, &pc)) continue;
+            bump<COUNT>(&pc, C_ACTIVE);
+            eval_pair<T, DIM, COUNT>(tab, itab, gi, gj, w, eps, par_eps, S, &pc);
         }
-        bump<COUNT>(&pc, C_TERMS, S.nterm);
-        T out[13];
-        totals(S, Ri, out);
-#pragma unroll
-        for (int k = 0; k < 13; ++k) store_value(a, i, k, (double)out[k]);
+        finish_particle(a, i, S, Ri);
     }
     if constexpr (COUNT)
         for (int k = 0; k < NCOUNT; ++k)
@@ -385,33 +540,38 @@ cudaError_t launch_thread(const PairArgs &a, int block, bool count, size_t smem,
 }
 
 // ---------------------------------------------------------------------------
-// WARP decomposition
-//
-// One warp per particle i (grid-stride over particles, persistent grid).  The
-// neighbour list is taken 32 entries at a time; each lane tests one entry
-// for the bounding-sphere range and, if in range, writes the pair setup
-// (M = R_i^T R_j, dl, r_cut, sigma^2, j's geometry) to a per-warp slot.
-// Then two compacted phases share the pair work evenly across the lanes:
-//   vertices: items = (slot, vertex of j or of i); each lane maps its vertex
-//     into the face owner's frame and tests its reach; the survivors' (vertex,
-//     face) tests (2D: (vertex, edge)) are re-spread over all lanes with a
-//     warp scan of their counts, the vertex data moving by shuffles;
-//   edges (3D): items = (slot, edge of j); each lane maps its edge into i's
-//     frame and tests its reach; the survivors' (edge of j, edge of i) tests
-//     are re-spread the same way.
-// Each lane keeps private sums; a fixed shuffle tree combines them (two-sum
-// merge in the compensated mode), so results are deterministic.  The 13
-// totals are rotated on lane 0 and written by 13 lanes at once.
+// WARP decomposition: 32 particles per warp, one lane per active pair
 // ---------------------------------------------------------------------------
-template <class T> struct Slot {
-    T m[9];
-    T dl[3];
+constexpr int PQ = 64;   // ring of queued pairs (one round adds at most 32)
+
+template <class T> struct alignas(16) QPair {
+    T m[12];             // row r: M[r][0..2], dl[r] at m[4r + 3]; reused for the partial
     T rc, sig2;
-    int gj;
-    int pad;
+    int gj, owner;       // owner: the particle's lane in the warp
+    unsigned vim, vjm, eim, ejm, fim, fjm;
+};
+template <class T> struct alignas(16) PInfo {   // one particle of the warp
+    T r[9];              // R_i
+    T x[3];              // FP32: delta_i; FP64: position
+    T R, rnd, sig_all;
+    int geom, rep, nn, pad;
+};
+template <class T> struct WarpSmem {
+    QPair<T> q[PQ];
+    PInfo<T> p[32];
+    int offs[32];
 };
 
-// Exclusive warp scan of v; *total = the warp's sum.
+__device__ __forceinline__ int owner_of(const int *off, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total) {
     int x = v;
 #pragma unroll
@@ -423,47 +583,46 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total) {
     return x - v;
 }
 
-// Largest k in [0, n) with off[k] <= t (off non-decreasing, off[0] = 0): the
-// owner of item t when owner k holds items [off[k], off[k+1]).
-__device__ __forceinline__ int owner_of(const int *off, int n, int t) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= t) lo = mid;
-        else hi = mid - 1;
+// Evaluate queued pairs [qh, qh + nb) (one per lane), then let each owner
+// lane add its pairs' partials in queue order.
+template <class T, bool COMP, int DIM, bool COUNT>
+__device__ __forceinline__ void run_batch(WarpSmem<T> &ws, int qh, int nb, int lane,
+                                          const typename R4T<T>::type *tab, const int *itab,
+                                          const Geom *geo, T eps, T par_eps,
+                                          SumSink<T, COMP> &S, PathCount *pc) {
+    if (lane < nb) {
+        QPair<T> &qp = ws.q[(qh + lane) & (PQ - 1)];
+        PairWork<T> w;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) w.M.m[r][c] = qp.m[4 * r + c];
+        w.dl = v3<T>(qp.m[3], qp.m[7], qp.m[11]);
+        w.rc = qp.rc;
+        w.sig2 = qp.sig2;
+        w.gj = qp.gj;
+        w.vim = qp.vim; w.vjm = qp.vjm; w.eim = qp.eim; w.ejm = qp.ejm;
+        w.fim = qp.fim; w.fjm = qp.fjm;
+        PartSink<T> part;
+        part.zero();
+        eval_pair<T, DIM, COUNT>(tab, itab, geo[ws.p[qp.owner].geom], geo[qp.gj], w, eps, par_eps,
+                                 part, pc);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) qp.m[k] = part.v[k];
+        qp.rc = part.v[12];
     }
-    return lo;
-}
-
-template <class T> __device__ __forceinline__ M33<T> slot_m(const Slot<T> &s) {
-    M33<T> M;
+    __syncwarp();
+    for (int e = 0; e < nb; ++e) {
+        const QPair<T> &qp = ws.q[(qh + e) & (PQ - 1)];
+        if (qp.owner == lane) {
+            T v[13];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) M.m[r][c] = s.m[3 * r + c];
-    return M;
-}
-
-template <class T, bool COMP> __device__ __forceinline__ void merge_down(Acc<T, COMP> &x, int o) {
-    const T s = __shfl_down_sync(FULL, x.s, o);
-    const T c = __shfl_down_sync(FULL, x.comp(), o);
-    x.merge(s, c);
-}
-
-template <class T, bool COMP>
-__device__ __forceinline__ void warp_sum(Sums<T, COMP> &S) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            merge_down(S.f[k], o);
-            merge_down(S.t[k], o);
+            for (int k = 0; k < 12; ++k) v[k] = qp.m[k];
+            v[12] = qp.rc;
+            S.add(v);
         }
-        merge_down(S.u, o);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) merge_down(S.w[k], o);
-        S.nterm += __shfl_down_sync(FULL, S.nterm, o);
     }
+    __syncwarp();
 }
 
 template <class T, bool COMP, int DIM, bool COUNT>
@@ -475,11 +634,9 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
     int *itab = reinterpret_cast<int *>(geo + a.n_geoms);
     size_t tb = (size_t)a.table_len * sizeof(R4) + sizeof(Geom) * a.n_geoms +
                 sizeof(int) * a.itable_len;
-    tb = (tb + 31) & ~(size_t)31;
+    tb = (tb + 127) & ~(size_t)127;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    Slot<T> *slots = reinterpret_cast<Slot<T> *>(smem + tb) + w * 32;
-    int *offs = reinterpret_cast<int *>(reinterpret_cast<Slot<T> *>(smem + tb) + wpb * 32) + w * 64;
-    int *loffs = offs + 32;
+    WarpSmem<T> &ws = reinterpret_cast<WarpSmem<T> *>(smem + tb)[w];
     stage_tables<T>(a, tab, geo, itab);
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0 && !COUNT) {
@@ -488,254 +645,117 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
     }
     const T eps = (T)a.eps;
     const T par_eps = (T)a.par_eps;
+    const T sig_all = a.sigma > 0.0 ? (T)a.sigma : T(0);
     PathCount pc;
     if constexpr (COUNT)
         for (int k = 0; k < NCOUNT; ++k) pc.v[k] = 0;
-    for (int i = blockIdx.x * wpb + w; i < a.n; i += gridDim.x * wpb) {
-        const ShapeDev &shi = a.shapes[a.shape[i]];
-        const Geom gi = geo[shi.geom];
-        const Owner<T> own = make_owner<T>(a, i, shi, gi);
-        const M33<T> Ri = orientation<T>(a, i);
-        Sums<T, COMP> S;
+    const int nwarps = gridDim.x * wpb;
+    for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
+        // ---- this lane's particle ----
+        const int i_me = base + lane;
+        const bool mine = i_me < a.n;
+        M33<T> Rme;
+        int nn_me = 0;
+        if (mine) {
+            const ShapeDev &shi = a.shapes[a.shape[i_me]];
+            Rme = orientation<T>(a, i_me);
+            PInfo<T> &pi = ws.p[lane];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) pi.r[3 * r + c] = Rme.m[r][c];
+            if constexpr (std::is_same<T, float>::value) {
+                const float4 dd = a.delta[i_me];
+                pi.x[0] = dd.x; pi.x[1] = dd.y; pi.x[2] = dd.z;
+                pi.rnd = shi.rounding_f;
+            } else {
+                const double4_32a xx = a.pos[i_me];
+                pi.x[0] = xx.x; pi.x[1] = xx.y; pi.x[2] = xx.z;
+                pi.rnd = shi.rounding;
+            }
+            pi.R = (T)geo[shi.geom].R;
+            pi.sig_all = sig_all;
+            pi.geom = shi.geom;
+            pi.rep = a.rep[i_me];
+            nn_me = a.nn[i_me];
+            pi.nn = nn_me;
+        }
+        SumSink<T, COMP> S;
         S.zero();
-        const int nn = a.nn[i];
-        for (int base = 0; base < nn; base += 32) {
-            // ---- pair setups of up to 32 list entries ----
-            const int k = base + lane;
-            PairGeom<T> pg;
-            bool inr = false;
-            int j = 0;
-            if (k < nn) {
+        int total;
+        ws.offs[lane] = warp_excl_scan(nn_me, lane, &total);
+        __syncwarp();
+        int qh = 0, qt = 0;
+        // ---- scan the list entries of the 32 particles ----
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            bool active = false;
+            PairWork<T> wk;
+            int pl = 0;
+            if (t < total) {
+                pl = owner_of(ws.offs, 32, t);
+                const int k = t - ws.offs[pl];
+                const int i = base + pl;
+                const PInfo<T> &pi = ws.p[pl];
+                const Geom &gi = geo[pi.geom];
+                Owner<T> own;
+                own.rp = &a.reps[pi.rep];
+                own.R = pi.R;
+                own.rnd = pi.rnd;
+                own.sig_all = pi.sig_all;
+                own.geom = pi.geom;
+                if constexpr (std::is_same<T, float>::value)
+                    own.delta = make_float4(pi.x[0], pi.x[1], pi.x[2], 0.f);
+                else
+                    own.x = make_double4_32a(pi.x[0], pi.x[1], pi.x[2], 0.0);
                 const float4 e = a.nlist[(size_t)k * a.n + i];
                 bump<COUNT>(&pc, C_NEIGH);
-                inr = in_range<T>(a, e, own, &j, &pg);
-            }
-            const unsigned m = __ballot_sync(FULL, inr);
-            const int ns = __popc(m);
-            if (ns == 0) continue;
-            if (inr) {
-                const int my = __popc(m & ((1u << lane) - 1u));
-                const M33<T> Rj = orientation<T>(a, j);
-                const M33<T> M = mul_tn(Ri, Rj);
-                const V3<T> dl = mul_t(Ri, pg.d);
-                Slot<T> &sl = slots[my];
+                PairGeom<T> pg;
+                int j;
+                if (in_range<T>(a, e, own, &j, &pg)) {
+                    const Geom &gj = geo[pg.gj];
+                    bump<COUNT>(&pc, C_PAIRS);
+                    bump<COUNT>(&pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
+                    M33<T> Ri;
 #pragma unroll
-                for (int r = 0; r < 3; ++r)
+                    for (int r = 0; r < 3; ++r)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) sl.m[3 * r + c] = M.m[r][c];
-                sl.dl[0] = dl.x; sl.dl[1] = dl.y; sl.dl[2] = dl.z;
-                sl.rc = (T)WCA_CUT * pg.sig;
-                sl.sig2 = pg.sig * pg.sig;
-                sl.gj = pg.gj;
-                const Geom &gj = geo[pg.gj];
-                if (gi.nv == 1 && gj.nv == 1) {
-                    // sphere / disk limit: the one central term, by this lane
-                    const V3<T> pi = xyz<T>(tab[gi.v_off]);
-                    const V3<T> rv = pi - (dl + mul(M, xyz<T>(tab[gj.v_off])));
-                    const T r2 = dot(rv, rv);
-                    if (r2 < sl.rc * sl.rc) {
-                        T U;
-                        const T wf = wca_factor(r2, sl.sig2, eps, &U);
-                        add_term_body(S, pi, rv * wf, dl, U);
-                    }
-                    bump<COUNT>(&pc, C_FPE, 1u);
-                } else if (DIM == 2) {
-                    bump<COUNT>(&pc, C_FPE, (unsigned)(gi.nv * gj.ne + gj.nv * gi.ne));
-                } else {
-                    bump<COUNT>(&pc, C_FPE, (unsigned)(gi.ne * gj.ne + gi.nv * gj.nf + gj.nv * gi.nf));
+                        for (int c = 0; c < 3; ++c) Ri.m[r][c] = pi.r[3 * r + c];
+                    wk.M = mul_tn(Ri, orientation<T>(a, j));
+                    wk.dl = mul_t(Ri, pg.d);
+                    wk.rc = (T)WCA_CUT * pg.sig;
+                    wk.sig2 = pg.sig * pg.sig;
+                    wk.gj = pg.gj;
+                    active = pair_setup<T, COUNT>(tab, itab, gi, gj, &wk, &pc);
+                    if (active) bump<COUNT>(&pc, C_ACTIVE);
                 }
-                bump<COUNT>(&pc, C_PAIRS);
             }
+            const unsigned m = __ballot_sync(FULL, active);
+            if (active) {
+                QPair<T> &qp = ws.q[(qt + __popc(m & ((1u << lane) - 1u))) & (PQ - 1)];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) qp.m[4 * r + c] = wk.M.m[r][c];
+                }
+                qp.m[3] = wk.dl.x; qp.m[7] = wk.dl.y; qp.m[11] = wk.dl.z;
+                qp.rc = wk.rc;
+                qp.sig2 = wk.sig2;
+                qp.gj = wk.gj;
+                qp.owner = pl;
+                qp.vim = wk.vim; qp.vjm = wk.vjm; qp.eim = wk.eim; qp.ejm = wk.ejm;
+                qp.fim = wk.fim; qp.fjm = wk.fjm;
+            }
+            qt += __popc(m);
             __syncwarp();
-
-            // ---- vertex phase ----
-            {
-                int c = 0;
-                if (lane < ns) {
-                    const Geom &gj = geo[slots[lane].gj];
-                    c = (gi.nv == 1 && gj.nv == 1) ? 0 : gj.nv + gi.nv;
-                }
-                int tot;
-                const int ex = warp_excl_scan(c, lane, &tot);
-                offs[lane] = ex;
-                __syncwarp();
-                for (int t0 = 0; t0 < tot; t0 += 32) {
-                    const int t = t0 + lane;
-                    bool surv = false;
-                    V3<T> p = v3<T>(T(0), T(0), T(0));
-                    int s = 0, dir = 0, vid = 0, nfc = 0;
-                    if (t < tot) {
-                        s = owner_of(offs, ns, t);
-                        const Slot<T> &sl = slots[s];
-                        const Geom &gj = geo[sl.gj];
-                        const M33<T> M = slot_m(sl);
-                        const V3<T> dl = v3<T>(sl.dl[0], sl.dl[1], sl.dl[2]);
-                        vid = t - offs[s];
-                        T reach;
-                        if (vid < gj.nv) {          // vertex of j against i's faces
-                            dir = 0;
-                            p = dl + mul(M, xyz<T>(tab[gj.v_off + vid]));
-                            reach = T(gi.R) + sl.rc;
-                            nfc = DIM == 3 ? gi.nf : gi.ne;
-                        } else {                    // vertex of i against j's faces
-                            dir = 1;
-                            vid -= gj.nv;
-                            p = mul_t(M, xyz<T>(tab[gi.v_off + vid]) - dl);
-                            reach = T(gj.R) + sl.rc;
-                            nfc = DIM == 3 ? gj.nf : gj.ne;
-                        }
-                        bump<COUNT>(&pc, C_VTX);
-                        surv = dot(p, p) < reach * reach;
-                    }
-                    int ftot;
-                    const int fex = warp_excl_scan(surv ? nfc : 0, lane, &ftot);
-                    loffs[lane] = fex;
-                    __syncwarp();
-                    for (int u0 = 0; u0 < ftot; u0 += 32) {
-                        const int u = u0 + lane;
-                        const int L = owner_of(loffs, 32, u < ftot ? u : ftot - 1);
-                        const T px = __shfl_sync(FULL, p.x, L);
-                        const T py = __shfl_sync(FULL, p.y, L);
-                        const T pz = __shfl_sync(FULL, p.z, L);
-                        const int os = __shfl_sync(FULL, s, L);
-                        const int od = __shfl_sync(FULL, dir, L);
-                        const int ov = __shfl_sync(FULL, vid, L);
-                        if (u < ftot) {
-                            const int f = u - loffs[L];
-                            const Slot<T> &sl = slots[os];
-                            const Geom &go = od == 0 ? gi : geo[sl.gj];
-                            const T rc = sl.rc;
-                            const V3<T> P = v3<T>(px, py, pz);
-                            V3<T> q;
-                            T r2;
-                            bool hit;
-                            if constexpr (DIM == 3) {
-                                hit = face_nearest<T, COUNT>(tab, itab, go.f_off + f, go.fi_off + 2 * f,
-                                                             P, rc, &q, &r2, &pc) && r2 < rc * rc;
-                            } else {
-                                const R4 ea = tab[go.e_off + 2 * f], ed = tab[go.e_off + 2 * f + 1];
-                                const V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
-                                const V3<T> cc = A + D * T(0.5) - P;
-                                const T lim = ea.w + rc;
-                                bump<COUNT>(&pc, C_SPHERE);
-                                hit = false;
-                                if (dot(cc, cc) < lim * lim) {
-                                    bump<COUNT>(&pc, C_PTSEG);
-                                    q = A + D * clamp01(dot(P - A, D) * ed.w);
-                                    const V3<T> rr = P - q;
-                                    r2 = dot(rr, rr);
-                                    hit = r2 < rc * rc;
-                                }
-                            }
-                            if (hit) {
-                                T U;
-                                const T wf = wca_factor(r2, sl.sig2, eps, &U);
-                                const V3<T> dl = v3<T>(sl.dl[0], sl.dl[1], sl.dl[2]);
-                                if (od == 0) {
-                                    add_term_body(S, q, (q - P) * wf, dl, U);
-                                } else {
-                                    bump<COUNT>(&pc, C_JTERMS);
-                                    add_term_body(S, xyz<T>(tab[gi.v_off + ov]),
-                                                  mul(slot_m(sl), (P - q) * wf), dl, U);
-                                }
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
+            if (qt - qh >= 32) {
+                run_batch<T, COMP, DIM, COUNT>(ws, qh, 32, lane, tab, itab, geo, eps, par_eps, S, &pc);
+                qh += 32;
             }
-
-            // ---- edge phase (3D) ----
-            if constexpr (DIM == 3) {
-                int c = 0;
-                if (lane < ns) {
-                    const Geom &gj = geo[slots[lane].gj];
-                    c = (gi.nv == 1 && gj.nv == 1) || gi.ne == 0 ? 0 : gj.ne;
-                }
-                int tot;
-                const int ex = warp_excl_scan(c, lane, &tot);
-                offs[lane] = ex;
-                __syncwarp();
-                for (int t0 = 0; t0 < tot; t0 += 32) {
-                    const int t = t0 + lane;
-                    bool surv = false;
-                    V3<T> A2 = v3<T>(T(0), T(0), T(0)), D2 = A2;
-                    T h2 = T(0), ic = T(0);
-                    int s = 0;
-                    if (t < tot) {
-                        s = owner_of(offs, ns, t);
-                        const Slot<T> &sl = slots[s];
-                        const Geom &gj = geo[sl.gj];
-                        const M33<T> M = slot_m(sl);
-                        const V3<T> dl = v3<T>(sl.dl[0], sl.dl[1], sl.dl[2]);
-                        const int eb = t - offs[s];
-                        const R4 ba = tab[gj.e_off + 2 * eb], bd = tab[gj.e_off + 2 * eb + 1];
-                        A2 = dl + mul(M, xyz<T>(ba));
-                        D2 = mul(M, xyz<T>(bd));
-                        h2 = ba.w;
-                        ic = bd.w;
-                        const V3<T> C2 = A2 + D2 * T(0.5);
-                        const T reach = T(gi.R) + sl.rc + h2;
-                        bump<COUNT>(&pc, C_EDGE);
-                        surv = dot(C2, C2) < reach * reach;
-                    }
-                    int etot;
-                    const int eex = warp_excl_scan(surv ? gi.ne : 0, lane, &etot);
-                    loffs[lane] = eex;
-                    __syncwarp();
-                    for (int u0 = 0; u0 < etot; u0 += 32) {
-                        const int u = u0 + lane;
-                        const int L = owner_of(loffs, 32, u < etot ? u : etot - 1);
-                        const V3<T> a2 = v3<T>(__shfl_sync(FULL, A2.x, L), __shfl_sync(FULL, A2.y, L),
-                                               __shfl_sync(FULL, A2.z, L));
-                        const V3<T> d2 = v3<T>(__shfl_sync(FULL, D2.x, L), __shfl_sync(FULL, D2.y, L),
-                                               __shfl_sync(FULL, D2.z, L));
-                        const T oh = __shfl_sync(FULL, h2, L);
-                        const T oic = __shfl_sync(FULL, ic, L);
-                        const int os = __shfl_sync(FULL, s, L);
-                        if (u < etot) {
-                            const int ea = u - loffs[L];
-                            const Slot<T> &sl = slots[os];
-                            const T rc = sl.rc;
-                            const R4 aa = tab[gi.e_off + 2 * ea], ad = tab[gi.e_off + 2 * ea + 1];
-                            const V3<T> A1 = xyz<T>(aa), D1 = xyz<T>(ad);
-                            const V3<T> dc = A1 + D1 * T(0.5) - (a2 + d2 * T(0.5));
-                            const T lim = aa.w + oh + rc;
-                            bump<COUNT>(&pc, C_SPHERE);
-                            if (dot(dc, dc) < lim * lim) {
-                                bump<COUNT>(&pc, C_SEGSEG);
-                                V3<T> P1, P2;
-                                segment_nearest<T>(A1, D1, ad.w, a2, d2, oic, par_eps, &P1, &P2);
-                                const V3<T> rv = P1 - P2;
-                                const T r2 = dot(rv, rv);
-                                if (r2 < rc * rc) {
-                                    T U;
-                                    const T wf = wca_factor(r2, sl.sig2, eps, &U);
-                                    add_term_body(S, P1, rv * wf,
-                                                  v3<T>(sl.dl[0], sl.dl[1], sl.dl[2]), U);
-                                }
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-            __syncwarp();
         }
-        warp_sum(S);
-        T out[13];
-        if (lane == 0) {
-            bump<COUNT>(&pc, C_TERMS, S.nterm);
-            totals(S, Ri, out);
-        }
-        // lane k stores value k: the 13 conversions to FP64 run side by side
-        T mine = T(0);
-#pragma unroll
-        for (int k = 0; k < 13; ++k) {
-            const T v = __shfl_sync(FULL, lane == 0 ? out[k] : T(0), 0);
-            if (lane == k) mine = v;
-        }
-        if (lane < 13) store_value(a, i, lane, (double)mine);
+        if (qt > qh) run_batch<T, COMP, DIM, COUNT>(ws, qh, qt - qh, lane, tab, itab, geo, eps, par_eps, S, &pc);
+        if (mine) finish_particle(a, i_me, S, Rme);
+        __syncwarp();
     }
     if constexpr (COUNT)
         for (int k = 0; k < NCOUNT; ++k)
@@ -772,11 +792,11 @@ int sm_count() {
 template <class T, bool COMP, int DIM>
 cudaError_t launch_warp(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
     const int block = 128;
-    size_t smem = ((smem_tables + 31) & ~(size_t)31) + (block / 32) * (32 * sizeof(Slot<T>) + 64 * sizeof(int));
+    size_t smem = ((smem_tables + 127) & ~(size_t)127) + (block / 32) * sizeof(WarpSmem<T>);
     auto launch = [&](auto kernel) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        long long need = (a.n + (block / 32) - 1) / (block / 32);
+        long long need = (a.n + block - 1) / block;        // 32 particles per warp
         long long cap = (long long)blocks_per_sm(kernel, block, smem) * sm_count();
         int grid = (int)(need < cap ? need : cap);
         if (grid < 1) grid = 1;

@@ -5,9 +5,9 @@
 // Frames: every term of the ordered pair (i, j) is evaluated in i's body
 // frame, where i's features are constants of the geometry table.  j's
 // vertices and edges are mapped in with M = R_i^T R_j and dl = R_i^T d
-// (d = x_j - x_i, minimum image, formed in FP64).  Vertex(i)-face(j) terms
-// are evaluated in j's body frame instead (j's faces are then table
-// constants) and their force is mapped back with M.
+// (d = x_j - x_i, minimum image).  Vertex(i)-face(j) terms are evaluated in
+// j's body frame instead (j's faces are then table constants) and their
+// force is mapped back with M.
 #pragma once
 
 #include "dem_internal.cuh"
@@ -116,21 +116,6 @@ template <> struct Acc<float, true> {
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
-// Per-particle accumulators of one owner i: force and torque in i's body
-// frame, energy, and the symmetric body-frame virial (xx, xy, xz, yy, yz, zz).
-template <class T, bool COMP> struct Sums {
-    Acc<T, COMP> f[3], t[3], u, w[6];
-    unsigned int nterm;  // terms evaluated (counting launches)
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { f[k].zero(); t[k].zero(); }
-        u.zero();
-#pragma unroll
-        for (int k = 0; k < 6; ++k) w[k].zero();
-        nterm = 0;
-    }
-};
-
 // WCA of one feature pair (Eq. LJ, Eq. WCA) at squared nearest-point distance
 // r2 < r_cut^2: returns w with the force on i equal to w (p_i - p_j), and
 // *U = 4 eps ((s/r)^12 - (s/r)^6) + eps (the shift removes U_LJ(r_cut) = -eps).
@@ -142,26 +127,6 @@ __device__ __forceinline__ T wca_factor(T r2, T sig2, T eps, T *U) {
     T s12 = s6 * s6;
     *U = T(4) * eps * (s12 - s6) + eps;
     return T(24) * eps * (T(2) * s12 - s6) * ir2;
-}
-
-// Accumulate one term: force f on i and lever arm pi = p_i - x_i, both in
-// i's frame; half the energy; the body-frame virial 1/2 sym((-dl) (x) f)
-// with dl = x_j - x_i in i's frame (the world virial is R_i W R_i^T).
-template <class T, bool COMP>
-__device__ __forceinline__ void add_term_body(Sums<T, COMP> &S, V3<T> pi, V3<T> f, V3<T> dl,
-                                              T U) {
-    V3<T> tq = cross(pi, f);
-    S.f[0].add(f.x); S.f[1].add(f.y); S.f[2].add(f.z);
-    S.t[0].add(tq.x); S.t[1].add(tq.y); S.t[2].add(tq.z);
-    S.u.add(T(0.5) * U);
-    const T x = -dl.x, y = -dl.y, z = -dl.z;
-    S.w[0].add(T(0.5) * x * f.x);
-    S.w[1].add(T(0.25) * (x * f.y + y * f.x));
-    S.w[2].add(T(0.25) * (x * f.z + z * f.x));
-    S.w[3].add(T(0.5) * y * f.y);
-    S.w[4].add(T(0.25) * (y * f.z + z * f.y));
-    S.w[5].add(T(0.5) * z * f.z);
-    S.nterm++;
 }
 
 // Work counters of a counting launch (see dem_get_counters).
@@ -179,7 +144,10 @@ enum {
     C_NEIGH = 10,      // neighbour-list entries scanned
     C_INSIDE = 11,     // vertex-face projections inside the face
     C_JTERMS = 12,     // terms evaluated in j's frame
-    NCOUNT = 16
+    C_ACTIVE = 15,     // pairs that pass the separating-axis test
+    C_PROJ = 16,       // vertex projections of the separating-axis test
+    C_LINE = 17,       // carrier-line distance tests of edge pairs
+    NCOUNT = 20
 };
 struct PathCount {
     unsigned int v[NCOUNT];
@@ -195,6 +163,13 @@ __device__ __forceinline__ void bump(PathCount *pc, int k, unsigned int n = 1) {
 // in-plane edge tests >= 0) q is the projection; else q is the nearest
 // point on the edges whose test fails (the nearest boundary point of a
 // convex polygon lies on such an edge).
+// The nearest point after a passed plane test (nf the face record, h the
+// signed plane distance of p).
+template <class T, bool COUNT, class R4>
+__device__ __forceinline__ void face_rest(const R4 *tab, const int *itab, int face_int,
+                                          const R4 &nf, V3<T> p, T h, V3<T> *q, T *r2,
+                                          PathCount *pc);
+
 template <class T, bool COUNT, class R4>
 __device__ __forceinline__ bool face_nearest(const R4 *tab, const int *itab, int face_rec,
                                              int face_int, V3<T> p, T rc, V3<T> *q, T *r2,
@@ -203,6 +178,14 @@ __device__ __forceinline__ bool face_nearest(const R4 *tab, const int *itab, int
     T h = nf.x * p.x + nf.y * p.y + nf.z * p.z - nf.w;
     bump<COUNT>(pc, C_PLANE);
     if (!(fabs(h) < rc)) return false;
+    face_rest<T, COUNT>(tab, itab, face_int, nf, p, h, q, r2, pc);
+    return true;
+}
+
+template <class T, bool COUNT, class R4>
+__device__ __forceinline__ void face_rest(const R4 *tab, const int *itab, int face_int,
+                                          const R4 &nf, V3<T> p, T h, V3<T> *q, T *r2,
+                                          PathCount *pc) {
     int fe = itab[face_int], cnt = itab[face_int + 1];
     bool inside = true;
     T best = T(3.0e38);
@@ -231,7 +214,6 @@ __device__ __forceinline__ bool face_nearest(const R4 *tab, const int *itab, int
         *q = bq;
         *r2 = best;
     }
-    return true;
 }
 
 // Nearest points of segments [A1, A1 + D1] and [A2, A2 + D2] (inv_a =

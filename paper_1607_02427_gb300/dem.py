@@ -247,7 +247,7 @@ def dem_autotune(ctx):
 
 
 def dem_get_counters(ctx) -> np.ndarray:
-    c = np.zeros(16, np.int64)
+    c = np.zeros(20, np.int64)
     _check(load().dem_get_counters(ctx, c.ctypes.data_as(C.POINTER(C.c_longlong))), ctx)
     return c
 
