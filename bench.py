@@ -85,7 +85,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the e2e, FP64 and CPU-baseline measurements")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--decomp", default="auto", choices=["auto", "thread", "warp"])
+    p.add_argument("--decomp", default="auto", choices=["auto", "thread", "warp", "staged"])
     return p.parse_args()
 
 
@@ -297,11 +297,11 @@ def main():
     if a.decomp == "auto":
         dem.dem_autotune(d.ctx)
     else:
-        d.set_param("decomp", {"thread": 1, "warp": 2}[a.decomp])
-    decomp_name = {1: "thread", 2: "warp", 3: "tiled"}[int(d.get_param("decomp"))]
+        d.set_param("decomp", {"thread": 1, "warp": 2, "staged": 3}[a.decomp])
+    decomp_name = {1: "thread", 2: "warp", 3: "staged"}[int(d.get_param("decomp"))]
     tune = {}
     if a.decomp == "auto":
-        for k, nm in enumerate(["thread64", "thread128", "warp128"]):
+        for k, nm in enumerate(["thread64", "thread128", "warp128", "staged128"]):
             tune[nm] = d.get_param(f"autotune_ms_{k}")
 
     # warm-up

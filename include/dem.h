@@ -83,7 +83,11 @@ extern "C" {
                                 culls, and evaluate 32 queued pairs at a time,
                                 one per lane; each particle's lane sums its
                                 pairs in queue order                           */
-#define DEM_DECOMP_TILED 3   /* reserved                                        */
+#define DEM_DECOMP_STAGED 3  /* one warp per 32 particles streams their work
+                                through shared-memory queues: (pair, vertex)
+                                and (pair, edge) items with the cheap tests,
+                                then the queued survivors (face nearest point,
+                                segment-segment, WCA terms) 32 at a time       */
 
 typedef struct dem_ctx dem_ctx;   /* opaque; owned by the library */
 
@@ -220,7 +224,8 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value);
 
 /* Run every pair-kernel decomposition and block size on the current state
  * and keep the fastest (timed with CUDA events on the context's stream).
- * Candidates, in order: THREAD with 64 and 128 threads per block, WARP;
+ * Candidates, in order: THREAD with 64 and 128 threads per block, WARP,
+ * STAGED;
  * their mean times are readable as parameters "autotune_ms_0", ... .
  * Results are identical for every choice up to floating-point summation
  * order; the chosen one is the "decomp" and "block" parameters. */

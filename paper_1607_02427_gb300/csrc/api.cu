@@ -325,7 +325,11 @@ void build_tables(const std::vector<HostGeom> &geoms, const std::vector<HostShap
         sd.rounding = h.rounding;
         sd.rounding_f = (float)h.rounding;
         sd.mass = h.mass;
-        for (int k = 0; k < 3; ++k) sd.inertia[k] = h.inertia[k];
+        sd.inv_mass = 1.0 / h.mass;
+        for (int k = 0; k < 3; ++k) {
+            sd.inertia[k] = h.inertia[k];
+            sd.inv_inertia[k] = h.inertia[k] > 0.0 ? 1.0 / h.inertia[k] : 0.0;
+        }
         t->rnd_max = std::max(t->rnd_max, h.rounding);
         t->shapes.push_back(sd);
     }
@@ -523,6 +527,7 @@ int setup_replicas(dem_ctx *ctx) {
         rp.allpairs = 0;
         for (int a = 0; a < 3; ++a) {
             rp.L[a] = a < ctx->dim ? ctx->box[3 * r + a] : 1.0;
+            rp.inv_L[a] = 1.0 / rp.L[a];
             if (a < ctx->dim) {
                 if (!(rp.L[a] >= 2.0 * rlist))
                     return set_err(ctx, DEM_ERR_BOX,
@@ -961,7 +966,7 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
         ctx->par_eps = value;
     } else if (n == "decomp") {
         int d = (int)value;
-        if (d < DEM_DECOMP_AUTO || d > DEM_DECOMP_TILED) return set_err(ctx, DEM_ERR_ARG, "bad decomp");
+        if (d < DEM_DECOMP_AUTO || d > DEM_DECOMP_STAGED) return set_err(ctx, DEM_ERR_ARG, "bad decomp");
         ctx->decomp = d == DEM_DECOMP_AUTO ? DEM_DECOMP_THREAD : d;
     } else if (n == "block") {
         int b = (int)value;
@@ -1305,7 +1310,7 @@ int dem_autotune(dem_ctx *ctx) {
     if (rc) return rc;
     struct Cand { int decomp, block; };
     const Cand cands[] = {{DEM_DECOMP_THREAD, 64}, {DEM_DECOMP_THREAD, 128},
-                          {DEM_DECOMP_WARP, 128}};
+                          {DEM_DECOMP_WARP, 128}, {DEM_DECOMP_STAGED, 128}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

@@ -60,12 +60,15 @@ struct ShapeDev {
     double rounding;
     double mass;
     double inertia[3];   // principal moments (2D: inertia[2] = I_z)
+    double inv_inertia[3];  // 1 / inertia[k], 0 where inertia[k] = 0
+    double inv_mass;
     float rounding_f;    // FP32 copy of rounding for the FP32 kernels
     float pad;
 };
 
 struct Rep {
     double L[3];
+    double inv_L[3];     // 1 / L[k]
     int off, n;          // particle range
     int cell_off;        // first cell of this replica in the global cell arrays
     int nc[3];           // cells per axis
@@ -155,6 +158,9 @@ struct StepArgs {
 cudaError_t launch_pair(const PairArgs &a, int precision, int decomp, int block, bool count,
                         cudaStream_t s);
 size_t pair_smem_bytes(const PairArgs &a, int precision);
+// STAGED decomposition (pair_staged.cu); smem_tables = pair_smem_bytes().
+cudaError_t launch_pair_staged(const PairArgs &a, int precision, bool count, size_t smem_tables,
+                               cudaStream_t s);
 cudaError_t launch_cells(const NlistArgs &a, int n_cells, cudaStream_t s);
 cudaError_t launch_nlist(const NlistArgs &a, cudaStream_t s);
 cudaError_t launch_first_half(const StepArgs &a, cudaStream_t s);

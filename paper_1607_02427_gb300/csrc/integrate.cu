@@ -36,15 +36,37 @@ __device__ __forceinline__ void set_comp(double4_32a &v, int k, double x) {
     if (k == 0) v.x = x; else if (k == 1) v.y = x; else v.z = x;
 }
 
-// One sincos of phi/2 serves both the quaternion (half angle) and the
-// angular momentum (cos phi = 1 - 2 s^2, sin phi = 2 s c): FP64
-// transcendentals are expensive on this part.
-__device__ __forceinline__ void free_rotor_axis(double4_32a &q, double4_32a &L, const double *I, int k,
-                                                double dt) {
-    if (!(I[k] > 0.0)) return;
-    double phi = comp(L, k) / I[k] * dt;
+// sin h and cos h for |h| <= 1/8 from their Maclaurin series, evaluated by
+// Horner's rule in h^2 and truncated after h^9 (sin) and h^10 (cos).  The
+// first omitted terms, h^11/11! and h^12/12!, are below 2.4e-17 |h| and
+// 3.1e-20: under half an ulp of either result.
+__device__ __forceinline__ void sincos_small(double h, double *s, double *c) {
+    const double h2 = h * h;
+    double ps = 1.0 / 362880.0;
+    ps = fma(ps, h2, -1.0 / 5040.0);
+    ps = fma(ps, h2, 1.0 / 120.0);
+    ps = fma(ps, h2, -1.0 / 6.0);
+    *s = fma(ps * h2, h, h);
+    double pc = -1.0 / 3628800.0;
+    pc = fma(pc, h2, 1.0 / 40320.0);
+    pc = fma(pc, h2, -1.0 / 720.0);
+    pc = fma(pc, h2, 1.0 / 24.0);
+    pc = fma(pc, h2, -0.5);
+    *c = fma(pc, h2, 1.0);
+}
+
+// One sine-cosine pair of phi/2 serves both the quaternion (half angle) and
+// the angular momentum (cos phi = 1 - 2 s^2, sin phi = 2 s c).  FP64 runs at
+// a small fraction of the FP32 rate on this part, so the rotation avoids
+// divisions (1/I is stored) and, for the usual small angles, the general
+// sincos.
+__device__ __forceinline__ void free_rotor_axis(double4_32a &q, double4_32a &L, const double *invI,
+                                                int k, double dt) {
+    if (!(invI[k] > 0.0)) return;
+    const double half = 0.5 * dt * comp(L, k) * invI[k];
     double sh, ch;
-    sincos(0.5 * phi, &sh, &ch);
+    if (fabs(half) <= 0.125) sincos_small(half, &sh, &ch);
+    else sincos(half, &sh, &ch);
     quat_rotate_body(q, k, ch, sh);
     int a = (k + 1) % 3, b = (k + 2) % 3;
     double c = 1.0 - 2.0 * sh * sh, s = 2.0 * sh * ch;
@@ -53,9 +75,11 @@ __device__ __forceinline__ void free_rotor_axis(double4_32a &q, double4_32a &L, 
     set_comp(L, b, -s * La + c * Lb);
 }
 
-__device__ __forceinline__ double wrap(double x, double L) {
-    x -= L * floor(x / L);
+// x mapped into [0, L) (invL = 1/L)
+__device__ __forceinline__ double wrap(double x, double L, double invL) {
+    x -= L * floor(x * invL);
     if (x >= L) x -= L;
+    else if (x < 0.0) x += L;
     return x;
 }
 
@@ -76,19 +100,19 @@ __global__ void k_first_half(const StepArgs a) {
             v.x *= s; v.y *= s; v.z *= s;
             L.x *= s; L.y *= s; L.z *= s;
         }
-        const double h = 0.5 * a.dt / sh.mass;
+        const double h = 0.5 * a.dt * sh.inv_mass;
         v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
         L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
-        x.x = wrap(x.x + a.dt * v.x, rp.L[0]);
-        x.y = wrap(x.y + a.dt * v.y, rp.L[1]);
-        if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2]);
-        free_rotor_axis(q, L, sh.inertia, 2, 0.5 * a.dt);
-        free_rotor_axis(q, L, sh.inertia, 1, 0.5 * a.dt);
-        free_rotor_axis(q, L, sh.inertia, 0, a.dt);
-        free_rotor_axis(q, L, sh.inertia, 1, 0.5 * a.dt);
-        free_rotor_axis(q, L, sh.inertia, 2, 0.5 * a.dt);
-        double nq = sqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-        q.x /= nq; q.y /= nq; q.z /= nq; q.w /= nq;
+        x.x = wrap(x.x + a.dt * v.x, rp.L[0], rp.inv_L[0]);
+        x.y = wrap(x.y + a.dt * v.y, rp.L[1], rp.inv_L[1]);
+        if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2], rp.inv_L[2]);
+        free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inv_inertia, 0, a.dt);
+        free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
+        const double inq = rsqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        q.x *= inq; q.y *= inq; q.z *= inq; q.w *= inq;
         a.pos[i] = x;
         a.vel[i] = v;
         a.angmom[i] = L;
@@ -96,9 +120,9 @@ __global__ void k_first_half(const StepArgs a) {
         a.quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
         double4_32a x0 = a.x_last[i];
         double dx = x.x - x0.x, dy = x.y - x0.y, dz = x.z - x0.z;
-        dx -= rp.L[0] * rint(dx / rp.L[0]);
-        dy -= rp.L[1] * rint(dy / rp.L[1]);
-        if (a.dim == 3) dz -= rp.L[2] * rint(dz / rp.L[2]); else dz = 0.0;
+        dx -= rp.L[0] * rint(dx * rp.inv_L[0]);
+        dy -= rp.L[1] * rint(dy * rp.inv_L[1]);
+        if (a.dim == 3) dz -= rp.L[2] * rint(dz * rp.inv_L[2]); else dz = 0.0;
         dmax = fmaxf(dmax, (float)(dx * dx + dy * dy + dz * dz));
         a.delta[i] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
     }
@@ -111,9 +135,8 @@ __global__ void k_first_half(const StepArgs a) {
 __device__ __forceinline__ double kinetic_of(const ShapeDev &sh, const double4_32a &v,
                                              const double4_32a &L) {
     double k = 0.5 * sh.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
-    if (sh.inertia[0] > 0.0) k += 0.5 * L.x * L.x / sh.inertia[0];
-    if (sh.inertia[1] > 0.0) k += 0.5 * L.y * L.y / sh.inertia[1];
-    if (sh.inertia[2] > 0.0) k += 0.5 * L.z * L.z / sh.inertia[2];
+    k += 0.5 * (L.x * L.x * sh.inv_inertia[0] + L.y * L.y * sh.inv_inertia[1] +
+                L.z * L.z * sh.inv_inertia[2]);
     return k;
 }
 
@@ -121,7 +144,7 @@ __global__ void k_second_half(const StepArgs a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const ShapeDev &sh = a.shapes[a.shape[i]];
         double4_32a v = a.vel[i], L = a.angmom[i], F = a.force[i], Tq = a.torque[i];
-        const double h = 0.5 * a.dt / sh.mass;
+        const double h = 0.5 * a.dt * sh.inv_mass;
         v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
         L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
         a.vel[i] = v;
@@ -230,9 +253,9 @@ __global__ void k_prepare(int n, int dim, double4_32a *pos, double4_32a *quat, f
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Rep &rp = reps[rep[i]];
         double4_32a x = pos[i];
-        x.x = wrap(x.x, rp.L[0]);
-        x.y = wrap(x.y, rp.L[1]);
-        x.z = dim == 3 ? wrap(x.z, rp.L[2]) : 0.0;
+        x.x = wrap(x.x, rp.L[0], rp.inv_L[0]);
+        x.y = wrap(x.y, rp.L[1], rp.inv_L[1]);
+        x.z = dim == 3 ? wrap(x.z, rp.L[2], rp.inv_L[2]) : 0.0;
         pos[i] = x;
         double4_32a q = quat[i];
         double nq = sqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);

@@ -55,9 +55,9 @@ __device__ __forceinline__ void consider(const NlistArgs &a, int i, int j, doubl
     if (j == i) return;
     double4_32a xj = a.pos[j];
     double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-    dx -= rp.L[0] * rint(dx / rp.L[0]);
-    dy -= rp.L[1] * rint(dy / rp.L[1]);
-    if (a.dim == 3) dz -= rp.L[2] * rint(dz / rp.L[2]); else dz = 0.0;
+    dx -= rp.L[0] * rint(dx * rp.inv_L[0]);
+    dy -= rp.L[1] * rint(dy * rp.inv_L[1]);
+    if (a.dim == 3) dz -= rp.L[2] * rint(dz * rp.inv_L[2]); else dz = 0.0;
     const ShapeDev &sj = a.shapes[a.shape[j]];
     double sig = a.sigma > 0.0 ? a.sigma : rnd_i + sj.rounding;
     double lim = Ri + (double)sj.R + WCA_CUT * sig + a.skin;

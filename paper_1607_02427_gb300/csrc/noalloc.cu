@@ -120,6 +120,7 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     Rep rp = {};
     for (int a = 0; a < 3; ++a) {
         rp.L[a] = a < dim ? box[a] : 1.0;
+        rp.inv_L[a] = 1.0 / rp.L[a];
         rp.nc[a] = 1;
         if (a < dim && !(rp.L[a] >= 2.0 * range))
             return fail(DEM_ERR_BOX, "dem_forces_noalloc: box edge below twice the interaction range");

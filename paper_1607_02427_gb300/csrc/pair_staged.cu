@@ -1,0 +1,690 @@
+// pair_staged.cu -- STAGED decomposition of the pair kernel (Eq. DEM,
+// Eq. DEM_2D; Section "Algorithm" of arXiv:1607.02427 re-designed for
+// sm_103a).
+//
+// One warp owns 32 particles at a time and streams their feature-pair work
+// through per-warp shared-memory rings, so that every stage runs with full
+// warps on uniform work instead of one lane walking all features of a pair:
+//
+//   scan     lanes take the 32 particles' list entries: range test, pair
+//            setup (M, dl, separating-axis test, feature masks); the pairs
+//            that pass are appended to the pair ring in ballot order.
+//   batch    32 queued pairs at a time:
+//     sphere   one-vertex pairs (sphere / disk limit): the one central term.
+//     vertex   lanes take (pair, vertex) items of both orders (j's masked
+//              vertices against i's faces, i's against j's): the vertex is
+//              mapped into the other body's frame once, reach-tested, then
+//              the warp walks the items' face masks in step; 3D: a plane test
+//              per (vertex, face), survivors queued; 2D: the edge
+//              bounding-sphere test and the point-segment nearest point.
+//     face     queued (vertex, face) candidates, 32 at a time: in-plane
+//              tests and the nearest point on the face.
+//     edge     lanes take (pair, edge of j) items: the edge is mapped into
+//              i's frame once and reach-tested, then the warp walks i's
+//              masked edges in step: bounding-sphere and carrier-line tests,
+//              survivors queued.
+//     segment  queued edge pairs, 32 at a time: segment-segment nearest
+//              points.
+//   terms    queued terms (r < r_cut), 32 at a time: WCA force, torque,
+//            energy and virial in i's frame; terms of the same owner are
+//            added by the owner's lane in queue order (shuffles), so each
+//            particle's sum has a fixed order.
+//
+// The arithmetic of every test and term is that of eval_pair (shared
+// helpers in pair_kernels.cuh / pair_common.cuh); only the work order
+// differs.  Rings hold at most 63 entries (a round adds at most 32 and a
+// stage runs as soon as 32 are queued).
+#include "pair_kernels.cuh"
+
+namespace dem {
+namespace {
+
+constexpr int RING = 64;
+constexpr int SBLOCK = 128;
+
+template <class T> struct SPair {      // a queued active pair
+    T m[9];                            // M = R_i^T R_j
+    T dl[3];                           // x_j - x_i in i's frame
+    T rc, sig2;
+    int gj, owner;                     // j's geometry; the owner's lane
+    unsigned vim, vjm, eim, ejm, fim, fjm;
+};
+template <class T> struct SInfo {      // one particle of the warp
+    T r[9];                            // R_i
+    T x[3];                            // FP32: delta_i; FP64: position
+    T rnd;
+    int geom, rep, pad;
+};
+template <class T> struct VFItem {     // (vertex, face) after the plane test
+    T p[3];                            // the vertex in the face owner's frame
+    T h;                               // its signed plane distance
+    int code;                          // pair | side << 5 | vertex << 6 | face << 11
+};
+template <class T> struct EEItem {     // edge pair after the sphere and line tests
+    T a2[3], d2[3];                    // j's edge in i's frame
+    int code;                          // pair | edge of i << 5 | edge of j << 10
+};
+template <class T> struct TermRec {    // a term with r < r_cut
+    T q[3];                            // the point on i's feature (i's frame)
+    T rv[3];                           // i's point minus j's point (i's frame)
+    T r2;
+    int pair;
+};
+template <class T> struct StagedSmem {
+    SInfo<T> info[32];
+    SPair<T> pr[RING];
+    union {
+        VFItem<T> vf[RING];
+        EEItem<T> ee[RING];
+    } fq;
+    TermRec<T> tq[RING];
+    int offs[32];                      // list offsets of the 32 particles
+    int boffs[32];                     // item offsets of the batch's pairs
+    unsigned gmask[32];                // per owner: lanes holding its terms
+};
+
+// Position of the n-th (from 0) set bit of m (n < popc(m)).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+    int pos = 0;
+    int c = __popc(m & 0xffffu);
+    if (n >= c) { n -= c; m >>= 16; pos += 16; }
+    c = __popc(m & 0xffu);
+    if (n >= c) { n -= c; m >>= 8; pos += 8; }
+    c = __popc(m & 0xfu);
+    if (n >= c) { n -= c; m >>= 4; pos += 4; }
+    c = __popc(m & 0x3u);
+    if (n >= c) { n -= c; m >>= 2; pos += 2; }
+    if (n >= (int)(m & 1u)) pos += 1;
+    return pos;
+}
+
+// Ring slot of this lane's entry when the lanes in m append at tail.
+__device__ __forceinline__ int ring_slot(unsigned m, int lane, int tail) {
+    return (tail + __popc(m & ((1u << lane) - 1u))) & (RING - 1);
+}
+
+template <class T> __device__ __forceinline__ M33<T> pair_m(const SPair<T> &P) {
+    M33<T> M;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M.m[r][c] = P.m[3 * r + c];
+    return M;
+}
+
+// Every stage has one call site (code size: the stages of 16 warps per SM
+// must share the instruction cache).  batch() is a loop whose body does one
+// action per turn: consumers first, so that no ring reaches 64 entries,
+// then one step of the current producer.
+template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
+    using R4 = typename R4T<T>::type;
+    const PairArgs &a;
+    const R4 *tab;
+    const Geom *geo;
+    const int *itab;
+    StagedSmem<T> &ws;
+    const int lane;
+    const T eps, par_eps;
+    PathCount pc;
+    SumSink<T, COMP> S;                // this lane's particle
+    int ph = 0, np = 0;                // pair ring: head, queued pairs
+    int fh = 0, ft = 0;                // feature ring (vertex-face or edge items)
+    int th = 0, tt = 0;                // term ring
+    // this lane's item: vertex phase (pair, side, vertex) with va = the
+    // vertex in the other body's frame; edge phase (pair, j's edge) with
+    // va, vb, vc = its start, direction and centre in i's frame
+    unsigned cm = 0u;                  // features of the other shape left to test
+    int cp = 0, cside = 0, cidx = 0, coff = 0;
+    V3<T> va, vb, vc;
+    T crb = T(0), crc = T(0);          // j's edge radius; r_cut
+
+    __device__ __forceinline__ Staged(const PairArgs &a_, const R4 *tab_, const Geom *geo_,
+                                      const int *itab_, StagedSmem<T> &ws_, int lane_)
+        : a(a_), tab(tab_), geo(geo_), itab(itab_), ws(ws_), lane(lane_), eps((T)a_.eps),
+          par_eps((T)a_.par_eps) {
+        if constexpr (COUNT)
+            for (int k = 0; k < NCOUNT; ++k) pc.v[k] = 0;
+    }
+
+    __device__ __forceinline__ SPair<T> &pair(int p) { return ws.pr[(ph + p) & (RING - 1)]; }
+    __device__ __forceinline__ const Geom &geom_i(const SPair<T> &P) {
+        return geo[ws.info[P.owner].geom];
+    }
+    __device__ __forceinline__ static bool spheres(const Geom &gi, const Geom &gj) {
+        return gi.nv == 1 && gj.nv == 1;
+    }
+
+    // ---- ring appends (the caller's loop consumes) ----
+    __device__ __forceinline__ void push_term(bool ok, V3<T> q, V3<T> rv, T r2, int p) {
+        const unsigned m = __ballot_sync(FULL, ok);
+        if (ok) {
+            TermRec<T> &t = ws.tq[ring_slot(m, lane, tt)];
+            t.q[0] = q.x; t.q[1] = q.y; t.q[2] = q.z;
+            t.rv[0] = rv.x; t.rv[1] = rv.y; t.rv[2] = rv.z;
+            t.r2 = r2;
+            t.pair = p;
+        }
+        tt += __popc(m);
+        __syncwarp();
+    }
+    __device__ __forceinline__ void push_face(bool ok, V3<T> pv, T h, int code) {
+        const unsigned m = __ballot_sync(FULL, ok);
+        if (ok) {
+            VFItem<T> &it = ws.fq.vf[ring_slot(m, lane, ft)];
+            it.p[0] = pv.x; it.p[1] = pv.y; it.p[2] = pv.z;
+            it.h = h;
+            it.code = code;
+        }
+        ft += __popc(m);
+        __syncwarp();
+    }
+    __device__ __forceinline__ void push_edge(bool ok, V3<T> A2, V3<T> D2, int code) {
+        const unsigned m = __ballot_sync(FULL, ok);
+        if (ok) {
+            EEItem<T> &it = ws.fq.ee[ring_slot(m, lane, ft)];
+            it.a2[0] = A2.x; it.a2[1] = A2.y; it.a2[2] = A2.z;
+            it.d2[0] = D2.x; it.d2[1] = D2.y; it.d2[2] = D2.z;
+            it.code = code;
+        }
+        ft += __popc(m);
+        __syncwarp();
+    }
+
+    // ---- consumers ----
+    // n queued terms: values in i's frame, added by the owners' lanes in
+    // queue order
+    __device__ __forceinline__ void run_terms(int n) {
+        T v[13];
+        const bool has = lane < n;
+        int owner = 32 + lane;                    // lanes without a term: distinct keys
+        if (has) {
+            const TermRec<T> &t = ws.tq[(th + lane) & (RING - 1)];
+            const SPair<T> &P = pair(t.pair);
+            owner = P.owner;
+            T U;
+            const T wf = wca_factor(t.r2, P.sig2, eps, &U);
+            term_values(v3<T>(t.q[0], t.q[1], t.q[2]),
+                        v3<T>(t.rv[0], t.rv[1], t.rv[2]) * wf,
+                        v3<T>(P.dl[0], P.dl[1], P.dl[2]), U, v);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 13; ++k) v[k] = T(0);
+        }
+        th += n;
+        const unsigned grp = __match_any_sync(FULL, owner);
+        if (has && lane == __ffs(grp) - 1) ws.gmask[owner] = grp;
+        __syncwarp();
+        unsigned rest = ws.gmask[lane];
+        const int cnt = __popc(rest);
+        const int rounds = (int)__reduce_max_sync(FULL, (unsigned)cnt);
+        for (int r = 0; r < rounds; ++r) {
+            const int src = rest ? __ffs(rest) - 1 : lane;
+            rest &= rest - 1u;
+            T x[13];
+#pragma unroll
+            for (int k = 0; k < 13; ++k) x[k] = __shfl_sync(FULL, v[k], src);
+            if (r < cnt) S.add(x);
+        }
+        ws.gmask[lane] = 0u;
+        __syncwarp();
+    }
+
+    // n queued (vertex, face) candidates: nearest point on the face
+    __device__ __forceinline__ void run_faces(int n) {
+        bool ok = false;
+        V3<T> q = v3<T>(0, 0, 0), rv = q;
+        T r2 = T(0);
+        int p = 0;
+        if (lane < n) {
+            const VFItem<T> it = ws.fq.vf[(fh + lane) & (RING - 1)];
+            p = it.code & 31;
+            const int side = (it.code >> 5) & 1, vtx = (it.code >> 6) & 31, f = (it.code >> 11) & 31;
+            const SPair<T> &P = pair(p);
+            const Geom &gi = geom_i(P);
+            const Geom &gf = side ? geo[P.gj] : gi;
+            const V3<T> pv = v3<T>(it.p[0], it.p[1], it.p[2]);
+            V3<T> qq;
+            T rr;
+            face_rest<T, COUNT>(tab, itab, gf.fi_off + 2 * f, tab[gf.f_off + f], pv, it.h, &qq, &rr,
+                                &pc);
+            if (rr < P.rc * P.rc) {
+                ok = true;
+                r2 = rr;
+                bump<COUNT>(&pc, C_TERMS);
+                if (side == 0) {
+                    q = qq;
+                    rv = qq - pv;
+                } else {
+                    bump<COUNT>(&pc, C_JTERMS);
+                    q = xyz<T>(tab[gi.v_off + vtx]);
+                    rv = mul(pair_m(P), pv - qq);
+                }
+            }
+        }
+        fh += n;
+        __syncwarp();
+        push_term(ok, q, rv, r2, p);
+    }
+
+    // n queued edge pairs: segment-segment nearest points
+    __device__ __forceinline__ void run_segments(int n) {
+        bool ok = false;
+        V3<T> q = v3<T>(0, 0, 0), rv = q;
+        T r2 = T(0);
+        int p = 0;
+        if (lane < n) {
+            const EEItem<T> it = ws.fq.ee[(fh + lane) & (RING - 1)];
+            p = it.code & 31;
+            const int ea = (it.code >> 5) & 31, eb = (it.code >> 10) & 31;
+            const SPair<T> &P = pair(p);
+            const Geom &gi = geom_i(P), &gj = geo[P.gj];
+            const R4 aa = tab[gi.e_off + 2 * ea], ad = tab[gi.e_off + 2 * ea + 1];
+            const T inv_c = tab[gj.e_off + 2 * eb + 1].w;
+            V3<T> P1, P2;
+            bump<COUNT>(&pc, C_SEGSEG);
+            segment_nearest<T>(xyz<T>(aa), xyz<T>(ad), ad.w, v3<T>(it.a2[0], it.a2[1], it.a2[2]),
+                               v3<T>(it.d2[0], it.d2[1], it.d2[2]), inv_c, par_eps, &P1, &P2);
+            const V3<T> d = P1 - P2;
+            const T rr = dot(d, d);
+            if (rr < P.rc * P.rc) {
+                ok = true;
+                bump<COUNT>(&pc, C_TERMS);
+                q = P1;
+                rv = d;
+                r2 = rr;
+            }
+        }
+        fh += n;
+        __syncwarp();
+        push_term(ok, q, rv, r2, p);
+    }
+
+    // ---- producers ----
+    // one-vertex pairs (sphere / disk limit): the one central term
+    __device__ __forceinline__ void sphere_terms(int nb) {
+        bool ok = false;
+        V3<T> q = v3<T>(0, 0, 0), rv = q;
+        T r2 = T(0);
+        if (lane < nb) {
+            const SPair<T> &P = pair(lane);
+            const Geom &gi = geom_i(P), &gj = geo[P.gj];
+            if (spheres(gi, gj)) {
+                q = xyz<T>(tab[gi.v_off]);
+                rv = q - (v3<T>(P.dl[0], P.dl[1], P.dl[2]) + mul(pair_m(P), xyz<T>(tab[gj.v_off])));
+                r2 = dot(rv, rv);
+                ok = r2 < P.rc * P.rc;
+                if (ok) bump<COUNT>(&pc, C_TERMS);
+            }
+        }
+        push_term(ok, q, rv, r2, lane);
+    }
+
+    // item offsets of the batch's pairs for a phase; returns the item count
+    __device__ __forceinline__ int phase_items(int nb, bool edges) {
+        int c = 0;
+        if (lane < nb) {
+            const SPair<T> &P = pair(lane);
+            const Geom &gi = geom_i(P), &gj = geo[P.gj];
+            if (!spheres(gi, gj)) {
+                if (edges) {
+                    if (P.eim) c = __popc(P.ejm);
+                } else {
+                    const unsigned oA = DIM == 3 ? P.fim : P.eim, oB = DIM == 3 ? P.fjm : P.ejm;
+                    c = (oA ? __popc(P.vjm) : 0) + (oB ? __popc(P.vim) : 0);
+                }
+            }
+        }
+        int total;
+        ws.boffs[lane] = warp_excl_scan(c, lane, &total);
+        __syncwarp();
+        return total;
+    }
+
+    // take vertex item t (t < total): map the vertex, reach test
+    __device__ __forceinline__ void load_vertex_item(int t, int total, int nb) {
+        cm = 0u;
+        if (t >= total) return;
+        cp = owner_of(ws.boffs, nb, t);
+        const int k = t - ws.boffs[cp];
+        const SPair<T> &P = pair(cp);
+        const Geom &gi = geom_i(P), &gj = geo[P.gj];
+        const unsigned oA = DIM == 3 ? P.fim : P.eim;
+        const int nA = oA ? __popc(P.vjm) : 0;
+        const M33<T> M = pair_m(P);
+        const V3<T> dl = v3<T>(P.dl[0], P.dl[1], P.dl[2]);
+        crc = P.rc;
+        T reach;
+        unsigned m;
+        if (k < nA) {
+            cside = 0;
+            cidx = nth_set_bit(P.vjm, k);
+            va = dl + mul(M, xyz<T>(tab[gj.v_off + cidx]));
+            reach = T(gi.R) + crc;
+            m = oA;
+            coff = DIM == 3 ? gi.f_off : gi.e_off;
+        } else {
+            cside = 1;
+            cidx = nth_set_bit(P.vim, k - nA);
+            va = mul_t(M, xyz<T>(tab[gi.v_off + cidx]) - dl);
+            reach = T(gj.R) + crc;
+            m = DIM == 3 ? P.fjm : P.ejm;
+            coff = DIM == 3 ? gj.f_off : gj.e_off;
+        }
+        bump<COUNT>(&pc, C_VTX);
+        if (dot(va, va) < reach * reach) cm = m;
+    }
+
+    // one face (3D: plane test, survivors queued) or edge (2D: sphere test
+    // and point-segment nearest point, terms queued) of each lane's item
+    __device__ __forceinline__ void vertex_step() {
+        bool ok = false;
+        int f = 0;
+        if constexpr (DIM == 3) {
+            T h = T(0);
+            if (cm) {
+                f = __ffs(cm) - 1;
+                cm &= cm - 1u;
+                const R4 nf = tab[coff + f];
+                h = nf.x * va.x + nf.y * va.y + nf.z * va.z - nf.w;
+                bump<COUNT>(&pc, C_PLANE);
+                ok = fabs(h) < crc;
+            }
+            push_face(ok, va, h, cp | (cside << 5) | (cidx << 6) | (f << 11));
+        } else {
+            V3<T> q = v3<T>(0, 0, 0), rv = q;
+            T r2 = T(0);
+            if (cm) {
+                f = __ffs(cm) - 1;
+                cm &= cm - 1u;
+                const R4 ea = tab[coff + 2 * f], ed = tab[coff + 2 * f + 1];
+                const V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
+                const V3<T> c = A + D * T(0.5) - va;
+                const T lim = ea.w + crc;
+                bump<COUNT>(&pc, C_SPHERE);
+                if (dot(c, c) < lim * lim) {
+                    bump<COUNT>(&pc, C_PTSEG);
+                    const V3<T> qq = A + D * clamp01(dot(va - A, D) * ed.w);
+                    const V3<T> d = va - qq;
+                    r2 = dot(d, d);
+                    if (r2 < crc * crc) {
+                        ok = true;
+                        bump<COUNT>(&pc, C_TERMS);
+                        if (cside == 0) {
+                            q = qq;
+                            rv = qq - va;
+                        } else {
+                            bump<COUNT>(&pc, C_JTERMS);
+                            const SPair<T> &P = pair(cp);
+                            q = xyz<T>(tab[geom_i(P).v_off + cidx]);
+                            rv = mul(pair_m(P), d);
+                        }
+                    }
+                }
+            }
+            push_term(ok, q, rv, r2, cp);
+        }
+    }
+
+    // take edge item t: j's edge into i's frame, reach test
+    __device__ __forceinline__ void load_edge_item(int t, int total, int nb) {
+        cm = 0u;
+        if (t >= total) return;
+        cp = owner_of(ws.boffs, nb, t);
+        const SPair<T> &P = pair(cp);
+        const Geom &gi = geom_i(P), &gj = geo[P.gj];
+        cidx = nth_set_bit(P.ejm, t - ws.boffs[cp]);
+        const R4 ba = tab[gj.e_off + 2 * cidx], bd = tab[gj.e_off + 2 * cidx + 1];
+        const M33<T> M = pair_m(P);
+        va = v3<T>(P.dl[0], P.dl[1], P.dl[2]) + mul(M, xyz<T>(ba));
+        vb = mul(M, xyz<T>(bd));
+        vc = va + vb * T(0.5);
+        crb = ba.w;
+        crc = P.rc;
+        coff = gi.e_off;
+        const T reach = T(gi.R) + crc + crb;
+        bump<COUNT>(&pc, C_EDGE);
+        if (dot(vc, vc) < reach * reach) cm = P.eim;
+    }
+
+    // one edge of i against each lane's j edge: sphere and carrier-line
+    // tests, survivors queued
+    __device__ __forceinline__ void edge_step() {
+        bool ok = false;
+        int ea = 0;
+        if (cm) {
+            ea = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            const R4 aa = tab[coff + 2 * ea], ad = tab[coff + 2 * ea + 1];
+            const V3<T> A1 = xyz<T>(aa), D1 = xyz<T>(ad);
+            const V3<T> dc = A1 + D1 * T(0.5) - vc;
+            const T lim = aa.w + crb + crc;
+            bump<COUNT>(&pc, C_SPHERE);
+            if (dot(dc, dc) < lim * lim) {
+                const V3<T> nrm = cross(D1, vb);
+                const T n2 = dot(nrm, nrm);
+                const T sep = dot(va - A1, nrm);
+                bump<COUNT>(&pc, C_LINE);
+                ok = !(sep * sep >= crc * crc * n2 && n2 > par_eps * dot(D1, D1) * dot(vb, vb));
+            }
+        }
+        push_edge(ok, va, vb, cp | (ea << 5) | (cidx << 10));
+    }
+
+    // ---- one batch of nb queued pairs ----
+    __device__ __forceinline__ void batch(int nb) {
+        // phase 0: sphere terms; 1: vertex items; 2: edge items; 3: done
+        int phase = 0, t0 = 0, total = 0;
+        cm = 0u;
+        for (;;) {
+            if (tt - th >= 32 || (phase == 3 && tt > th)) {
+                run_terms(tt - th < 32 ? tt - th : 32);
+                continue;
+            }
+            const bool produced = t0 >= total && !__any_sync(FULL, cm);
+            if (ft - fh >= 32 || (produced && ft > fh)) {
+                const int n = ft - fh < 32 ? ft - fh : 32;
+                if (DIM == 3 && phase == 2) run_segments(n);
+                else run_faces(n);
+                continue;
+            }
+            if (phase == 3) break;
+            if (produced) {
+                ++phase;
+                if (phase == 1) {
+                    sphere_terms(nb);
+                    total = phase_items(nb, false);
+                } else if (phase == 2) {
+                    total = DIM == 3 ? phase_items(nb, true) : 0;
+                } else {
+                    total = 0;
+                }
+                t0 = 0;
+                continue;
+            }
+            if (!__any_sync(FULL, cm)) {
+                if (phase == 1) load_vertex_item(t0 + lane, total, nb);
+                else load_edge_item(t0 + lane, total, nb);
+                t0 += 32;
+                continue;
+            }
+            if (DIM == 3 && phase == 2) edge_step();
+            else vertex_step();
+        }
+        ph = (ph + nb) & (RING - 1);
+        np -= nb;
+    }
+};
+
+template <class T, bool COMP, int DIM, bool COUNT>
+__global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
+    k_pair_staged(const PairArgs a) {
+    using R4 = typename R4T<T>::type;
+    extern __shared__ __align__(32) unsigned char smem[];
+    R4 *tab = reinterpret_cast<R4 *>(smem);
+    Geom *geo = reinterpret_cast<Geom *>(tab + a.table_len);
+    int *itab = reinterpret_cast<int *>(geo + a.n_geoms);
+    size_t tb = (size_t)a.table_len * sizeof(R4) + sizeof(Geom) * a.n_geoms +
+                sizeof(int) * a.itable_len;
+    tb = (tb + 127) & ~(size_t)127;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    StagedSmem<T> &ws = reinterpret_cast<StagedSmem<T> *>(smem + tb)[w];
+    stage_tables<T>(a, tab, geo, itab);
+    ws.gmask[lane] = 0u;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !COUNT) {
+        a.status->maxdisp2 = 0u;
+        a.status->rebuild = 0;
+    }
+    const T sig_all = a.sigma > 0.0 ? (T)a.sigma : T(0);
+    Staged<T, COMP, DIM, COUNT> st(a, tab, geo, itab, ws, lane);
+    const int nwarps = gridDim.x * wpb;
+    for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
+        const int i_me = base + lane;
+        const bool mine = i_me < a.n;
+        int nn_me = 0;
+        if (mine) {
+            const ShapeDev &shi = a.shapes[a.shape[i_me]];
+            const M33<T> R = orientation<T>(a, i_me);
+            SInfo<T> &pi = ws.info[lane];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) pi.r[3 * r + c] = R.m[r][c];
+            if constexpr (std::is_same<T, float>::value) {
+                const float4 dd = a.delta[i_me];
+                pi.x[0] = dd.x; pi.x[1] = dd.y; pi.x[2] = dd.z;
+                pi.rnd = shi.rounding_f;
+            } else {
+                const double4_32a xx = a.pos[i_me];
+                pi.x[0] = xx.x; pi.x[1] = xx.y; pi.x[2] = xx.z;
+                pi.rnd = shi.rounding;
+            }
+            pi.geom = shi.geom;
+            pi.rep = a.rep[i_me];
+            nn_me = a.nn[i_me];
+        }
+        st.S.zero();
+        int total;
+        ws.offs[lane] = warp_excl_scan(nn_me, lane, &total);
+        __syncwarp();
+        // one batch call site: batches run when 32 pairs are queued and at
+        // the end of the particles' lists
+        int t0 = 0;
+        for (;;) {
+            if (st.np >= 32 || (t0 >= total && st.np > 0)) {
+                st.batch(st.np < 32 ? st.np : 32);
+                continue;
+            }
+            if (t0 >= total) break;
+            const int t = t0 + lane;
+            t0 += 32;
+            bool active = false;
+            PairWork<T> wk;
+            int pl = 0;
+            if (t < total) {
+                pl = owner_of(ws.offs, 32, t);
+                const int k = t - ws.offs[pl];
+                const int i = base + pl;
+                const SInfo<T> &pi = ws.info[pl];
+                const Geom &gi = geo[pi.geom];
+                Owner<T> own;
+                own.rp = &a.reps[pi.rep];
+                own.R = (T)gi.R;
+                own.rnd = pi.rnd;
+                own.sig_all = sig_all;
+                own.geom = pi.geom;
+                if constexpr (std::is_same<T, float>::value)
+                    own.delta = make_float4(pi.x[0], pi.x[1], pi.x[2], 0.f);
+                else
+                    own.x = make_double4_32a(pi.x[0], pi.x[1], pi.x[2], 0.0);
+                const float4 e = a.nlist[(size_t)k * a.n + i];
+                bump<COUNT>(&st.pc, C_NEIGH);
+                PairGeom<T> pg;
+                int j;
+                if (in_range<T>(a, e, own, &j, &pg)) {
+                    const Geom &gj = geo[pg.gj];
+                    bump<COUNT>(&st.pc, C_PAIRS);
+                    bump<COUNT>(&st.pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
+                    M33<T> Ri;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Ri.m[r][c] = pi.r[3 * r + c];
+                    wk.M = mul_tn(Ri, orientation<T>(a, j));
+                    wk.dl = mul_t(Ri, pg.d);
+                    wk.rc = (T)WCA_CUT * pg.sig;
+                    wk.sig2 = pg.sig * pg.sig;
+                    wk.gj = pg.gj;
+                    active = pair_setup<T, COUNT>(tab, itab, gi, gj, &wk, &st.pc);
+                    if (active) bump<COUNT>(&st.pc, C_ACTIVE);
+                }
+            }
+            const unsigned m = __ballot_sync(FULL, active);
+            if (active) {
+                SPair<T> &P = ws.pr[ring_slot(m, lane, st.ph + st.np)];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) P.m[3 * r + c] = wk.M.m[r][c];
+                P.dl[0] = wk.dl.x; P.dl[1] = wk.dl.y; P.dl[2] = wk.dl.z;
+                P.rc = wk.rc;
+                P.sig2 = wk.sig2;
+                P.gj = wk.gj;
+                P.owner = pl;
+                P.vim = wk.vim; P.vjm = wk.vjm; P.eim = wk.eim; P.ejm = wk.ejm;
+                P.fim = wk.fim; P.fjm = wk.fjm;
+            }
+            st.np += __popc(m);
+            __syncwarp();
+        }
+        if (mine) {
+            const SInfo<T> &pi = ws.info[lane];
+            M33<T> R;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) R.m[r][c] = pi.r[3 * r + c];
+            finish_particle(a, i_me, st.S, R);
+        }
+        __syncwarp();
+    }
+    if constexpr (COUNT)
+        for (int k = 0; k < NCOUNT; ++k)
+            if (st.pc.v[k]) atomicAdd(a.counters + k, (unsigned long long)st.pc.v[k]);
+}
+
+template <class T, bool COMP, int DIM>
+cudaError_t launch_dim(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
+    const size_t smem = ((smem_tables + 127) & ~(size_t)127) + (SBLOCK / 32) * sizeof(StagedSmem<T>);
+    auto launch = [&](auto kernel) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const long long need = (a.n + SBLOCK - 1) / SBLOCK;   // 32 particles per warp
+        const long long cap = (long long)blocks_per_sm(kernel, SBLOCK, smem) * sm_count();
+        int grid = (int)(need < cap ? need : cap);
+        if (grid < 1) grid = 1;
+        kernel<<<grid, SBLOCK, smem, s>>>(a);
+    };
+    if (count) launch(k_pair_staged<T, COMP, DIM, true>);
+    else launch(k_pair_staged<T, COMP, DIM, false>);
+    return cudaGetLastError();
+}
+
+template <class T, bool COMP>
+cudaError_t launch_prec(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
+    if (a.dim == 2) return launch_dim<T, COMP, 2>(a, count, smem_tables, s);
+    return launch_dim<T, COMP, 3>(a, count, smem_tables, s);
+}
+
+}  // namespace
+
+cudaError_t launch_pair_staged(const PairArgs &a, int precision, bool count, size_t smem_tables,
+                               cudaStream_t s) {
+    switch (precision) {
+        case DEM_FP64: return launch_prec<double, false>(a, count, smem_tables, s);
+        case DEM_FP32: return launch_prec<float, false>(a, count, smem_tables, s);
+        default: return launch_prec<float, true>(a, count, smem_tables, s);
+    }
+}
+
+}  // namespace dem

@@ -64,16 +64,17 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("decomp", [1, 3], ids=["thread", "staged"])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-9), (2, 1e-4), (1, 1e-4)],
                          ids=["fp64", "fp32c", "fp32"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_trajectory_matches_oracle(dem, name, precision, tol):
+def test_trajectory_matches_oracle(dem, name, precision, tol, decomp):
     mk, ens = CASES[name]
     s = mk()
     n, dt = 100, 1e-3
     ref, tr = oracle.run(s, n, dt, ensemble=ens, kT=1.0, tau=0.5)
     assert tr[0, :, 2].max() > 0.1, "the run must have interactions"
-    with dem.DEM(s, precision) as d:
+    with dem.DEM(s, precision, decomp=decomp) as d:
         d.step(n, dt, dem.DEM_NVT if ens == "nvt" else dem.DEM_NVE, kT=1.0, tau_T=0.5)
         st = d.state()
         U, K, H = d.energy()
