@@ -302,13 +302,20 @@ void build_tables(const std::vector<HostGeom> &geoms, const std::vector<HostShap
             }
         }
         G.nfe = nfe;
-        // vertex membership masks: bit k set when vertex k bounds the edge/face
-        G.em_off = (int)t->itab.size();
-        for (auto &e : g.edges) t->itab.push_back((int)((1u << e.first) | (1u << e.second)));
-        G.fm_off = (int)t->itab.size();
-        for (auto &loop : g.faces) {
+        // incidence masks: per vertex, bit k set when the vertex bounds edge / face k
+        G.vem_off = (int)t->itab.size();
+        for (int v = 0; v < G.nv; ++v) {
             unsigned m = 0;
-            for (int v : loop) m |= 1u << v;
+            for (size_t k = 0; k < g.edges.size(); ++k)
+                if (g.edges[k].first == v || g.edges[k].second == v) m |= 1u << k;
+            t->itab.push_back((int)m);
+        }
+        G.vfm_off = (int)t->itab.size();
+        for (int v = 0; v < G.nv; ++v) {
+            unsigned m = 0;
+            for (size_t f = 0; f < g.faces.size(); ++f)
+                for (int u : g.faces[f])
+                    if (u == v) m |= 1u << f;
             t->itab.push_back((int)m);
         }
         t->geoms.push_back(G);

@@ -50,8 +50,8 @@ struct Geom {
     int v_off, e_off, f_off, fe_off;
     int fi_off;          // offset of this geometry's faces in the int table
     float R;             // circumradius of the inner shape
-    int em_off;          // int table: vertex-membership mask of each edge
-    int fm_off;          // int table: vertex-membership mask of each face
+    int vem_off;         // int table: per vertex, the mask of its edges
+    int vfm_off;         // int table: per vertex, the mask of its faces
 };
 
 struct ShapeDev {

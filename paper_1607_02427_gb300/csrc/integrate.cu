@@ -124,7 +124,7 @@ __global__ void k_first_half(const StepArgs a) {
         dy -= rp.L[1] * rint(dy * rp.inv_L[1]);
         if (a.dim == 3) dz -= rp.L[2] * rint(dz * rp.inv_L[2]); else dz = 0.0;
         dmax = fmaxf(dmax, (float)(dx * dx + dy * dy + dz * dz));
-        a.delta[i] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
+        a.delta[i] = make_float4((float)dx, (float)dy, (float)dz, __int_as_float(a.shape[i]));
     }
     // warp max, one atomic per warp (non-negative floats order like their bits)
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));

@@ -119,7 +119,7 @@ __global__ void k_nlist(const NlistArgs a) {
         }
         a.nn[i] = count;
         a.x_last[i] = xi;
-        a.delta[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.delta[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(a.shape[i]));   // w: shape index
     }
 }
 

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
             bump<COUNT>(&pc, C_PAIRS);
             bump<COUNT>(&pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
             PairWork<T> w;
-            w.M = mul_tn(Ri, orientation<T>(a, j));
+            w.M = mul_tn(Ri, orientation_j<T>(a, j, pg));
             w.dl = mul_t(Ri, pg.d);
             w.rc = (T)WCA_CUT * pg.sig;
             w.sig2 = pg.sig * pg.sig;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) Ri.m[r][c] = pi.r[3 * r + c];
-                    wk.M = mul_tn(Ri, orientation<T>(a, j));
+                    wk.M = mul_tn(Ri, orientation_j<T>(a, j, pg));
                     wk.dl = mul_t(Ri, pg.d);
                     wk.rc = (T)WCA_CUT * pg.sig;
                     wk.sig2 = pg.sig * pg.sig;

@@ -46,6 +46,7 @@ template <class T> struct PairGeom {
     V3<T> d;             // x_j - x_i (minimum image), world frame
     T sig;               // sigma_ij
     int gj;              // geometry of j
+    float4 qj;           // FP32 modes: j's orientation (loaded with its displacement)
 };
 
 // Bounding-sphere range test of list entry e of owner o.
@@ -54,9 +55,13 @@ __device__ __forceinline__ bool in_range(const PairArgs &a, const float4 &e, con
                                          int *jout, PairGeom<T> *pg) {
     const int j = __float_as_int(e.w);
     *jout = j;
-    const ShapeDev &shj = a.shapes[__ldg(a.shape + j)];
     if constexpr (std::is_same<T, float>::value) {
+        // one round of gathers: the displacement (w: shape index) and the
+        // orientation, which the pair setup needs when the test passes
         const float4 dj = a.delta[j];
+        pg->qj = a.quatf[j];
+        const ShapeDev &shj = a.shapes[__float_as_int(dj.w)];
+        pg->gj = shj.geom;
         const float dx = e.x + (dj.x - o.delta.x);
         const float dy = e.y + (dj.y - o.delta.y);
         const float dz = e.z + (dj.z - o.delta.z);
@@ -66,6 +71,8 @@ __device__ __forceinline__ bool in_range(const PairArgs &a, const float4 &e, con
         pg->d = v3<float>(dx, dy, dz);
         pg->sig = sig;
     } else {
+        const ShapeDev &shj = a.shapes[__ldg(a.shape + j)];
+        pg->gj = shj.geom;
         const double4_32a xj = a.pos[j];
         const Rep &rp = *o.rp;
         double d[3] = {xj.x - o.x.x, xj.y - o.x.y, a.dim == 3 ? xj.z - o.x.z : 0.0};
@@ -80,7 +87,6 @@ __device__ __forceinline__ bool in_range(const PairArgs &a, const float4 &e, con
         pg->d = v3<double>(d[0], d[1], d[2]);
         pg->sig = sig;
     }
-    pg->gj = shj.geom;
     return true;
 }
 
@@ -92,6 +98,13 @@ template <> __device__ __forceinline__ M33<float> orientation<float>(const PairA
 template <> __device__ __forceinline__ M33<double> orientation<double>(const PairArgs &a, int i) {
     double4_32a q = a.quat[i];
     return quat_mat<double>(q.x, q.y, q.z, q.w);
+}
+
+// Orientation of the neighbour of an in-range list entry.
+template <class T>
+__device__ __forceinline__ M33<T> orientation_j(const PairArgs &a, int j, const PairGeom<T> &pg) {
+    if constexpr (std::is_same<T, float>::value) return quat_mat<float>(pg.qj.x, pg.qj.y, pg.qj.z, pg.qj.w);
+    else return orientation<T>(a, j);
 }
 
 template <class T>
@@ -131,11 +144,11 @@ template <class T> struct PairWork {
 
 __device__ __forceinline__ unsigned low_bits(int n) { return n >= 32 ? FULL : ((1u << n) - 1u); }
 
-// Mask of the features (edges or faces) with a vertex in vmask.
-__device__ __forceinline__ unsigned feature_mask(const int *mtab, int n, unsigned vmask) {
+// Mask of the features (edges or faces) with a vertex in vmask, from the
+// per-vertex incidence masks inc.
+__device__ __forceinline__ unsigned feature_mask(const int *inc, unsigned vmask) {
     unsigned m = 0;
-    for (int k = 0; k < n; ++k)
-        if ((unsigned)mtab[k] & vmask) m |= 1u << k;
+    for (unsigned v = vmask; v; v &= v - 1u) m |= (unsigned)inc[__ffs(v) - 1];
     return m;
 }
 
@@ -178,10 +191,10 @@ __device__ __forceinline__ bool pair_setup(const typename R4T<T>::type *tab, con
         if (dot(xyz<T>(tab[gj.v_off + k]), uj) < hi_j) vjm |= 1u << k;
     w->vim = vim;
     w->vjm = vjm;
-    w->eim = feature_mask(itab + gi.em_off, gi.ne, vim);
-    w->ejm = feature_mask(itab + gj.em_off, gj.ne, vjm);
-    w->fim = feature_mask(itab + gi.fm_off, gi.nf, vim);
-    w->fjm = feature_mask(itab + gj.fm_off, gj.nf, vjm);
+    w->eim = feature_mask(itab + gi.vem_off, vim);
+    w->ejm = feature_mask(itab + gj.vem_off, vjm);
+    w->fim = feature_mask(itab + gi.vfm_off, vim);
+    w->fjm = feature_mask(itab + gj.vfm_off, vjm);
     return true;
 }
 

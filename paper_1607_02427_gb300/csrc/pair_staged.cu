@@ -42,33 +42,33 @@ namespace {
 constexpr int RING = 64;
 constexpr int SBLOCK = 128;
 
+// Records are rows of R4 (float4 / double4) so that they move with vector
+// shared-memory accesses.
 template <class T> struct SPair {      // a queued active pair
-    T m[9];                            // M = R_i^T R_j
-    T dl[3];                           // x_j - x_i in i's frame
+    typename R4T<T>::type row[3];      // (M[r][0], M[r][1], M[r][2], dl[r]): M = R_i^T R_j,
+                                       // dl = x_j - x_i in i's frame
     T rc, sig2;
     int gj, owner;                     // j's geometry; the owner's lane
-    unsigned vim, vjm, eim, ejm, fim, fjm;
+    unsigned vim, vjm, eim, ejm, fim, fjm, pad0, pad1;
 };
 template <class T> struct SInfo {      // one particle of the warp
-    T r[9];                            // R_i
-    T x[3];                            // FP32: delta_i; FP64: position
+    typename R4T<T>::type row[3];      // (R_i[r][0..2], x[r]); x: FP32 delta_i, FP64 position
     T rnd;
     int geom, rep, pad;
 };
 template <class T> struct VFItem {     // (vertex, face) after the plane test
-    T p[3];                            // the vertex in the face owner's frame
-    T h;                               // its signed plane distance
+    typename R4T<T>::type p;           // the vertex in the face owner's frame; w: its
+                                       // signed plane distance
     int code;                          // pair | side << 5 | vertex << 6 | face << 11
 };
 template <class T> struct EEItem {     // edge pair after the sphere and line tests
-    T a2[3], d2[3];                    // j's edge in i's frame
-    int code;                          // pair | edge of i << 5 | edge of j << 10
+    typename R4T<T>::type a2;          // j's edge start in i's frame; w: code =
+                                       // pair | edge of i << 5 | edge of j << 10
+    typename R4T<T>::type d2;          // j's edge direction in i's frame
 };
 template <class T> struct TermRec {    // a term with r < r_cut
-    T q[3];                            // the point on i's feature (i's frame)
-    T rv[3];                           // i's point minus j's point (i's frame)
-    T r2;
-    int pair;
+    typename R4T<T>::type q;           // the point on i's feature (i's frame); w: r^2
+    typename R4T<T>::type rv;          // i's point minus j's point (i's frame); w: pair
 };
 template <class T> struct StagedSmem {
     SInfo<T> info[32];
@@ -103,13 +103,29 @@ __device__ __forceinline__ int ring_slot(unsigned m, int lane, int tail) {
     return (tail + __popc(m & ((1u << lane) - 1u))) & (RING - 1);
 }
 
+// M and dl of a queued pair, or R_i and x of a particle (three vector loads).
+template <class R4, class T>
+__device__ __forceinline__ void load_rows(const R4 *row, M33<T> *M, V3<T> *x) {
+    const R4 r0 = row[0], r1 = row[1], r2 = row[2];
+    M->m[0][0] = r0.x; M->m[0][1] = r0.y; M->m[0][2] = r0.z;
+    M->m[1][0] = r1.x; M->m[1][1] = r1.y; M->m[1][2] = r1.z;
+    M->m[2][0] = r2.x; M->m[2][1] = r2.y; M->m[2][2] = r2.z;
+    *x = v3<T>(r0.w, r1.w, r2.w);
+}
+template <class R4, class T>
+__device__ __forceinline__ void store_rows(R4 *row, const M33<T> &M, V3<T> x) {
+    row[0] = {M.m[0][0], M.m[0][1], M.m[0][2], x.x};
+    row[1] = {M.m[1][0], M.m[1][1], M.m[1][2], x.y};
+    row[2] = {M.m[2][0], M.m[2][1], M.m[2][2], x.z};
+}
 template <class T> __device__ __forceinline__ M33<T> pair_m(const SPair<T> &P) {
     M33<T> M;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) M.m[r][c] = P.m[3 * r + c];
+    V3<T> dl;
+    load_rows(P.row, &M, &dl);
     return M;
+}
+template <class T> __device__ __forceinline__ V3<T> pair_dl(const SPair<T> &P) {
+    return v3<T>(P.row[0].w, P.row[1].w, P.row[2].w);
 }
 
 // Every stage has one call site (code size: the stages of 16 warps per SM
@@ -159,10 +175,8 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
         const unsigned m = __ballot_sync(FULL, ok);
         if (ok) {
             TermRec<T> &t = ws.tq[ring_slot(m, lane, tt)];
-            t.q[0] = q.x; t.q[1] = q.y; t.q[2] = q.z;
-            t.rv[0] = rv.x; t.rv[1] = rv.y; t.rv[2] = rv.z;
-            t.r2 = r2;
-            t.pair = p;
+            t.q = {q.x, q.y, q.z, r2};
+            t.rv = {rv.x, rv.y, rv.z, (T)p};
         }
         tt += __popc(m);
         __syncwarp();
@@ -171,8 +185,7 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
         const unsigned m = __ballot_sync(FULL, ok);
         if (ok) {
             VFItem<T> &it = ws.fq.vf[ring_slot(m, lane, ft)];
-            it.p[0] = pv.x; it.p[1] = pv.y; it.p[2] = pv.z;
-            it.h = h;
+            it.p = {pv.x, pv.y, pv.z, h};
             it.code = code;
         }
         ft += __popc(m);
@@ -182,9 +195,8 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
         const unsigned m = __ballot_sync(FULL, ok);
         if (ok) {
             EEItem<T> &it = ws.fq.ee[ring_slot(m, lane, ft)];
-            it.a2[0] = A2.x; it.a2[1] = A2.y; it.a2[2] = A2.z;
-            it.d2[0] = D2.x; it.d2[1] = D2.y; it.d2[2] = D2.z;
-            it.code = code;
+            it.a2 = {A2.x, A2.y, A2.z, (T)code};
+            it.d2 = {D2.x, D2.y, D2.z, T(0)};
         }
         ft += __popc(m);
         __syncwarp();
@@ -199,13 +211,12 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
         int owner = 32 + lane;                    // lanes without a term: distinct keys
         if (has) {
             const TermRec<T> &t = ws.tq[(th + lane) & (RING - 1)];
-            const SPair<T> &P = pair(t.pair);
+            const auto tq = t.q, trv = t.rv;
+            const SPair<T> &P = pair((int)trv.w);
             owner = P.owner;
             T U;
-            const T wf = wca_factor(t.r2, P.sig2, eps, &U);
-            term_values(v3<T>(t.q[0], t.q[1], t.q[2]),
-                        v3<T>(t.rv[0], t.rv[1], t.rv[2]) * wf,
-                        v3<T>(P.dl[0], P.dl[1], P.dl[2]), U, v);
+            const T wf = wca_factor(tq.w, P.sig2, eps, &U);
+            term_values(v3<T>(tq.x, tq.y, tq.z), v3<T>(trv.x, trv.y, trv.z) * wf, pair_dl(P), U, v);
         } else {
 #pragma unroll
             for (int k = 0; k < 13; ++k) v[k] = T(0);
@@ -236,16 +247,18 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
         T r2 = T(0);
         int p = 0;
         if (lane < n) {
-            const VFItem<T> it = ws.fq.vf[(fh + lane) & (RING - 1)];
-            p = it.code & 31;
-            const int side = (it.code >> 5) & 1, vtx = (it.code >> 6) & 31, f = (it.code >> 11) & 31;
+            const VFItem<T> &it = ws.fq.vf[(fh + lane) & (RING - 1)];
+            const auto ip = it.p;
+            const int code = it.code;
+            p = code & 31;
+            const int side = (code >> 5) & 1, vtx = (code >> 6) & 31, f = (code >> 11) & 31;
             const SPair<T> &P = pair(p);
             const Geom &gi = geom_i(P);
             const Geom &gf = side ? geo[P.gj] : gi;
-            const V3<T> pv = v3<T>(it.p[0], it.p[1], it.p[2]);
+            const V3<T> pv = v3<T>(ip.x, ip.y, ip.z);
             V3<T> qq;
             T rr;
-            face_rest<T, COUNT>(tab, itab, gf.fi_off + 2 * f, tab[gf.f_off + f], pv, it.h, &qq, &rr,
+            face_rest<T, COUNT>(tab, itab, gf.fi_off + 2 * f, tab[gf.f_off + f], pv, ip.w, &qq, &rr,
                                 &pc);
             if (rr < P.rc * P.rc) {
                 ok = true;
@@ -273,17 +286,19 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
         T r2 = T(0);
         int p = 0;
         if (lane < n) {
-            const EEItem<T> it = ws.fq.ee[(fh + lane) & (RING - 1)];
-            p = it.code & 31;
-            const int ea = (it.code >> 5) & 31, eb = (it.code >> 10) & 31;
+            const EEItem<T> &it = ws.fq.ee[(fh + lane) & (RING - 1)];
+            const auto a2 = it.a2, d2 = it.d2;
+            const int code = (int)a2.w;
+            p = code & 31;
+            const int ea = (code >> 5) & 31, eb = (code >> 10) & 31;
             const SPair<T> &P = pair(p);
             const Geom &gi = geom_i(P), &gj = geo[P.gj];
             const R4 aa = tab[gi.e_off + 2 * ea], ad = tab[gi.e_off + 2 * ea + 1];
             const T inv_c = tab[gj.e_off + 2 * eb + 1].w;
             V3<T> P1, P2;
             bump<COUNT>(&pc, C_SEGSEG);
-            segment_nearest<T>(xyz<T>(aa), xyz<T>(ad), ad.w, v3<T>(it.a2[0], it.a2[1], it.a2[2]),
-                               v3<T>(it.d2[0], it.d2[1], it.d2[2]), inv_c, par_eps, &P1, &P2);
+            segment_nearest<T>(xyz<T>(aa), xyz<T>(ad), ad.w, v3<T>(a2.x, a2.y, a2.z),
+                               v3<T>(d2.x, d2.y, d2.z), inv_c, par_eps, &P1, &P2);
             const V3<T> d = P1 - P2;
             const T rr = dot(d, d);
             if (rr < P.rc * P.rc) {
@@ -310,7 +325,10 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
             const Geom &gi = geom_i(P), &gj = geo[P.gj];
             if (spheres(gi, gj)) {
                 q = xyz<T>(tab[gi.v_off]);
-                rv = q - (v3<T>(P.dl[0], P.dl[1], P.dl[2]) + mul(pair_m(P), xyz<T>(tab[gj.v_off])));
+                M33<T> M;
+                V3<T> dl;
+                load_rows(P.row, &M, &dl);
+                rv = q - (dl + mul(M, xyz<T>(tab[gj.v_off])));
                 r2 = dot(rv, rv);
                 ok = r2 < P.rc * P.rc;
                 if (ok) bump<COUNT>(&pc, C_TERMS);
@@ -350,8 +368,9 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
         const Geom &gi = geom_i(P), &gj = geo[P.gj];
         const unsigned oA = DIM == 3 ? P.fim : P.eim;
         const int nA = oA ? __popc(P.vjm) : 0;
-        const M33<T> M = pair_m(P);
-        const V3<T> dl = v3<T>(P.dl[0], P.dl[1], P.dl[2]);
+        M33<T> M;
+        V3<T> dl;
+        load_rows(P.row, &M, &dl);
         crc = P.rc;
         T reach;
         unsigned m;
@@ -434,8 +453,10 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
         const Geom &gi = geom_i(P), &gj = geo[P.gj];
         cidx = nth_set_bit(P.ejm, t - ws.boffs[cp]);
         const R4 ba = tab[gj.e_off + 2 * cidx], bd = tab[gj.e_off + 2 * cidx + 1];
-        const M33<T> M = pair_m(P);
-        va = v3<T>(P.dl[0], P.dl[1], P.dl[2]) + mul(M, xyz<T>(ba));
+        M33<T> M;
+        V3<T> dl;
+        load_rows(P.row, &M, &dl);
+        va = dl + mul(M, xyz<T>(ba));
         vb = mul(M, xyz<T>(bd));
         vc = va + vb * T(0.5);
         crb = ba.w;
@@ -546,17 +567,13 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             const ShapeDev &shi = a.shapes[a.shape[i_me]];
             const M33<T> R = orientation<T>(a, i_me);
             SInfo<T> &pi = ws.info[lane];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) pi.r[3 * r + c] = R.m[r][c];
             if constexpr (std::is_same<T, float>::value) {
                 const float4 dd = a.delta[i_me];
-                pi.x[0] = dd.x; pi.x[1] = dd.y; pi.x[2] = dd.z;
+                store_rows(pi.row, R, v3<float>(dd.x, dd.y, dd.z));
                 pi.rnd = shi.rounding_f;
             } else {
                 const double4_32a xx = a.pos[i_me];
-                pi.x[0] = xx.x; pi.x[1] = xx.y; pi.x[2] = xx.z;
+                store_rows(pi.row, R, v3<double>(xx.x, xx.y, xx.z));
                 pi.rnd = shi.rounding;
             }
             pi.geom = shi.geom;
@@ -587,6 +604,9 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
                 const int i = base + pl;
                 const SInfo<T> &pi = ws.info[pl];
                 const Geom &gi = geo[pi.geom];
+                M33<T> Ri;
+                V3<T> xi;
+                load_rows(pi.row, &Ri, &xi);
                 Owner<T> own;
                 own.rp = &a.reps[pi.rep];
                 own.R = (T)gi.R;
@@ -594,9 +614,9 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
                 own.sig_all = sig_all;
                 own.geom = pi.geom;
                 if constexpr (std::is_same<T, float>::value)
-                    own.delta = make_float4(pi.x[0], pi.x[1], pi.x[2], 0.f);
+                    own.delta = make_float4(xi.x, xi.y, xi.z, 0.f);
                 else
-                    own.x = make_double4_32a(pi.x[0], pi.x[1], pi.x[2], 0.0);
+                    own.x = make_double4_32a(xi.x, xi.y, xi.z, 0.0);
                 const float4 e = a.nlist[(size_t)k * a.n + i];
                 bump<COUNT>(&st.pc, C_NEIGH);
                 PairGeom<T> pg;
@@ -605,12 +625,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
                     const Geom &gj = geo[pg.gj];
                     bump<COUNT>(&st.pc, C_PAIRS);
                     bump<COUNT>(&st.pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
-                    M33<T> Ri;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) Ri.m[r][c] = pi.r[3 * r + c];
-                    wk.M = mul_tn(Ri, orientation<T>(a, j));
+                    wk.M = mul_tn(Ri, orientation_j<T>(a, j, pg));
                     wk.dl = mul_t(Ri, pg.d);
                     wk.rc = (T)WCA_CUT * pg.sig;
                     wk.sig2 = pg.sig * pg.sig;
@@ -622,11 +637,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             const unsigned m = __ballot_sync(FULL, active);
             if (active) {
                 SPair<T> &P = ws.pr[ring_slot(m, lane, st.ph + st.np)];
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) P.m[3 * r + c] = wk.M.m[r][c];
-                P.dl[0] = wk.dl.x; P.dl[1] = wk.dl.y; P.dl[2] = wk.dl.z;
+                store_rows(P.row, wk.M, wk.dl);
                 P.rc = wk.rc;
                 P.sig2 = wk.sig2;
                 P.gj = wk.gj;
@@ -638,12 +649,9 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             __syncwarp();
         }
         if (mine) {
-            const SInfo<T> &pi = ws.info[lane];
             M33<T> R;
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) R.m[r][c] = pi.r[3 * r + c];
+            V3<T> x;
+            load_rows(ws.info[lane].row, &R, &x);
             finish_particle(a, i_me, st.S, R);
         }
         __syncwarp();
