@@ -189,7 +189,7 @@ def algorithmic_flops(counts, comp):
 
 def pair_source_hash():
     h = hashlib.sha256()
-    for name in ("pair.cu", "pair_common.cuh"):
+    for name in ("pair.cu", "pair_staged.cu", "pair_kernels.cuh", "pair_common.cuh"):
         with open(os.path.join(ROOT, "paper_1607_02427_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
