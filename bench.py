@@ -108,6 +108,20 @@ def make_workload(name, rank, replicas):
     return W.config_squares_2d(seed_index=0 + off), dict(dt=1e-3, ensemble="nve", kT=1.0, tau=0.5)
 
 
+def reduce_over_ranks(dist, ms, n, device):
+    """Whole-job timing over the ranks: the largest timed milliseconds and the
+    total particle count (every rank runs its own replicas; no other data
+    crosses ranks)."""
+    if dist is None:
+        return ms, n
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    nt = torch.tensor([float(n)], dtype=torch.float64, device=device)
+    dist.all_reduce(nt)
+    return float(t.item()), int(round(nt.item()))
+
+
 def prepare(dem, system, run, precision, compress_steps, equil_steps):
     """Context at the target density: compress from the safe lattice start
     (NVT, geometric box schedule), then equilibrate."""
@@ -329,15 +343,7 @@ def main():
     launches = int(d.get_param("launches") - l0)
     pair_ms = d.get_param("pair_ms_total") / max(1.0, d.get_param("pair_launches"))
     d.set_param("profile", 0)
-    t_max = ms
-    n_total = system.n
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        nt = torch.tensor([float(system.n)], device="cuda")
-        dist.all_reduce(nt)
-        n_total = int(nt.item())
+    t_max, n_total = reduce_over_ranks(dist, ms, system.n, "cuda")
     value = n_total * a.steps / (t_max / 1e3)
 
     counts = d.counters()
