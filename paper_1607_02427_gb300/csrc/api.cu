@@ -620,6 +620,7 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     a.force = ctx->force; a.torque = ctx->torque;
     a.shape = ctx->shape; a.rep = ctx->rep; a.reps = ctx->d_reps; a.shapes = ctx->d_shapes;
     a.ke = ctx->ke; a.thermo = ctx->thermo; a.status = ctx->status;
+    a.rotor32 = ctx->precision != DEM_FP64;
     return a;
 }
 

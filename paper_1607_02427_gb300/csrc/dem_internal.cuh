@@ -152,6 +152,7 @@ struct StepArgs {
     double *ke;
     Thermo *thermo;
     Status *status;
+    int rotor32;             // FP32 modes: free-rotor increments in FP32
 };
 
 // ---- launch wrappers (pair.cu, nlist.cu, integrate.cu) ----

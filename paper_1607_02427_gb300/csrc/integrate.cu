@@ -75,6 +75,69 @@ __device__ __forceinline__ void free_rotor_axis(double4_32a &q, double4_32a &L, 
     set_comp(L, b, -s * La + c * Lb);
 }
 
+// FP32: sin h and cos h - 1 (|h| <= 1/8: Maclaurin series, truncated where
+// the remainder is below 2e-10 of either result; cos h - 1 comes straight
+// from the series, so it keeps its relative precision for small h).
+__device__ __forceinline__ void sincosm1_f(float h, float *s, float *cm1) {
+    if (fabsf(h) <= 0.125f) {
+        const float h2 = h * h;
+        *s = fmaf(h2 * fmaf(h2, 1.f / 120.f, -1.f / 6.f), h, h);
+        *cm1 = h2 * fmaf(h2, fmaf(h2, -1.f / 720.f, 1.f / 24.f), -0.5f);
+    } else {
+        const float sh = sinf(0.5f * h);
+        *s = sinf(h);
+        *cm1 = -2.f * sh * sh;
+    }
+}
+
+// The free rotor of the FP32 modes: the five sub-rotations (z, y, x, y, z)
+// run in FP32 as increments, the change dL of the body angular momentum and
+// the composite rotation r = 1 + rho (r = r_1 r_2 ... r_5, each r_s =
+// (cos h_s, sin h_s e_k)), and are applied to the FP64 state as L += dL and
+// q += q rho.  The increments are of order h ~ dt |L| / I, so their FP32
+// rounding is of order 1e-7 h: far below the FP32 force error.
+__device__ __forceinline__ void free_rotor_f32(double4_32a &q, double4_32a &L, const double *invI,
+                                               double dt) {
+    const float ii[3] = {(float)invI[0], (float)invI[1], (float)invI[2]};
+    float Lc[3] = {(float)L.x, (float)L.y, (float)L.z};
+    float dL[3] = {0.f, 0.f, 0.f};
+    float rw = 0.f, rv[3] = {0.f, 0.f, 0.f};
+    const float hd = (float)(0.25 * dt);
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int k = step == 2 ? 0 : (step == 1 || step == 3 ? 1 : 2);
+        if (!(ii[k] > 0.f)) continue;
+        const float h = (step == 2 ? 2.f * hd : hd) * Lc[k] * ii[k];
+        float sh, cm1;
+        sincosm1_f(h, &sh, &cm1);
+        // L_b rotates by phi = 2h about k: cos phi - 1 = -2 sh^2, sin phi = 2 sh ch
+        const int a = (k + 1) % 3, b = (k + 2) % 3;
+        const float c1 = -2.f * sh * sh, s2 = 2.f * sh * (1.f + cm1);
+        const float ia = c1 * Lc[a] + s2 * Lc[b], ib = c1 * Lc[b] - s2 * Lc[a];
+        Lc[a] += ia; Lc[b] += ib;
+        dL[a] += ia; dL[b] += ib;
+        // (1 + rho) <- (1 + rho)(1 + sigma), sigma = (cm1, sh e_k)
+        float cx[3] = {0.f, 0.f, 0.f};      // rv x e_k
+        cx[a] = rv[b];
+        cx[b] = -rv[a];
+        const float nw = rw + cm1 + (rw * cm1 - rv[k] * sh);
+        float nv[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+            nv[m] = rv[m] + (m == k ? sh : 0.f) + (m == k ? rw * sh : 0.f) + cm1 * rv[m] + sh * cx[m];
+        rw = nw;
+        rv[0] = nv[0]; rv[1] = nv[1]; rv[2] = nv[2];
+    }
+    // q rho in FP32, added to the FP64 quaternion; q = (x: w, y: x, z: y, w: z)
+    const float qw = (float)q.x, qx = (float)q.y, qy = (float)q.z, qz = (float)q.w;
+    const float dw = qw * rw - (qx * rv[0] + qy * rv[1] + qz * rv[2]);
+    const float dx = qw * rv[0] + rw * qx + (qy * rv[2] - qz * rv[1]);
+    const float dy = qw * rv[1] + rw * qy + (qz * rv[0] - qx * rv[2]);
+    const float dz = qw * rv[2] + rw * qz + (qx * rv[1] - qy * rv[0]);
+    q.x += (double)dw; q.y += (double)dx; q.z += (double)dy; q.w += (double)dz;
+    L.x += (double)dL[0]; L.y += (double)dL[1]; L.z += (double)dL[2];
+}
+
 // x mapped into [0, L) (invL = 1/L)
 __device__ __forceinline__ double wrap(double x, double L, double invL) {
     x -= L * floor(x * invL);
@@ -106,11 +169,15 @@ __global__ void k_first_half(const StepArgs a) {
         x.x = wrap(x.x + a.dt * v.x, rp.L[0], rp.inv_L[0]);
         x.y = wrap(x.y + a.dt * v.y, rp.L[1], rp.inv_L[1]);
         if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2], rp.inv_L[2]);
-        free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
-        free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
-        free_rotor_axis(q, L, sh.inv_inertia, 0, a.dt);
-        free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
-        free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
+        if (a.rotor32) {
+            free_rotor_f32(q, L, sh.inv_inertia, a.dt);
+        } else {
+            free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
+            free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
+            free_rotor_axis(q, L, sh.inv_inertia, 0, a.dt);
+            free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
+            free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
+        }
         const double inq = rsqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
         q.x *= inq; q.y *= inq; q.z *= inq; q.w *= inq;
         a.pos[i] = x;
