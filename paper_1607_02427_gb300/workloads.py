@@ -443,6 +443,50 @@ def config_large(counts=(64, 128, 128), kT: float = 1.0, seed_index: int = 4) ->
                    params=dict(dt=1e-3, steps=1000, ensemble="nvt", kT=kT, tau_T=0.5))
 
 
+PAPER_TABLE_SHAPES = ("sphere", "cube", "icosahedron")
+
+
+def config_paper_table(shape: str = "icosahedron", n: int = 65536, phi: float = 0.45,
+                       kT: float = 1.0, seed_index: int = 5) -> System:
+    """One dense-fluid system of the paper's performance table (Section
+    "Performance": spheres with the central WCA, cubes and icosahedra, N = 256,
+    4096 or 65,536).  The paper gives no density, size or rounding for these
+    runs; here: packing fraction 0.45 of the rounded volume, sphere diameter
+    sigma = 1 (rounding 0.5), cube and icosahedron edge 1 with rounding 0.15
+    (sigma = 0.3), a seeded subset of ceil(N^(1/3))^3 simple-cubic sites,
+    compressed from the safe spacing like the other 3D configs; NVT kT = 1."""
+    rng = np.random.default_rng(np.random.SeedSequence(BASE_SEED + seed_index))
+    makers = {"sphere": lambda: sphere(0.5), "cube": lambda: cube(1.0, 0.15),
+              "icosahedron": lambda: icosahedron(1.0, 0.15)}
+    sh = makers[shape]()
+    m = int(math.ceil(n ** (1.0 / 3.0) - 1e-9))
+    pos, start, target = _compressible_sc(rng, sh, [m] * 3, phi, n_use=n)
+    return _finish(rng, 3, [sh], np.zeros(n, np.int32), pos, [start], [n], kT,
+                   epsilon=1.0, sigma=0.0, target_box=target.reshape(1, 3),
+                   name=f"{shape}s_N{n}_phi{phi:.2f}",
+                   params=dict(dt=1e-3, ensemble="nvt", kT=kT, tau_T=0.5))
+
+
+def sample_like(system: System, n_target: int = 512, kT: float = 1.0, seed: int = 0) -> System:
+    """A small system like replica 0 of ``system``: the same shapes (drawn in
+    the replica's proportions) at its target density, on m^d simple-cubic
+    sites in a cubic box (m = round(n_target^(1/d))); for timing the CPU oracle
+    on workloads too large for it."""
+    rep = system.replica(0)
+    dim = rep.dim
+    box = rep.target_box[0] if rep.target_box is not None else rep.box[0]
+    rho = rep.n / float(np.prod(np.asarray(box, np.float64)[:dim]))
+    m = max(2, int(round(n_target ** (1.0 / dim))))
+    n = m ** dim
+    L = (n / rho) ** (1.0 / dim)
+    rng = np.random.default_rng(np.random.SeedSequence(BASE_SEED + 900 + seed))
+    ids = rep.shape_id[rng.integers(0, rep.n, size=n)]
+    pos = sc_sites([m] * dim, [L / m] * dim)
+    return _finish(rng, dim, rep.shapes, ids, pos, [[L] * dim], [n], kT,
+                   epsilon=rep.epsilon, sigma=rep.sigma,
+                   name=f"{rep.name}_sample{n}")
+
+
 # ---------------------------------------------------------------------------
 # Contact-rich random clusters (force tests)
 # ---------------------------------------------------------------------------

@@ -69,4 +69,5 @@ SHAPES_3D = {
     "tetrahedron": lambda: W.tetrahedron(1.0, 0.15),
     "octahedron": lambda: W.octahedron(1.0, 0.1),
     "prism": lambda: W.triangular_prism(1.0, 1.0, 0.15),
+    "icosahedron": lambda: W.icosahedron(0.8, 0.15),
 }

@@ -48,6 +48,8 @@ def _systems():
                                               np.zeros(300, int), [12.0, 12.0, 12.0], 7)
     out["spheres"] = lambda: _periodic_cluster([W.sphere(0.3, 0.036)], np.zeros(400, int),
                                                [9.0, 9.0, 9.0], 8)
+    out["icosas"] = lambda: _periodic_cluster([W.icosahedron(0.8, 0.15)], np.zeros(250, int),
+                                              [12.0, 12.0, 12.0], 10)
     out["mixed3d"] = lambda: _periodic_cluster(
         [W.cube(1.0, 0.15), W.tetrahedron(1.0, 0.1), W.triangular_prism(1.0, 1.0, 0.2),
          W.sphere(0.3, 0.036), W.octahedron(0.9, 0.12)], np.arange(290) % 5,
