@@ -540,7 +540,8 @@ static double compute_forces(sys_t *S, const double *pos, const double *orient) 
     return U;
 }
 
-/* kinetic energies; Lb is body-frame angular momentum (n*3, 2D: n) */
+/* kinetic energies; Lb is body-frame angular momentum (n*3, 2D: n), or NULL
+ * for the translational part only */
 static void kinetic(sys_t *S, const double *vel, const double *Lb, double *Kt, double *Kr) {
     *Kt = 0.0; *Kr = 0.0;
     for (int i = 0; i < S->n; ++i) {
@@ -549,6 +550,7 @@ static void kinetic(sys_t *S, const double *vel, const double *Lb, double *Kt, d
         for (int a = 0; a < S->dim; ++a) v2 += vel[S->dim * i + a] * vel[S->dim * i + a];
         *Kt += 0.5 * S->mass[s] * v2;
         const double *I = S->inertia + 3 * s;
+        if (!Lb) continue;
         if (S->dim == 3) {
             for (int k = 0; k < 3; ++k)
                 if (I[k] > 0.0) *Kr += 0.5 * Lb[3 * i + k] * Lb[3 * i + k] / I[k];
@@ -574,16 +576,82 @@ static void thermostat(sys_t *S, double *vel, double *Lb, double *xi, double *et
     *xi += 0.5 * delta * (2.0 * K / (g * kT) - 1.0) / (tau * tau);
 }
 
-/* Run nsteps of NVE (ensemble 0) or NVT (ensemble 1) from the given state.
- * angmom is world-frame (3D n*3, 2D n); thermo = {xi, eta}.  trace, if not
- * NULL, receives per step {K_trans, K_rot, U, H} after the step, where H is
- * the conserved quantity (K + U for NVE).  Returns 0, or -1 on bad input. */
+/* sinh(x)/x (Maclaurin series below |x| = 1e-2, remainder < 1e-17) */
+static double sinhc(double x) {
+    if (fabs(x) < 1e-2) {
+        double x2 = x * x;
+        return 1.0 + x2 / 6.0 * (1.0 + x2 / 20.0 * (1.0 + x2 / 42.0));
+    }
+    return sinh(x) / x;
+}
+
+/* Translational kinetic energy sum m v^2 / 2 */
+static double kinetic_trans(sys_t *S, const double *vel) {
+    double Kt, Kr;
+    kinetic(S, vel, NULL, &Kt, &Kr);
+    return Kt;
+}
+
+/* Isotropic barostat (ensemble 2), the MTK equations integrated as in
+ * Tuckerman et al., J. Phys. A 39, 5629 (2006), which Section "Assembly"
+ * cites for its NPT runs (the paper gives no formulas; this reading:
+ * isotropic scaling of the orthorhombic box, one Nose-Hoover thermostat
+ * shared by the particles and the barostat):
+ *   dx/dt = v + v_e x,   dv/dt = F/m - alpha v_e v - xi v,   alpha = 1 + d/N_f,
+ *   dL_b/dt = tau_b - xi L_b (+ the free rotor),
+ *   dV/dt = d V v_e,     v_e = p_e / W,
+ *   dp_e/dt = alpha sum m v^2 + Tr(Wvir) - d V P - xi p_e,
+ *   dxi/dt = (2K + p_e^2/W - (g + 1) kT) / Q,   Q = (g + 1) kT tau^2,
+ * N_f = d (N - 1), W = (N_f + d) kT tau_P^2, Wvir = sum_{i<j} x_ij (x) f_ij.
+ * Conserved: K + U + p_e^2/(2W) + P V + (g + 1) kT (tau^2 xi^2 / 2 + eta).
+ * One step: T(dt/2) B(dt/2) V(dt/2) X(dt) [forces] V(dt/2) B(dt/2) T(dt/2),
+ * each factor solved exactly:
+ *   T: the thermostat (as for NVT, also scaling p_e);
+ *   B: p_e += delta (alpha 2 K_t + Tr(Wvir) - d V P);
+ *   V: v <- v exp(-alpha v_e delta) + (F/m) delta exp(-alpha v_e delta/2)
+ *        sinhc(alpha v_e delta/2), L_b += delta tau_b;
+ *   X: x <- x exp(v_e dt) + v dt exp(v_e dt/2) sinhc(v_e dt/2), box <- box
+ *        exp(v_e dt), then the free rotor over dt. */
+static void thermostat_npt(sys_t *S, double *vel, double *Lb, double *pe, double W,
+                           double *xi, double *eta, double g1, double kT, double tau,
+                           double delta) {
+    double Kt, Kr;
+    kinetic(S, vel, Lb, &Kt, &Kr);
+    double K = Kt + Kr + 0.5 * (*pe) * (*pe) / W;
+    *xi += 0.5 * delta * (2.0 * K / (g1 * kT) - 1.0) / (tau * tau);
+    double s = exp(-(*xi) * delta);
+    int tdim = S->dim == 3 ? 3 : 1;
+    for (int i = 0; i < S->n * S->dim; ++i) vel[i] *= s;
+    for (int i = 0; i < S->n * tdim; ++i) Lb[i] *= s;
+    *pe *= s;
+    *eta += (*xi) * delta;
+    K *= s * s;
+    *xi += 0.5 * delta * (2.0 * K / (g1 * kT) - 1.0) / (tau * tau);
+}
+
+static double volume(int dim, const double *box) {
+    double V = 1.0;
+    for (int a = 0; a < dim; ++a) V *= box[a];
+    return V;
+}
+
+static double virial_trace(sys_t *S) {
+    return S->virial[0] + S->virial[4] + (S->dim == 3 ? S->virial[8] : 0.0);
+}
+
+/* Run nsteps of NVE (ensemble 0), NVT (ensemble 1) or NPT (ensemble 2) from
+ * the given state.  angmom is world-frame (3D n*3, 2D n); thermo = {xi, eta,
+ * p_e} (p_e only for NPT); box (dim lengths) is updated by NPT; P and tau_P
+ * are the NPT pressure and barostat time.  trace, if not NULL, receives per
+ * step {K_trans, K_rot, U, H, V} after the step, where H is the conserved
+ * quantity (K + U for NVE).  Returns 0, or -1 on bad input. */
 int oracle_run(int dim, int n_shapes, const int *vert_off, const double *verts,
                const int *shape_face_off, const int *face_vert_off, const int *face_idx,
                const double *rounding, const double *mass, const double *inertia, double eps,
                double sigma, double par_eps, int n, const int *shape_id, double *pos,
-               double *orient, double *vel, double *angmom, const double *box, double *thermo,
-               int nsteps, double dt, int ensemble, double kT, double tau, double *trace) {
+               double *orient, double *vel, double *angmom, double *box, double *thermo,
+               int nsteps, double dt, int ensemble, double kT, double tau, double P,
+               double tau_P, double *trace) {
     shape_t *shapes = (shape_t *)malloc(sizeof(shape_t) * (n_shapes > 0 ? n_shapes : 1));
     int tdim = dim == 3 ? 3 : 1;
     double *force = (double *)malloc(sizeof(double) * dim * n);
@@ -617,15 +685,29 @@ int oracle_run(int dim, int n_shapes, const int *vert_off, const double *verts,
         }
     }
     double xi = thermo ? thermo[0] : 0.0, eta = thermo ? thermo[1] : 0.0;
+    double pe = (thermo && ensemble == 2) ? thermo[2] : 0.0;
+    const double Nf = dim * (n - 1.0), alpha = 1.0 + dim / Nf;
+    const double W = (Nf + dim) * kT * tau_P * tau_P;
+    if (ensemble == 2 && !(n >= 2 && tau_P > 0.0)) return -1;
     double U = compute_forces(&S, pos, orient);
 
     for (int step = 0; step < nsteps; ++step) {
         if (ensemble == 1) thermostat(&S, vel, Lb, &xi, &eta, g, kT, tau, 0.5 * dt);
+        if (ensemble == 2) {
+            thermostat_npt(&S, vel, Lb, &pe, W, &xi, &eta, g + 1.0, kT, tau, 0.5 * dt);
+            pe += 0.5 * dt * (alpha * 2.0 * kinetic_trans(&S, vel) + virial_trace(&S) -
+                              dim * volume(dim, box) * P);
+        }
+        const double ve = ensemble == 2 ? pe / W : 0.0;
+        /* velocity factors of the V(dt/2) step (1 and dt/2 without a barostat) */
+        const double av = exp(-alpha * ve * 0.5 * dt);
+        const double bv = 0.5 * dt * exp(-alpha * ve * 0.25 * dt) * sinhc(alpha * ve * 0.25 * dt);
         for (int half = 0; half < 2; ++half) {
             /* half kick with the force and the body-frame torque */
             for (int i = 0; i < n; ++i) {
                 double m = mass[shape_id[i]];
-                for (int a = 0; a < dim; ++a) vel[dim * i + a] += 0.5 * dt * force[dim * i + a] / m;
+                for (int a = 0; a < dim; ++a)
+                    vel[dim * i + a] = vel[dim * i + a] * av + bv * force[dim * i + a] / m;
                 if (dim == 3) {
                     double R[3][3];
                     quat_to_mat(orient + 4 * i, R);
@@ -637,10 +719,13 @@ int oracle_run(int dim, int n_shapes, const int *vert_off, const double *verts,
                 }
             }
             if (half == 1) break;
-            /* drift, free rotation, wrap */
+            /* drift (with the box dilation under NPT), free rotation, wrap */
+            const double ax = exp(ve * dt), bx = dt * exp(0.5 * ve * dt) * sinhc(0.5 * ve * dt);
+            if (ensemble == 2)
+                for (int a = 0; a < dim; ++a) box[a] *= ax;
             for (int i = 0; i < n; ++i) {
                 for (int a = 0; a < dim; ++a) {
-                    double x = pos[dim * i + a] + dt * vel[dim * i + a];
+                    double x = pos[dim * i + a] * ax + bx * vel[dim * i + a];
                     x -= box[a] * floor(x / box[a]);
                     if (x >= box[a]) x -= box[a];
                     pos[dim * i + a] = x;
@@ -662,13 +747,22 @@ int oracle_run(int dim, int n_shapes, const int *vert_off, const double *verts,
             U = compute_forces(&S, pos, orient);
         }
         if (ensemble == 1) thermostat(&S, vel, Lb, &xi, &eta, g, kT, tau, 0.5 * dt);
+        if (ensemble == 2) {
+            pe += 0.5 * dt * (alpha * 2.0 * kinetic_trans(&S, vel) + virial_trace(&S) -
+                              dim * volume(dim, box) * P);
+            thermostat_npt(&S, vel, Lb, &pe, W, &xi, &eta, g + 1.0, kT, tau, 0.5 * dt);
+        }
         if (trace) {
             double Kt, Kr;
             kinetic(&S, vel, Lb, &Kt, &Kr);
             double H = Kt + Kr + U;
             if (ensemble == 1) H += g * kT * (0.5 * tau * tau * xi * xi + eta);
-            trace[4 * step + 0] = Kt; trace[4 * step + 1] = Kr;
-            trace[4 * step + 2] = U;  trace[4 * step + 3] = H;
+            if (ensemble == 2)
+                H += 0.5 * pe * pe / W + P * volume(dim, box) +
+                     (g + 1.0) * kT * (0.5 * tau * tau * xi * xi + eta);
+            trace[5 * step + 0] = Kt; trace[5 * step + 1] = Kr;
+            trace[5 * step + 2] = U;  trace[5 * step + 3] = H;
+            trace[5 * step + 4] = volume(dim, box);
         }
     }
     /* body -> world angular momentum */
@@ -682,7 +776,7 @@ int oracle_run(int dim, int n_shapes, const int *vert_off, const double *verts,
             angmom[i] = Lb[i];
         }
     }
-    if (thermo) { thermo[0] = xi; thermo[1] = eta; }
+    if (thermo) { thermo[0] = xi; thermo[1] = eta; if (ensemble == 2) thermo[2] = pe; }
     free(shapes); free(force); free(torque); free(energy); free(Lb); free(tb);
     return 0;
 }

@@ -50,7 +50,8 @@ def _load():
         lib.oracle_run.restype = C.c_int
         lib.oracle_run.argtypes = [C.c_int, C.c_int, ip, dp, ip, ip, ip, dp, dp, dp, C.c_double,
                                    C.c_double, C.c_double, C.c_int, ip, dp, dp, dp, dp, dp, dp,
-                                   C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, dp]
+                                   C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, dp]
         lib.oracle_point_segment.restype = C.c_double
         lib.oracle_point_segment.argtypes = [dp, dp, dp, dp]
         lib.oracle_point_face.restype = C.c_double
@@ -148,11 +149,15 @@ def forces(system, par_eps: float = DEFAULT_PAR_EPS, scales: bool = True):
 
 
 def run(system, nsteps: int, dt: float, ensemble: str = "nve", kT: float = 1.0,
-        tau: float = 0.5, par_eps: float = DEFAULT_PAR_EPS, thermo=None):
+        tau: float = 0.5, par_eps: float = DEFAULT_PAR_EPS, thermo=None,
+        P: float = 1.0, tau_P: float = 1.0):
     """Integrate ``nsteps`` from the system's state (copied, not modified).
 
-    Returns (state dict with pos, orient, vel, angmom, thermo per replica,
-    trace (R, nsteps, 4) = K_trans, K_rot, U, H per step).
+    ensemble: "nve", "nvt" or "npt" (isotropic barostat at pressure P with
+    barostat time tau_P; see oracle_run in dem_oracle.c).  thermo: per replica
+    {xi, eta, p_e}.  Returns (state dict with pos, orient, vel, angmom, thermo
+    (R, 3), box (R, dim) per replica, trace (R, nsteps, 5) = K_trans, K_rot, U,
+    H, V per step).
     """
     lib = _load()
     dim = system.dim
@@ -174,14 +179,19 @@ def run(system, nsteps: int, dt: float, ensemble: str = "nve", kT: float = 1.0,
     orient = np.array(system.orient, np.float64)
     vel = np.array(system.vel, np.float64)
     angmom = np.array(system.angmom, np.float64)
-    th = np.zeros((system.n_replicas, 2)) if thermo is None else np.array(thermo, np.float64)
-    trace = np.zeros((system.n_replicas, nsteps, 4))
-    ens = {"nve": 0, "nvt": 1}[ensemble]
+    th = np.zeros((system.n_replicas, 3))
+    if thermo is not None:
+        t = np.atleast_2d(np.array(thermo, np.float64))
+        th[:, :t.shape[1]] = t
+    trace = np.zeros((system.n_replicas, nsteps, 5))
+    boxes = np.array(system.box, np.float64).reshape(system.n_replicas, dim).copy()
+    ens = {"nve": 0, "nvt": 1, "npt": 2}[ensemble]
     for r, sl in enumerate(system.replica_slices()):
         m = sl.stop - sl.start
         p_, o_, v_, a_ = (np.ascontiguousarray(x[sl]) for x in (pos, orient, vel, angmom))
         t_ = np.ascontiguousarray(th[r])
-        tr = np.zeros((nsteps, 4))
+        b_ = np.ascontiguousarray(boxes[r])
+        tr = np.zeros((nsteps, 5))
         rc = lib.oracle_run(dim, len(system.shapes), ip(pk["vert_off"]), dp(pk["verts"]),
                             ip(pk["shape_face_off"]), ip(pk["face_vert_off"]),
                             ip(pk["face_idx"]), dp(pk["rounding"]), dp(mass), dp(inertia),
@@ -191,15 +201,17 @@ def run(system, nsteps: int, dt: float, ensemble: str = "nve", kT: float = 1.0,
                             o_.ctypes.data_as(C.POINTER(C.c_double)),
                             v_.ctypes.data_as(C.POINTER(C.c_double)),
                             a_.ctypes.data_as(C.POINTER(C.c_double)),
-                            dp(system.box[r]), t_.ctypes.data_as(C.POINTER(C.c_double)),
-                            int(nsteps), float(dt), ens, float(kT), float(tau),
-                            tr.ctypes.data_as(C.POINTER(C.c_double)))
+                            b_.ctypes.data_as(C.POINTER(C.c_double)),
+                            t_.ctypes.data_as(C.POINTER(C.c_double)),
+                            int(nsteps), float(dt), ens, float(kT), float(tau), float(P),
+                            float(tau_P), tr.ctypes.data_as(C.POINTER(C.c_double)))
         if rc != 0:
             raise ValueError(f"oracle_run failed ({rc})")
         pos[sl], orient[sl], vel[sl], angmom[sl] = p_, o_, v_, a_
         th[r] = t_
+        boxes[r] = b_
         trace[r] = tr
-    return dict(pos=pos, orient=orient, vel=vel, angmom=angmom, thermo=th), trace
+    return dict(pos=pos, orient=orient, vel=vel, angmom=angmom, thermo=th, box=boxes), trace
 
 
 def _vec(x):
