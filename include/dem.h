@@ -74,6 +74,7 @@ extern "C" {
 /* ---- ensembles ---- */
 #define DEM_NVE 0
 #define DEM_NVT 1
+#define DEM_NPT 2   /* NVT plus an isotropic barostat (dem_set_barostat)      */
 
 /* ---- pair-kernel decompositions (parameter "decomp") ---- */
 #define DEM_DECOMP_AUTO 0    /* chosen by dem_autotune (default: THREAD)        */
@@ -154,24 +155,50 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
 
 /* Read the state (host or device arrays; any pointer may be NULL):
  * pos N*dim, orient N*4 (3D) or N (2D), vel N*dim, angmom N*3 (3D, world
- * frame) or N (2D), thermostat n_replicas * 2 (xi, eta). */
+ * frame) or N (2D), thermostat n_replicas * 3 (xi, eta, p_e). */
 int dem_get_state(dem_ctx *ctx, double *pos, double *orient, double *vel, double *angmom,
                   double *thermostat, int device_ptrs);
 
-/* Set the Nose-Hoover variables (xi, eta) of each replica (host array,
- * n_replicas * 2).  xi is the friction coefficient, eta its time integral. */
+/* Set the extended variables of each replica (host array, n_replicas * 3):
+ * the Nose-Hoover friction xi, its time integral eta, and the barostat
+ * momentum p_e (used by DEM_NPT; 0 otherwise). */
 int dem_set_thermostat(dem_ctx *ctx, const double *thermostat);
 
+/* Barostat of DEM_NPT steps: pressure P >= 0 and time constant tau_P > 0.
+ * Section "Assembly" runs NPT with a Nose-Hoover thermostat on translation
+ * and rotation and a barostat that takes the pressure from the virial
+ * tensor as in MD, citing Tuckerman et al. (J. Phys. A 39, 5629 (2006)); the
+ * paper gives no formulas.  This library integrates the MTK equations for an
+ * isotropically scaled box (each replica its own), with one thermostat
+ * shared by the particles and the barostat:
+ *   dx/dt = v + v_e x, dv/dt = F/m - alpha v_e v - xi v, alpha = 1 + d/N_f,
+ *   dV/dt = d V v_e, v_e = p_e / W, dp_e/dt = alpha sum m v^2 + Tr W_vir
+ *   - d V P - xi p_e, dxi/dt = (2K + p_e^2/W - (g + 1) kT) / Q,
+ * N_f = d (N_r - 1), W = (N_f + d) kT tau_P^2, Q = (g + 1) kT tau_T^2, by
+ * the symmetric factorisation T B V X V B T of that paper, each factor
+ * solved exactly.  Errors: DEM_ERR_ARG. */
+int dem_set_barostat(dem_ctx *ctx, double P, double tau_P);
+
+/* Current box lengths of every replica (host array, n_replicas * dim);
+ * DEM_NPT steps change them. */
+int dem_get_box(dem_ctx *ctx, double *box);
+
 /* Advance all replicas n steps of size dt.
- *   ensemble  DEM_NVE, or DEM_NVT (Nose-Hoover at temperature kT with
+ *   ensemble  DEM_NVE, DEM_NVT (Nose-Hoover at temperature kT with
  *             time constant tau_T: dxi/dt = (2K/(g kT) - 1) / tau_T^2,
- *             g = dim (N_r - 1) + rotational degrees of freedom)
- * One step: thermostat half step (NVT), half kick of v and L, drift and
- * free rotation, neighbour-list rebuild if some particle moved more than
- * skin/2 since the last build, pair forces, half kick, thermostat half step.
- * Errors: DEM_ERR_STATE, DEM_ERR_NONFINITE, DEM_ERR_NLIST_OVERFLOW (after
- * an internal grow-and-retry from the state at the start of the call),
- * DEM_ERR_CUDA. */
+ *             g = dim (N_r - 1) + rotational degrees of freedom), or DEM_NPT
+ *             (see dem_set_barostat; every replica needs N_r >= 2)
+ * One step: thermostat half step (NVT, NPT), barostat half step (NPT), half
+ * kick of v and L, drift (with the box dilation under NPT) and free
+ * rotation, neighbour-list rebuild if some particle moved more than skin/2
+ * since the last build (under NPT less the distance a shrinking box can
+ * close), pair forces, half kick, barostat and thermostat half steps.  NPT
+ * calls run in chunks of "npt_chunk" steps; between chunks the boxes come
+ * back to the host and the cell grids follow them.
+ * Errors: DEM_ERR_ARG, DEM_ERR_STATE, DEM_ERR_NONFINITE,
+ * DEM_ERR_NLIST_OVERFLOW (after an internal grow-and-retry from the state at
+ * the start of the call), DEM_ERR_BOX (NPT: a box shrank by more than 5%
+ * within a chunk or below twice the list cutoff), DEM_ERR_CUDA. */
 int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T);
 
 /* Evaluate forces, torques, energies and virials at the current state. */
@@ -184,7 +211,9 @@ int dem_get_forces(dem_ctx *ctx, double *force, double *torque, int device_ptrs)
 /* Per-replica totals (host arrays of n_replicas, any may be NULL):
  * potential energy U (sum over pairs of Eq. DEM / Eq. DEM_2D), kinetic
  * energy K (translational + rotational) and the conserved quantity
- * (K + U in NVE; K + U + g kT (tau_T^2 xi^2 / 2 + eta) after an NVT call).
+ * (K + U in NVE; K + U + g kT (tau_T^2 xi^2 / 2 + eta) after an NVT call;
+ * K + U + p_e^2/(2W) + P V + (g + 1) kT (tau_T^2 xi^2 / 2 + eta) after an
+ * NPT call).
  * Per-particle energies (N, half of each pair's energy to each particle)
  * may be read with dem_get_particle_energy. */
 int dem_get_energy(dem_ctx *ctx, double *per_replica_U, double *per_replica_K,
@@ -210,6 +239,7 @@ int dem_set_box(dem_ctx *ctx, const double *box);
  *   "block"       threads per block of the pair kernel (0 = default)
  *   "graph"       1 = replay each step as a captured CUDA graph (default 1)
  *   "nlist_cap"   neighbour slots per particle (grown automatically)
+ *   "npt_chunk"   DEM_NPT steps between host updates of the cell grids (100)
  *   "profile"     1 = time every pair-kernel launch of dem_step with a pair
  *                 of CUDA events on the context's stream (inside the
  *                 captured graph too); setting it resets the totals

@@ -17,6 +17,7 @@ using namespace dem;
 namespace {
 
 constexpr double WCA_CUT = 1.122462048309373;   // 2^(1/6)
+constexpr double CELL_MARGIN = 0.05;           // fraction a box may shrink before its grid is redone
 thread_local std::string g_create_error;
 
 // ---------------------------------------------------------------------------
@@ -393,11 +394,14 @@ struct dem_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph = nullptr;
-    double g_dt = 0, g_kT = 0, g_tau = 0;
+    double g_dt = 0, g_kT = 0, g_tau = 0, g_P = 0, g_tauP = 0;
     int g_ens = -1;
-    // thermostat parameters of the last NVT call (conserved quantity)
-    double last_kT = 1.0, last_tau = 1.0;
+    // thermostat / barostat parameters of the last NVT or NPT call (conserved quantity)
+    double last_kT = 1.0, last_tau = 1.0, last_P = 0.0, last_tauP = 1.0;
     int last_ens = DEM_NVE;
+    // barostat (dem_set_barostat) and the steps per NPT chunk
+    double P = 0.0, tau_P = 0.0;
+    int npt_chunk = 100;
     // device memory
     double4_32a *pos = nullptr, *vel = nullptr, *quat = nullptr, *angmom = nullptr;
     double4_32a *force = nullptr, *torque = nullptr, *x_last = nullptr;
@@ -405,7 +409,7 @@ struct dem_ctx {
     int *shape = nullptr, *rep = nullptr, *nn = nullptr;
     float4 *nlist = nullptr, *delta = nullptr;
     int *cell_count = nullptr, *cell_slots = nullptr;
-    double *energy = nullptr, *virial = nullptr, *ke = nullptr;
+    double *energy = nullptr, *virial = nullptr, *ke = nullptr, *ket = nullptr;
     double *staging = nullptr;        // N * 4 doubles
     double *red = nullptr;            // R * 6 doubles
     double *scale3 = nullptr;         // R * 3
@@ -421,6 +425,7 @@ struct dem_ctx {
     // snapshot for the overflow retry
     double4_32a *snap = nullptr;
     Thermo *snap_thermo = nullptr;
+    Rep *snap_reps = nullptr;
     bool have_state = false;
     long long rebuilds = 0;
     // kernel launches issued (a graph replay counts each of its kernels)
@@ -540,13 +545,20 @@ int setup_replicas(dem_ctx *ctx) {
                     return set_err(ctx, DEM_ERR_BOX,
                                    "replica %d: box edge %g below twice the list cutoff %g", r,
                                    rp.L[a], rlist);
-                rp.nc[a] = (int)floor(rp.L[a] / rlist);
+                // cells keep a margin so that a barostat may shrink the box by
+                // CELL_MARGIN before the grid has to be rebuilt on the host
+                rp.nc[a] = (int)floor(rp.L[a] * (1.0 - CELL_MARGIN) / rlist);
                 if (rp.nc[a] < 3) rp.allpairs = 1;
                 vol *= rp.L[a];
             } else {
                 rp.nc[a] = 1;
             }
         }
+        rp.r_list = rlist;
+        rp.L_build0 = rp.L[0];
+        rp.sc_d = 1.0;
+        rp.sc = 1.f;
+        rp.disp_pad = 0.f;
         double rho = rp.n / vol;
         double expect = ctx->dim == 3 ? 4.18879 * rlist * rlist * rlist * rho : 3.14159 * rlist * rlist * rho;
         worst_ratio = std::max(worst_ratio, expect);
@@ -608,12 +620,16 @@ NlistArgs nlist_args(dem_ctx *ctx) {
     a.nlist = ctx->nlist; a.nn = ctx->nn; a.x_last = ctx->x_last; a.status = ctx->status;
     a.delta = ctx->delta;
     a.half_skin2 = (float)(0.25 * ctx->skin * ctx->skin);
+    a.reps_rw = ctx->d_reps;
     return a;
 }
 
 StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     StepArgs a = {};
-    a.n = ctx->N; a.dim = ctx->dim; a.n_reps = ctx->R; a.dt = dt; a.nvt = ens == DEM_NVT;
+    a.n = ctx->N; a.dim = ctx->dim; a.n_reps = ctx->R; a.dt = dt;
+    a.nvt = ens == DEM_NVT || ens == DEM_NPT;
+    a.npt = ens == DEM_NPT;
+    a.P = ctx->P; a.tau_P = ctx->tau_P;
     a.kT = kT; a.tau = tau;
     a.pos = ctx->pos; a.vel = ctx->vel; a.quat = ctx->quat; a.angmom = ctx->angmom;
     a.x_last = ctx->x_last; a.quatf = ctx->quatf; a.delta = ctx->delta;
@@ -621,6 +637,7 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     a.shape = ctx->shape; a.rep = ctx->rep; a.reps = ctx->d_reps; a.shapes = ctx->d_shapes;
     a.ke = ctx->ke; a.thermo = ctx->thermo; a.status = ctx->status;
     a.rotor32 = ctx->precision != DEM_FP64;
+    a.ket = ctx->ket; a.virial = ctx->virial; a.reps_rw = ctx->d_reps;
     return a;
 }
 
@@ -641,12 +658,16 @@ int launch_forces(dem_ctx *ctx, bool count, cudaEvent_t e0 = nullptr, cudaEvent_
 int launch_step(dem_ctx *ctx, double dt, int ens, double kT, double tau,
                 cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
     StepArgs sa = step_args(ctx, dt, ens, kT, tau);
+    if (ens == DEM_NPT) {
+        CK(launch_box(sa, ctx->stream));
+        ctx->launches += 1;
+    }
     CK(launch_first_half(sa, ctx->stream));
     int rc = launch_forces(ctx, false, e0, e1);
     if (rc) return rc;
-    ctx->launches += ens == DEM_NVT ? 4 : 2;
+    ctx->launches += ens != DEM_NVE ? 4 : 2;
     CK(launch_second_half(sa, ctx->stream));
-    if (ens == DEM_NVT) {
+    if (ens != DEM_NVE) {
         CK(launch_thermo_end(sa, ctx->stream));
         CK(launch_scale(sa, ctx->stream));
     }
@@ -661,8 +682,9 @@ int read_status(dem_ctx *ctx, Status *st) {
 }
 
 int clear_flags(dem_ctx *ctx) {
-    // nlist_overflow, cell_overflow, nonfinite
+    // nlist_overflow, cell_overflow, nonfinite; box_limit
     CK(cudaMemsetAsync(&ctx->status->nlist_overflow, 0, 3 * sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(&ctx->status->box_limit, 0, sizeof(int), ctx->stream));
     return DEM_OK;
 }
 
@@ -721,6 +743,7 @@ int snapshot(dem_ctx *ctx, bool restore) {
     if (!ctx->snap) {
         CK(dalloc(&ctx->snap, 7 * n));
         CK(dalloc(&ctx->snap_thermo, (size_t)ctx->R));
+        CK(dalloc(&ctx->snap_reps, (size_t)ctx->R));
     }
     double4_32a *arrs[7] = {ctx->pos, ctx->vel, ctx->quat, ctx->angmom, ctx->force, ctx->torque, ctx->x_last};
     for (int k = 0; k < 7; ++k) {
@@ -729,10 +752,13 @@ int snapshot(dem_ctx *ctx, bool restore) {
         else
             CK(cudaMemcpyAsync(ctx->snap + k * n, arrs[k], sizeof(double4_32a) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     }
-    if (restore)
+    if (restore) {
         CK(cudaMemcpyAsync(ctx->thermo, ctx->snap_thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToDevice, ctx->stream));
-    else
+        CK(cudaMemcpyAsync(ctx->d_reps, ctx->snap_reps, sizeof(Rep) * ctx->R, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
         CK(cudaMemcpyAsync(ctx->snap_thermo, ctx->thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->snap_reps, ctx->d_reps, sizeof(Rep) * ctx->R, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     if (restore) {
         // float copy of the orientations
         CK(launch_prepare_state(ctx->N, ctx->dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom,
@@ -747,7 +773,8 @@ int snapshot(dem_ctx *ctx, bool restore) {
 // they are pointed at a fresh pair of events.
 int get_graph(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     if (ctx->graph && ctx->g_dt == dt && ctx->g_ens == ens && ctx->g_kT == kT &&
-        ctx->g_tau == tau && (ctx->ev_node[0] != nullptr) == ctx->profile)
+        ctx->g_tau == tau && ctx->g_P == ctx->P && ctx->g_tauP == ctx->tau_P &&
+        (ctx->ev_node[0] != nullptr) == ctx->profile)
         return DEM_OK;
     free_graph(ctx);
     if (ctx->profile && !ctx->cap_ev[0]) {
@@ -786,6 +813,7 @@ int get_graph(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     if (ctx->profile && (!ctx->ev_node[0] || !ctx->ev_node[1]))
         return set_err(ctx, DEM_ERR_CUDA, "profiling events missing from the captured step");
     ctx->g_dt = dt; ctx->g_ens = ens; ctx->g_kT = kT; ctx->g_tau = tau;
+    ctx->g_P = ctx->P; ctx->g_tauP = ctx->tau_P;
     return DEM_OK;
 }
 
@@ -835,7 +863,7 @@ void dem_destroy(dem_ctx *ctx) {
                     ctx->cell_count, ctx->cell_slots, ctx->energy, ctx->virial, ctx->ke,
                     ctx->staging, ctx->red, ctx->scale3, ctx->status, ctx->thermo, ctx->d_reps,
                     ctx->d_shapes, ctx->d_geoms, ctx->d_table, ctx->d_itable, ctx->d_counters,
-                    ctx->snap, ctx->snap_thermo};
+                    ctx->snap, ctx->snap_thermo, ctx->snap_reps, ctx->ket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
@@ -917,7 +945,7 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
         CK(dalloc(&ctx->x_last, n)); CK(dalloc(&ctx->quatf, n)); CK(dalloc(&ctx->delta, n));
         CK(cudaMemset(ctx->delta, 0, sizeof(float4) * n));
         CK(dalloc(&ctx->shape, n)); CK(dalloc(&ctx->rep, n)); CK(dalloc(&ctx->nn, n));
-        CK(dalloc(&ctx->energy, n)); CK(dalloc(&ctx->virial, 6 * n)); CK(dalloc(&ctx->ke, n));
+        CK(dalloc(&ctx->energy, n)); CK(dalloc(&ctx->virial, 6 * n)); CK(dalloc(&ctx->ke, n)); CK(dalloc(&ctx->ket, n));
         CK(dalloc(&ctx->staging, 4 * n));
         CK(dalloc(&ctx->red, 6 * (size_t)ctx->R)); CK(dalloc(&ctx->scale3, 3 * (size_t)ctx->R));
         CK(dalloc(&ctx->status, 1)); CK(dalloc(&ctx->thermo, (size_t)ctx->R));
@@ -969,6 +997,9 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
             rc = force_rebuild(ctx);
             if (rc) return rc;
         }
+    } else if (n == "npt_chunk") {
+        if (!(value >= 1) || value > 1e9) return set_err(ctx, DEM_ERR_ARG, "npt_chunk must be >= 1");
+        ctx->npt_chunk = (int)value;
     } else if (n == "par_eps") {
         if (!(value >= 0)) return set_err(ctx, DEM_ERR_ARG, "par_eps must be >= 0");
         ctx->par_eps = value;
@@ -1010,6 +1041,7 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
     std::string n(name);
     if (n == "skin") *value = ctx->skin < 0 ? max_sigma(ctx) : ctx->skin;
     else if (n == "par_eps") *value = ctx->par_eps;
+    else if (n == "npt_chunk") *value = ctx->npt_chunk;
     else if (n == "decomp") *value = ctx->decomp;
     else if (n == "block") *value = ctx->block;
     else if (n == "graph") *value = ctx->use_graph;
@@ -1109,7 +1141,11 @@ int dem_get_state(dem_ctx *ctx, double *pos, double *orient, double *vel, double
         std::vector<Thermo> th(ctx->R);
         CK(cudaMemcpyAsync(th.data(), ctx->thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
-        for (int r = 0; r < ctx->R; ++r) { thermostat[2 * r] = th[r].xi; thermostat[2 * r + 1] = th[r].eta; }
+        for (int r = 0; r < ctx->R; ++r) {
+            thermostat[3 * r] = th[r].xi;
+            thermostat[3 * r + 1] = th[r].eta;
+            thermostat[3 * r + 2] = th[r].pe;
+        }
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return DEM_OK;
@@ -1120,7 +1156,11 @@ int dem_set_thermostat(dem_ctx *ctx, const double *thermostat) {
     std::vector<Thermo> th(ctx->R);
     CK(cudaMemcpyAsync(th.data(), ctx->thermo, sizeof(Thermo) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    for (int r = 0; r < ctx->R; ++r) { th[r].xi = thermostat[2 * r]; th[r].eta = thermostat[2 * r + 1]; }
+    for (int r = 0; r < ctx->R; ++r) {
+        th[r].xi = thermostat[3 * r];
+        th[r].eta = thermostat[3 * r + 1];
+        th[r].pe = thermostat[3 * r + 2];
+    }
     CK(cudaMemcpyAsync(ctx->thermo, th.data(), sizeof(Thermo) * ctx->R, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return DEM_OK;
@@ -1132,14 +1172,14 @@ int dem_compute(dem_ctx *ctx) {
     return compute_forces(ctx);
 }
 
-int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T) {
-    if (!valid(ctx)) return DEM_ERR_ARG;
-    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
-    if (n < 0 || !(dt > 0) || (ensemble != DEM_NVE && ensemble != DEM_NVT))
-        return set_err(ctx, DEM_ERR_ARG, "bad step arguments");
-    if (ensemble == DEM_NVT && (!(kT > 0) || !(tau_T > 0)))
-        return set_err(ctx, DEM_ERR_ARG, "NVT needs kT > 0 and tau_T > 0");
-    if (n == 0) return DEM_OK;
+}  // extern "C"
+
+namespace {
+
+// n steps with no host work in between (graph replays or launches), with the
+// overflow retry: the state is snapshotted, and after a list or cell overflow
+// the capacities grow and the steps are replayed from the snapshot.
+int step_run(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T) {
     int rc;
     for (int attempt = 0; attempt < 4; ++attempt) {
         rc = snapshot(ctx, false);
@@ -1147,8 +1187,14 @@ int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau
         rc = clear_flags(ctx);
         if (rc) return rc;
         StepArgs sa = step_args(ctx, dt, ensemble, kT, tau_T);
-        if (ensemble == DEM_NVT) CK(launch_thermo_begin(sa, ctx->stream));
-        if (ensemble == DEM_NVT) ctx->launches += 1;
+        if (ensemble == DEM_NPT) {
+            CK(launch_kinetic(sa, ctx->stream));
+            ctx->launches += 1;
+        }
+        if (ensemble != DEM_NVE) {
+            CK(launch_thermo_begin(sa, ctx->stream));
+            ctx->launches += 1;
+        }
         if (ctx->profile) {
             rc = ensure_events(ctx, 2 * (size_t)n);
             if (rc) return rc;
@@ -1196,11 +1242,81 @@ int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau
             continue;
         }
         if (st.nonfinite) return set_err(ctx, DEM_ERR_NONFINITE, "non-finite force or energy");
-        if (ensemble == DEM_NVT) { ctx->last_kT = kT; ctx->last_tau = tau_T; }
-        ctx->last_ens = ensemble;
+        if (st.box_limit)
+            return set_err(ctx, DEM_ERR_BOX,
+                           "a barostat moved a box beyond its cell grid or below twice the list "
+                           "cutoff within %d steps (lower the npt_chunk parameter)", n);
         return DEM_OK;
     }
     return set_err(ctx, DEM_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+}
+
+// After NPT steps: the boxes come back to the host, the cell grids and list
+// cutoffs follow them, and the list is rebuilt in the new boxes.
+int sync_boxes(dem_ctx *ctx) {
+    std::vector<Rep> hr(ctx->R);
+    CK(cudaMemcpyAsync(hr.data(), ctx->d_reps, sizeof(Rep) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < ctx->R; ++r)
+        for (int a = 0; a < ctx->dim; ++a) ctx->box[3 * r + a] = hr[r].L[a];
+    int rc = setup_replicas(ctx);
+    if (rc) return rc;
+    return force_rebuild(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
+    if (n < 0 || !(dt > 0) || (ensemble != DEM_NVE && ensemble != DEM_NVT && ensemble != DEM_NPT))
+        return set_err(ctx, DEM_ERR_ARG, "bad step arguments");
+    if (ensemble != DEM_NVE && (!(kT > 0) || !(tau_T > 0)))
+        return set_err(ctx, DEM_ERR_ARG, "NVT and NPT need kT > 0 and tau_T > 0");
+    if (ensemble == DEM_NPT) {
+        if (!(ctx->tau_P > 0))
+            return set_err(ctx, DEM_ERR_ARG, "NPT needs dem_set_barostat (tau_P > 0)");
+        for (int r = 0; r < ctx->R; ++r)
+            if (ctx->sizes[r] < 2)
+                return set_err(ctx, DEM_ERR_ARG, "NPT needs at least 2 particles per replica");
+    }
+    if (n == 0) return DEM_OK;
+    int rc;
+    if (ensemble == DEM_NPT) {
+        for (int done = 0; done < n;) {
+            const int m = std::min(ctx->npt_chunk, n - done);
+            rc = step_run(ctx, m, dt, ensemble, kT, tau_T);
+            if (rc == DEM_OK) rc = sync_boxes(ctx);
+            if (rc) return rc;
+            done += m;
+        }
+        ctx->last_P = ctx->P;
+        ctx->last_tauP = ctx->tau_P;
+    } else {
+        rc = step_run(ctx, n, dt, ensemble, kT, tau_T);
+        if (rc) return rc;
+    }
+    if (ensemble != DEM_NVE) { ctx->last_kT = kT; ctx->last_tau = tau_T; }
+    ctx->last_ens = ensemble;
+    return DEM_OK;
+}
+
+int dem_set_barostat(dem_ctx *ctx, double P, double tau_P) {
+    if (!valid(ctx)) return DEM_ERR_ARG;
+    if (!(P >= 0) || !isfinite(P) || !(tau_P > 0) || !isfinite(tau_P))
+        return set_err(ctx, DEM_ERR_ARG, "barostat needs P >= 0 and tau_P > 0");
+    ctx->P = P;
+    ctx->tau_P = tau_P;
+    return DEM_OK;
+}
+
+int dem_get_box(dem_ctx *ctx, double *box) {
+    if (!valid(ctx) || !box) return DEM_ERR_ARG;
+    for (int r = 0; r < ctx->R; ++r)
+        for (int a = 0; a < ctx->dim; ++a) box[ctx->dim * r + a] = ctx->box[3 * r + a];
+    return DEM_OK;
 }
 
 int dem_get_forces(dem_ctx *ctx, double *force, double *torque, int device_ptrs) {
@@ -1253,6 +1369,16 @@ int dem_get_energy(dem_ctx *ctx, double *U, double *K, double *conserved) {
             if (ctx->last_ens == DEM_NVT) {
                 double g = ctx->reps[r].g_dof;
                 c += g * ctx->last_kT * (0.5 * ctx->last_tau * ctx->last_tau * th[r].xi * th[r].xi + th[r].eta);
+            }
+            if (ctx->last_ens == DEM_NPT) {
+                // K + U + p_e^2/2W + P V + (g + 1) kT (tau^2 xi^2 / 2 + eta)
+                const double g1 = ctx->reps[r].g_dof + 1.0, d = ctx->dim;
+                const double W = (d * (ctx->sizes[r] - 1.0) + d) * ctx->last_kT * ctx->last_tauP *
+                                 ctx->last_tauP;
+                double V = 1.0;
+                for (int a = 0; a < ctx->dim; ++a) V *= ctx->box[3 * r + a];
+                c += 0.5 * th[r].pe * th[r].pe / W + ctx->last_P * V +
+                     g1 * ctx->last_kT * (0.5 * ctx->last_tau * ctx->last_tau * th[r].xi * th[r].xi + th[r].eta);
             }
             conserved[r] = c;
         }

@@ -74,6 +74,12 @@ struct Rep {
     int nc[3];           // cells per axis
     int allpairs;        // 1: neighbour search over all particles of the replica
     int g_dof;           // degrees of freedom for the thermostat (as int)
+    double r_list;       // neighbour-list cutoff (largest pair range + skin)
+    double L_build0;     // L[0] when the list was last built
+    double sc_d;         // L[0] / L_build0: list separations scale with the box (NPT)
+    float sc;            // FP32 copy of sc_d for the FP32 pair kernels
+    float disp_pad;      // 0.5 max(0, 1 - sc) r_list, added to displacements in the
+                         // rebuild test so that a shrinking box cannot hide a pair
 };
 
 // Device status word block.
@@ -85,7 +91,8 @@ struct Status {
     int nonfinite;           // 1 if a non-finite force/energy was produced
     int rebuilds;            // rebuild counter
     int built;               // set by the list build when it ran this step
-    int pad;
+    int box_limit;           // NPT: a box fell below what its cell grid or minimum
+                             // image allows within the call
 };
 
 // Per-replica thermostat state (FP64): canonical end-of-step values and the
@@ -95,6 +102,10 @@ struct Thermo {
     double xi_h, eta_h;      // after this step's first half step
     double s1;               // velocity scale of this step's first half step
     double s2;               // velocity scale of this step's second half step
+    double pe;               // NPT: barostat momentum (canonical)
+    double pe_h;             // NPT: after this step's first half step
+    double av, bv;           // NPT: v <- av v + bv F/m (half kick with dilation)
+    double ax, bx;           // NPT: x <- ax x + bx v, box <- ax box (drift)
     double pad;
 };
 
@@ -136,6 +147,7 @@ struct NlistArgs {
     float4 *delta;
     Status *status;
     float half_skin2;        // rebuild threshold (skin/2)^2
+    Rep *reps_rw;            // a rebuild records the box it was built in
 };
 
 struct StepArgs {
@@ -153,6 +165,11 @@ struct StepArgs {
     Thermo *thermo;
     Status *status;
     int rotor32;             // FP32 modes: free-rotor increments in FP32
+    int npt;                 // isotropic barostat (ensemble DEM_NPT)
+    double P, tau_P;         // NPT pressure and barostat time
+    double *ket;             // NPT: translational kinetic energy per particle
+    const double *virial;    // per-particle virial (xx, xy, xz, yy, yz, zz)
+    Rep *reps_rw;            // the replica records (NPT moves the box)
 };
 
 // ---- launch wrappers (pair.cu, nlist.cu, integrate.cu) ----
@@ -168,6 +185,7 @@ cudaError_t launch_first_half(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_second_half(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_thermo_begin(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_thermo_end(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_box(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_scale(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_kinetic(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_replica_sums(int n_reps, const Rep *reps, const double *per_particle,

@@ -163,12 +163,24 @@ __global__ void k_first_half(const StepArgs a) {
             v.x *= s; v.y *= s; v.z *= s;
             L.x *= s; L.y *= s; L.z *= s;
         }
-        const double h = 0.5 * a.dt * sh.inv_mass;
-        v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
-        L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
-        x.x = wrap(x.x + a.dt * v.x, rp.L[0], rp.inv_L[0]);
-        x.y = wrap(x.y + a.dt * v.y, rp.L[1], rp.inv_L[1]);
-        if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2], rp.inv_L[2]);
+        if (a.npt) {
+            // half kick and drift with the box dilation (the box itself moved
+            // by ax in k_box before this kernel)
+            const Thermo &t = a.thermo[r];
+            const double b = t.bv * sh.inv_mass;
+            v.x = t.av * v.x + b * F.x; v.y = t.av * v.y + b * F.y; v.z = t.av * v.z + b * F.z;
+            L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
+            x.x = wrap(t.ax * x.x + t.bx * v.x, rp.L[0], rp.inv_L[0]);
+            x.y = wrap(t.ax * x.y + t.bx * v.y, rp.L[1], rp.inv_L[1]);
+            if (a.dim == 3) x.z = wrap(t.ax * x.z + t.bx * v.z, rp.L[2], rp.inv_L[2]);
+        } else {
+            const double h = 0.5 * a.dt * sh.inv_mass;
+            v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
+            L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
+            x.x = wrap(x.x + a.dt * v.x, rp.L[0], rp.inv_L[0]);
+            x.y = wrap(x.y + a.dt * v.y, rp.L[1], rp.inv_L[1]);
+            if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2], rp.inv_L[2]);
+        }
         if (a.rotor32) {
             free_rotor_f32(q, L, sh.inv_inertia, a.dt);
         } else {
@@ -185,12 +197,20 @@ __global__ void k_first_half(const StepArgs a) {
         a.angmom[i] = L;
         a.quat[i] = q;
         a.quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+        // displacement since the list build; the build position scales with
+        // the box (sc = 1 unless a barostat moved it)
         double4_32a x0 = a.x_last[i];
-        double dx = x.x - x0.x, dy = x.y - x0.y, dz = x.z - x0.z;
+        const double sc = rp.sc_d;
+        double dx = x.x - sc * x0.x, dy = x.y - sc * x0.y, dz = x.z - sc * x0.z;
         dx -= rp.L[0] * rint(dx * rp.inv_L[0]);
         dy -= rp.L[1] * rint(dy * rp.inv_L[1]);
         if (a.dim == 3) dz -= rp.L[2] * rint(dz * rp.inv_L[2]); else dz = 0.0;
-        dmax = fmaxf(dmax, (float)(dx * dx + dy * dy + dz * dz));
+        double d2 = dx * dx + dy * dy + dz * dz;
+        if (rp.disp_pad > 0.f) {
+            const double d = sqrt(d2) + (double)rp.disp_pad;
+            d2 = d * d;
+        }
+        dmax = fmaxf(dmax, (float)d2);
         a.delta[i] = make_float4((float)dx, (float)dy, (float)dz, __int_as_float(a.shape[i]));
     }
     // warp max, one atomic per warp (non-negative floats order like their bits)
@@ -207,12 +227,23 @@ __device__ __forceinline__ double kinetic_of(const ShapeDev &sh, const double4_3
     return k;
 }
 
+__device__ __forceinline__ double kinetic_trans(const ShapeDev &sh, const double4_32a &v) {
+    return 0.5 * sh.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+}
+
 __global__ void k_second_half(const StepArgs a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const ShapeDev &sh = a.shapes[a.shape[i]];
         double4_32a v = a.vel[i], L = a.angmom[i], F = a.force[i], Tq = a.torque[i];
-        const double h = 0.5 * a.dt * sh.inv_mass;
-        v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
+        if (a.npt) {
+            const Thermo &t = a.thermo[a.rep[i]];
+            const double b = t.bv * sh.inv_mass;
+            v.x = t.av * v.x + b * F.x; v.y = t.av * v.y + b * F.y; v.z = t.av * v.z + b * F.z;
+            a.ket[i] = kinetic_trans(sh, v);
+        } else {
+            const double h = 0.5 * a.dt * sh.inv_mass;
+            v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
+        }
         L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
         a.vel[i] = v;
         a.angmom[i] = L;
@@ -221,8 +252,12 @@ __global__ void k_second_half(const StepArgs a) {
 }
 
 __global__ void k_kinetic(const StepArgs a) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
-        a.ke[i] = kinetic_of(a.shapes[a.shape[i]], a.vel[i], a.angmom[i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const ShapeDev &sh = a.shapes[a.shape[i]];
+        const double4_32a v = a.vel[i];
+        a.ke[i] = kinetic_of(sh, v, a.angmom[i]);
+        if (a.ket) a.ket[i] = kinetic_trans(sh, v);
+    }
 }
 
 // Fixed-order block sum of x[off..off+n) (deterministic).
@@ -279,6 +314,132 @@ __global__ void k_thermo_begin(const StepArgs a) {
     t.eta_h = t.eta + xh * d;
     t.xi_h = xh + 0.5 * d * nh_rate(t.K * s1 * s1, g, a.kT, a.tau);
     t.s1 = s1;
+}
+
+// ---- isotropic barostat (NPT) ----
+// sinh(x)/x (Maclaurin series below |x| = 1e-2, remainder < 1e-17)
+__device__ __forceinline__ double sinhc(double x) {
+    if (fabs(x) < 1e-2) {
+        const double x2 = x * x;
+        return 1.0 + x2 / 6.0 * (1.0 + x2 / 20.0 * (1.0 + x2 / 42.0));
+    }
+    return sinh(x) / x;
+}
+
+struct NptConst {
+    double W;        // barostat mass (N_f + d) kT tau_P^2
+    double alpha;    // 1 + d / N_f, N_f = d (N - 1)
+    double g1;       // thermostat degrees of freedom: g + 1 (the barostat)
+    double V;        // current volume
+    double dim;
+};
+
+__device__ __forceinline__ NptConst npt_const(const StepArgs &a, const Rep &rp) {
+    NptConst c;
+    const double nf = a.dim * (rp.n - 1.0);
+    c.W = (nf + a.dim) * a.kT * a.tau_P * a.tau_P;
+    c.alpha = 1.0 + a.dim / nf;
+    c.g1 = (double)rp.g_dof + 1.0;
+    c.V = rp.L[0] * rp.L[1] * (a.dim == 3 ? rp.L[2] : 1.0);
+    c.dim = (double)a.dim;
+    return c;
+}
+
+// First half of a step from the canonical state (t.xi, t.eta, t.pe) with the
+// replica's translational and rotational kinetic energies Kt, Kr and virial
+// trace vir: thermostat T(dt/2) on the particles and the barostat momentum,
+// barostat B(dt/2): p_e += dt/2 (alpha 2 K_t + Tr W - d V P), then the
+// factors of the dilating half kick, v <- av v + bv F/m, and of the drift,
+// x <- ax x + bx v (box <- ax box), each the exact solution of its sub-step.
+__device__ void npt_first_half(const StepArgs &a, Thermo &t, const NptConst &c, double Kt,
+                               double Kr, double vir) {
+    const double d = 0.5 * a.dt;
+    double Ktot = Kt + Kr + 0.5 * t.pe * t.pe / c.W;
+    const double xh = t.xi + 0.5 * d * nh_rate(Ktot, c.g1, a.kT, a.tau);
+    const double s1 = exp(-xh * d);
+    t.eta_h = t.eta + xh * d;
+    Ktot *= s1 * s1;
+    t.xi_h = xh + 0.5 * d * nh_rate(Ktot, c.g1, a.kT, a.tau);
+    t.s1 = s1;
+    const double pe = t.pe * s1 + d * (c.alpha * 2.0 * Kt * s1 * s1 + vir - c.dim * c.V * a.P);
+    t.pe_h = pe;
+    const double ve = pe / c.W;
+    t.av = exp(-c.alpha * ve * d);
+    t.bv = d * exp(-0.5 * c.alpha * ve * d) * sinhc(0.5 * c.alpha * ve * d);
+    t.ax = exp(ve * a.dt);
+    t.bx = a.dt * exp(0.5 * ve * a.dt) * sinhc(0.5 * ve * a.dt);
+}
+
+// Replica sums of the NPT state: total and translational kinetic energy and
+// the virial trace (fixed order).
+__device__ __forceinline__ void npt_sums(const StepArgs &a, const Rep &rp, double *K, double *Kt,
+                                         double *vir) {
+    *K = block_sum(a.ke, rp.off, rp.n, 1, 0);
+    *Kt = block_sum(a.ket, rp.off, rp.n, 1, 0);
+    *vir = block_sum(a.virial, rp.off, rp.n, 6, 0) + block_sum(a.virial, rp.off, rp.n, 6, 3) +
+           (a.dim == 3 ? block_sum(a.virial, rp.off, rp.n, 6, 5) : 0.0);
+}
+
+// One block per replica, end of an NPT step (after the second half kick):
+// B(dt/2) and T(dt/2) of this step, then the first half of the next one.
+__global__ void k_thermo_end_npt(const StepArgs a) {
+    const int r = blockIdx.x;
+    const Rep &rp = a.reps[r];
+    double K, Kt, vir;
+    npt_sums(a, rp, &K, &Kt, &vir);
+    if (threadIdx.x == 0) {
+        Thermo &t = a.thermo[r];
+        const NptConst c = npt_const(a, rp);
+        const double d = 0.5 * a.dt;
+        double Kr = K - Kt;
+        double pe = t.pe_h + d * (c.alpha * 2.0 * Kt + vir - c.dim * c.V * a.P);
+        double Ktot = Kt + Kr + 0.5 * pe * pe / c.W;
+        double xi = t.xi_h + 0.5 * d * nh_rate(Ktot, c.g1, a.kT, a.tau);
+        const double s2 = exp(-xi * d);
+        const double eta = t.eta_h + xi * d;
+        Ktot *= s2 * s2;
+        Kt *= s2 * s2;
+        Kr *= s2 * s2;
+        pe *= s2;
+        xi += 0.5 * d * nh_rate(Ktot, c.g1, a.kT, a.tau);
+        t.xi = xi; t.eta = eta; t.pe = pe; t.K = Kt + Kr;
+        t.s2 = s2;
+        npt_first_half(a, t, c, Kt, Kr, vir);
+    }
+}
+
+// One block per replica, start of an NPT call: the first half step from the
+// canonical state (ke and ket current, forces and virial current).
+__global__ void k_thermo_begin_npt(const StepArgs a) {
+    const int r = blockIdx.x;
+    const Rep &rp = a.reps[r];
+    double K, Kt, vir;
+    npt_sums(a, rp, &K, &Kt, &vir);
+    if (threadIdx.x == 0) {
+        Thermo &t = a.thermo[r];
+        t.K = K;
+        npt_first_half(a, t, npt_const(a, rp), Kt, K - Kt, vir);
+    }
+}
+
+// One thread per replica, start of an NPT step: the box follows the drift
+// factor; the list scale and the rebuild pad follow the box; a box below
+// twice the list cutoff or below its cell grid's reach is flagged.
+__global__ void k_box(const StepArgs a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n_reps) return;
+    Rep &rp = a.reps_rw[r];
+    const double ax = a.thermo[r].ax;
+    for (int k = 0; k < a.dim; ++k) {
+        rp.L[k] *= ax;
+        rp.inv_L[k] = 1.0 / rp.L[k];
+        if (!(rp.L[k] >= 2.0 * rp.r_list) || (!rp.allpairs && rp.L[k] < rp.nc[k] * rp.r_list))
+            a.status->box_limit = 1;
+    }
+    const double sc = rp.L[0] / rp.L_build0;
+    rp.sc_d = sc;
+    rp.sc = (float)sc;
+    rp.disp_pad = (float)(0.5 * fmax(0.0, 1.0 - sc) * rp.r_list);
 }
 
 __global__ void k_scale(const StepArgs a) {
@@ -444,11 +605,18 @@ cudaError_t launch_kinetic(const StepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_thermo_end(const StepArgs &a, cudaStream_t s) {
-    k_thermo_end<<<a.n_reps, 256, 0, s>>>(a);
+    if (a.npt) k_thermo_end_npt<<<a.n_reps, 256, 0, s>>>(a);
+    else k_thermo_end<<<a.n_reps, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box(const StepArgs &a, cudaStream_t s) {
+    k_box<<<(a.n_reps + 127) / 128, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_thermo_begin(const StepArgs &a, cudaStream_t s) {
-    k_thermo_begin<<<grid_for(a.n_reps, 128), 128, 0, s>>>(a);
+    if (a.npt) k_thermo_begin_npt<<<a.n_reps, 256, 0, s>>>(a);
+    else k_thermo_begin<<<grid_for(a.n_reps, 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_scale(const StepArgs &a, cudaStream_t s) {

@@ -120,6 +120,15 @@ __global__ void k_nlist(const NlistArgs a) {
         a.nn[i] = count;
         a.x_last[i] = xi;
         a.delta[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(a.shape[i]));   // w: shape index
+        if (i == rp.off && a.reps_rw) {
+            // the list of this replica is now in its current box
+            Rep &w = a.reps_rw[a.rep[i]];
+            const double L0 = rp.L[0];
+            w.L_build0 = L0;
+            w.sc_d = 1.0;
+            w.sc = 1.f;
+            w.disp_pad = 0.f;
+        }
     }
 }
 

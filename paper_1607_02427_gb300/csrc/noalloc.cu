@@ -129,6 +129,11 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     rp.n = n;
     rp.allpairs = 1;
     rp.g_dof = 0;
+    rp.r_list = range;
+    rp.L_build0 = rp.L[0];
+    rp.sc_d = 1.0;
+    rp.sc = 1.f;
+    rp.disp_pad = 0.f;
 
     void *base = nullptr;
     rc = scratch_base(&base, &err);

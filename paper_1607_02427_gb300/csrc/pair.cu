@@ -130,7 +130,8 @@ template <class T> struct alignas(16) PInfo {   // one particle of the warp
     T r[9];              // R_i
     T x[3];              // FP32: delta_i; FP64: position
     T R, rnd, sig_all;
-    int geom, rep, nn, pad;
+    int geom, rep, nn;
+    float sc;            // FP32 list separation scale of the replica
 };
 template <class T> struct WarpSmem {
     QPair<T> q[PQ];
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
             pi.sig_all = sig_all;
             pi.geom = shi.geom;
             pi.rep = a.rep[i_me];
+            pi.sc = a.reps[pi.rep].sc;
             nn_me = a.nn[i_me];
             pi.nn = nn_me;
         }
@@ -254,6 +256,7 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
                 const Geom &gi = geo[pi.geom];
                 Owner<T> own;
                 own.rp = &a.reps[pi.rep];
+                own.sc = pi.sc;
                 own.R = pi.R;
                 own.rnd = pi.rnd;
                 own.sig_all = pi.sig_all;

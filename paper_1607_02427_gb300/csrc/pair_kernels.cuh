@@ -34,6 +34,7 @@ __device__ __forceinline__ void stage_tables(const PairArgs &a, typename R4T<T>:
 
 // Particle i's data for the range tests of its list entries.
 template <class T> struct Owner {
+    float sc;            // FP32 modes: list separation scale (1 unless a barostat moved the box)
     float4 delta;        // FP32 modes
     double4_32a x;       // FP64 mode
     T R, rnd;
@@ -62,9 +63,9 @@ __device__ __forceinline__ bool in_range(const PairArgs &a, const float4 &e, con
         pg->qj = a.quatf[j];
         const ShapeDev &shj = a.shapes[__float_as_int(dj.w)];
         pg->gj = shj.geom;
-        const float dx = e.x + (dj.x - o.delta.x);
-        const float dy = e.y + (dj.y - o.delta.y);
-        const float dz = e.z + (dj.z - o.delta.z);
+        const float dx = fmaf(e.x, o.sc, dj.x - o.delta.x);
+        const float dy = fmaf(e.y, o.sc, dj.y - o.delta.y);
+        const float dz = fmaf(e.z, o.sc, dj.z - o.delta.z);
         const float sig = o.sig_all > 0.f ? o.sig_all : o.rnd + shj.rounding_f;
         const float lim = o.R + shj.R + (float)WCA_CUT * sig;
         if (!(dx * dx + dy * dy + dz * dz < lim * lim)) return false;
@@ -112,6 +113,7 @@ __device__ __forceinline__ Owner<T> make_owner(const PairArgs &a, int i, const S
                                                const Geom &gi) {
     Owner<T> o;
     o.rp = &a.reps[a.rep[i]];
+    o.sc = o.rp->sc;
     o.R = (T)gi.R;
     o.geom = shi.geom;
     o.sig_all = a.sigma > 0.0 ? (T)a.sigma : T(0);

@@ -54,7 +54,8 @@ template <class T> struct SPair {      // a queued active pair
 template <class T> struct SInfo {      // one particle of the warp
     typename R4T<T>::type row[3];      // (R_i[r][0..2], x[r]); x: FP32 delta_i, FP64 position
     T rnd;
-    int geom, rep, pad;
+    int geom, rep;
+    float sc;                          // FP32 list separation scale of the replica
 };
 template <class T> struct VFItem {     // (vertex, face) after the plane test
     typename R4T<T>::type p;           // the vertex in the face owner's frame; w: its
@@ -578,6 +579,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             }
             pi.geom = shi.geom;
             pi.rep = a.rep[i_me];
+            pi.sc = a.reps[pi.rep].sc;
             nn_me = a.nn[i_me];
         }
         st.S.zero();
@@ -609,6 +611,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
                 load_rows(pi.row, &Ri, &xi);
                 Owner<T> own;
                 own.rp = &a.reps[pi.rep];
+                own.sc = pi.sc;
                 own.R = (T)gi.R;
                 own.rnd = pi.rnd;
                 own.sig_all = sig_all;

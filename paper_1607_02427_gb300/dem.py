@@ -28,7 +28,7 @@ DEM_ERR_STATE = -7
 DEM_ERR_NOMEM = -8
 
 DEM_FP64, DEM_FP32, DEM_FP32_COMP = 0, 1, 2
-DEM_NVE, DEM_NVT = 0, 1
+DEM_NVE, DEM_NVT, DEM_NPT = 0, 1, 2
 DEM_DECOMP_AUTO, DEM_DECOMP_THREAD, DEM_DECOMP_WARP, DEM_DECOMP_STAGED = 0, 1, 2, 3
 PRECISIONS = {"fp64": DEM_FP64, "fp32": DEM_FP32, "fp32c": DEM_FP32_COMP}
 
@@ -37,7 +37,7 @@ EXPORTS = ["dem_create", "dem_set_state", "dem_get_state", "dem_set_thermostat",
            "dem_compute", "dem_get_forces", "dem_get_energy", "dem_get_particle_energy",
            "dem_get_virial", "dem_set_box", "dem_set_param", "dem_get_param", "dem_autotune",
            "dem_get_counters", "dem_set_stream", "dem_shape_info", "dem_last_error",
-           "dem_destroy", "dem_forces_noalloc"]
+           "dem_destroy", "dem_forces_noalloc", "dem_set_barostat", "dem_get_box"]
 DEM_NOALLOC_MAX_N = 16384
 DEM_NOALLOC_MAX_NEIGHBOURS = 64
 
@@ -74,6 +74,8 @@ def load():
         "dem_set_state": [vp, vp, vp, vp, vp, vp, C.c_int],
         "dem_get_state": [vp, vp, vp, vp, vp, vp, C.c_int],
         "dem_set_thermostat": [vp, dp],
+        "dem_set_barostat": [vp, C.c_double, C.c_double],
+        "dem_get_box": [vp, dp],
         "dem_step": [vp, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double],
         "dem_compute": [vp],
         "dem_get_forces": [vp, vp, vp, C.c_int],
@@ -191,9 +193,22 @@ def dem_get_state(ctx, pos=None, orient=None, vel=None, angmom=None, thermostat=
 
 
 def dem_set_thermostat(ctx, thermostat):
+    """Per replica (xi, eta, p_e)."""
     lib = load()
     t = _host(thermostat, np.float64)
     return _check(lib.dem_set_thermostat(ctx, t.ctypes.data_as(C.POINTER(C.c_double))), ctx)
+
+
+def dem_set_barostat(ctx, P: float, tau_P: float):
+    lib = load()
+    return _check(lib.dem_set_barostat(ctx, float(P), float(tau_P)), ctx)
+
+
+def dem_get_box(ctx, n_replicas: int, dim: int) -> np.ndarray:
+    lib = load()
+    out = np.zeros((n_replicas, dim))
+    _check(lib.dem_get_box(ctx, out.ctypes.data_as(C.POINTER(C.c_double))), ctx)
+    return out
 
 
 def dem_step(ctx, n: int, dt: float, ensemble: int, kT: float = 1.0, tau_T: float = 1.0):
@@ -338,9 +353,10 @@ class DEM:
         orient = np.zeros((self.n, 4 if self.dim == 3 else 1))
         vel = np.zeros((self.n, self.dim))
         ang = np.zeros((self.n, 3 if self.dim == 3 else 1))
-        th = np.zeros((self.n_replicas, 2))
+        th = np.zeros((self.n_replicas, 3))
         dem_get_state(self.ctx, pos, orient, vel, ang, th)
-        return dict(pos=pos, orient=orient, vel=vel, angmom=ang, thermo=th)
+        return dict(pos=pos, orient=orient, vel=vel, angmom=ang, thermo=th,
+                    box=dem_get_box(self.ctx, self.n_replicas, self.dim))
 
     def step(self, n, dt, ensemble=DEM_NVE, kT=1.0, tau_T=0.5):
         dem_step(self.ctx, n, dt, ensemble, kT, tau_T)
@@ -359,6 +375,12 @@ class DEM:
 
     def set_box(self, box):
         dem_set_box(self.ctx, box)
+
+    def set_barostat(self, P, tau_P):
+        dem_set_barostat(self.ctx, P, tau_P)
+
+    def box(self):
+        return dem_get_box(self.ctx, self.n_replicas, self.dim)
 
     def set_thermostat(self, th):
         dem_set_thermostat(self.ctx, th)
