@@ -442,12 +442,15 @@ def measure_extras(a, dem, d, system, run, ens, prec, torch):
         sysc = _with_state(system, st)
         with dem.DEM(sysc, p) as d2:
             k = 20 if p == dem.DEM_FP64 else 200
+            dem.dem_autotune(d2.ctx)
             d2.step(3, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             d2.step(k, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
             torch.cuda.synchronize()
-            out[name] = {"value": n * k / (time.perf_counter() - t0), "unit": UNIT, "steps": k}
+            out[name] = {"value": n * k / (time.perf_counter() - t0), "unit": UNIT, "steps": k,
+                         "decomposition": {1: "thread", 2: "warp", 3: "staged"}[
+                             int(d2.get_param("decomp"))]}
     # plain FP64 single-system path: one context per replica, launch by launch
     if system.n_replicas > 1:
         sample = list(range(0, system.n_replicas, max(1, system.n_replicas // 24)))[:24]

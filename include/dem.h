@@ -238,7 +238,7 @@ int dem_set_box(dem_ctx *ctx, const double *box);
  *   "decomp"      DEM_DECOMP_* of the pair kernel
  *   "block"       threads per block of the pair kernel (0 = default)
  *   "graph"       1 = replay each step as a captured CUDA graph (default 1)
- *   "nlist_cap"   neighbour slots per particle (grown automatically)
+ *   "nlist_cap"   neighbour slots per particle (grown automatically, at most 768)
  *   "npt_chunk"   DEM_NPT steps between host updates of the cell grids (100)
  *   "profile"     1 = time every pair-kernel launch of dem_step with a pair
  *                 of CUDA events on the context's stream (inside the

@@ -18,6 +18,7 @@ namespace {
 
 constexpr double WCA_CUT = 1.122462048309373;   // 2^(1/6)
 constexpr double CELL_MARGIN = 0.05;           // fraction a box may shrink before its grid is redone
+constexpr int MAX_NLIST_CAP = 768;             // list slots per particle (the build sorts in shared memory)
 thread_local std::string g_create_error;
 
 // ---------------------------------------------------------------------------
@@ -407,9 +408,12 @@ struct dem_ctx {
     double4_32a *force = nullptr, *torque = nullptr, *x_last = nullptr;
     float4 *quatf = nullptr;
     int *shape = nullptr, *rep = nullptr, *nn = nullptr;
-    float4 *nlist = nullptr, *delta = nullptr;
+    float4 *nlist = nullptr, *delta = nullptr, *posf = nullptr;
     int *cell_count = nullptr, *cell_slots = nullptr;
     double *energy = nullptr, *virial = nullptr, *ke = nullptr, *ket = nullptr;
+    int n_chunks = 0;                 // replica-sum chunks (SUM_CHUNK particles)
+    int *chunk_rep = nullptr;
+    double *partial = nullptr;        // n_chunks * 3
     double *staging = nullptr;        // N * 4 doubles
     double *red = nullptr;            // R * 6 doubles
     double *scale3 = nullptr;         // R * 3
@@ -572,10 +576,27 @@ int setup_replicas(dem_ctx *ctx) {
             worst_cell = std::max(worst_cell, rho * cv);
         }
     }
+    // reduction chunks
+    std::vector<int> chunk_rep;
+    for (int r = 0; r < ctx->R; ++r) {
+        reps[r].chunk_off = (int)chunk_rep.size();
+        reps[r].n_chunk = std::max(1, (reps[r].n + SUM_CHUNK - 1) / SUM_CHUNK);
+        for (int c = 0; c < reps[r].n_chunk; ++c) chunk_rep.push_back(r);
+    }
+    if ((int)chunk_rep.size() != ctx->n_chunks || !ctx->chunk_rep) {
+        ctx->n_chunks = (int)chunk_rep.size();
+        if (ctx->chunk_rep) cudaFree(ctx->chunk_rep);
+        if (ctx->partial) cudaFree(ctx->partial);
+        CK(dalloc(&ctx->chunk_rep, (size_t)ctx->n_chunks));
+        CK(dalloc(&ctx->partial, 3 * (size_t)ctx->n_chunks));
+        free_graph(ctx);
+    }
+    CK(cudaMemcpy(ctx->chunk_rep, chunk_rep.data(), sizeof(int) * ctx->n_chunks, cudaMemcpyHostToDevice));
     ctx->reps = reps;
     int want_cap = (int)(2.0 * worst_ratio + 16);
     want_cap = (want_cap + 7) / 8 * 8;
     int want_cell = (int)(2.5 * worst_cell + 8);
+    want_cap = std::min(want_cap, MAX_NLIST_CAP);
     if ((want_cap > ctx->cap && !ctx->cap_fixed) || !ctx->nlist) {
         ctx->cap = std::max(ctx->cap, ctx->cap_fixed ? 1 : want_cap);
         if (ctx->nlist) cudaFree(ctx->nlist);
@@ -621,6 +642,7 @@ NlistArgs nlist_args(dem_ctx *ctx) {
     a.delta = ctx->delta;
     a.half_skin2 = (float)(0.25 * ctx->skin * ctx->skin);
     a.reps_rw = ctx->d_reps;
+    a.posf = ctx->posf;
     return a;
 }
 
@@ -638,6 +660,7 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     a.ke = ctx->ke; a.thermo = ctx->thermo; a.status = ctx->status;
     a.rotor32 = ctx->precision != DEM_FP64;
     a.ket = ctx->ket; a.virial = ctx->virial; a.reps_rw = ctx->d_reps;
+    a.n_chunks = ctx->n_chunks; a.chunk_rep = ctx->chunk_rep; a.partial = ctx->partial;
     return a;
 }
 
@@ -668,8 +691,10 @@ int launch_step(dem_ctx *ctx, double dt, int ens, double kT, double tau,
     ctx->launches += ens != DEM_NVE ? 4 : 2;
     CK(launch_second_half(sa, ctx->stream));
     if (ens != DEM_NVE) {
+        CK(launch_chunk_sums(sa, ctx->stream));
         CK(launch_thermo_end(sa, ctx->stream));
         CK(launch_scale(sa, ctx->stream));
+        ctx->launches += 1;
     }
     return DEM_OK;
 }
@@ -699,7 +724,11 @@ int force_rebuild(dem_ctx *ctx) {
 int grow(dem_ctx *ctx, const Status &st, int *grown) {
     *grown = 0;
     if (st.nlist_overflow > ctx->cap) {
-        ctx->cap = (st.nlist_overflow * 3 / 2 + 7) / 8 * 8;
+        if (st.nlist_overflow > MAX_NLIST_CAP)
+            return set_err(ctx, DEM_ERR_NLIST_OVERFLOW,
+                           "%d neighbours within the list cutoff (at most %d are supported)",
+                           st.nlist_overflow, MAX_NLIST_CAP);
+        ctx->cap = std::min(MAX_NLIST_CAP, (st.nlist_overflow * 3 / 2 + 7) / 8 * 8);
         cudaFree(ctx->nlist);
         CK(dalloc(&ctx->nlist, (size_t)ctx->cap * ctx->N));
         *grown = 1;
@@ -863,7 +892,8 @@ void dem_destroy(dem_ctx *ctx) {
                     ctx->cell_count, ctx->cell_slots, ctx->energy, ctx->virial, ctx->ke,
                     ctx->staging, ctx->red, ctx->scale3, ctx->status, ctx->thermo, ctx->d_reps,
                     ctx->d_shapes, ctx->d_geoms, ctx->d_table, ctx->d_itable, ctx->d_counters,
-                    ctx->snap, ctx->snap_thermo, ctx->snap_reps, ctx->ket};
+                    ctx->snap, ctx->snap_thermo, ctx->snap_reps, ctx->ket, ctx->chunk_rep,
+                    ctx->partial, ctx->posf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
@@ -943,6 +973,7 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
         CK(dalloc(&ctx->pos, n)); CK(dalloc(&ctx->vel, n)); CK(dalloc(&ctx->quat, n));
         CK(dalloc(&ctx->angmom, n)); CK(dalloc(&ctx->force, n)); CK(dalloc(&ctx->torque, n));
         CK(dalloc(&ctx->x_last, n)); CK(dalloc(&ctx->quatf, n)); CK(dalloc(&ctx->delta, n));
+        CK(dalloc(&ctx->posf, n));
         CK(cudaMemset(ctx->delta, 0, sizeof(float4) * n));
         CK(dalloc(&ctx->shape, n)); CK(dalloc(&ctx->rep, n)); CK(dalloc(&ctx->nn, n));
         CK(dalloc(&ctx->energy, n)); CK(dalloc(&ctx->virial, 6 * n)); CK(dalloc(&ctx->ke, n)); CK(dalloc(&ctx->ket, n));
@@ -1019,7 +1050,7 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
         ctx->prof_n = 0;
     } else if (n == "nlist_cap") {
         int c = (int)value;
-        if (c < 1) return set_err(ctx, DEM_ERR_ARG, "bad nlist_cap");
+        if (c < 1 || c > MAX_NLIST_CAP) return set_err(ctx, DEM_ERR_ARG, "bad nlist_cap");
         ctx->cap = c;
         ctx->cap_fixed = true;
         if (ctx->nlist) cudaFree(ctx->nlist);
@@ -1115,6 +1146,7 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
     if (rc) return rc;
     StepArgs sa = step_args(ctx, 0.0, DEM_NVE, 1.0, 1.0);
     CK(launch_kinetic(sa, ctx->stream));
+    CK(launch_chunk_sums(sa, ctx->stream));
     CK(launch_thermo_end(sa, ctx->stream));   // NVE branch: stores K per replica
     CK(cudaStreamSynchronize(ctx->stream));
     return DEM_OK;
@@ -1189,7 +1221,8 @@ int step_run(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau
         StepArgs sa = step_args(ctx, dt, ensemble, kT, tau_T);
         if (ensemble == DEM_NPT) {
             CK(launch_kinetic(sa, ctx->stream));
-            ctx->launches += 1;
+            CK(launch_chunk_sums(sa, ctx->stream));
+            ctx->launches += 2;
         }
         if (ensemble != DEM_NVE) {
             CK(launch_thermo_begin(sa, ctx->stream));

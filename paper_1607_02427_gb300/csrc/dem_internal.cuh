@@ -80,7 +80,13 @@ struct Rep {
     float sc;            // FP32 copy of sc_d for the FP32 pair kernels
     float disp_pad;      // 0.5 max(0, 1 - sc) r_list, added to displacements in the
                          // rebuild test so that a shrinking box cannot hide a pair
+    int chunk_off, n_chunk;   // this replica's reduction chunks (see SUM_CHUNK)
 };
+
+// Per-step replica sums run over fixed chunks of SUM_CHUNK particles (one
+// block each), then over each replica's chunk partials: a fixed order, and
+// a large replica is not summed by a single block.
+constexpr int SUM_CHUNK = 1024;
 
 // Device status word block.
 struct Status {
@@ -148,6 +154,7 @@ struct NlistArgs {
     Status *status;
     float half_skin2;        // rebuild threshold (skin/2)^2
     Rep *reps_rw;            // a rebuild records the box it was built in
+    float4 *posf;            // FP32 positions for the candidate test (w: shape index)
 };
 
 struct StepArgs {
@@ -170,6 +177,9 @@ struct StepArgs {
     double *ket;             // NPT: translational kinetic energy per particle
     const double *virial;    // per-particle virial (xx, xy, xz, yy, yz, zz)
     Rep *reps_rw;            // the replica records (NPT moves the box)
+    int n_chunks;            // reduction chunks over all replicas
+    const int *chunk_rep;    // replica of each chunk
+    double *partial;         // n_chunks * 3 chunk sums: K, K_trans (NPT), Tr W (NPT)
 };
 
 // ---- launch wrappers (pair.cu, nlist.cu, integrate.cu) ----
@@ -186,6 +196,7 @@ cudaError_t launch_second_half(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_thermo_begin(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_thermo_end(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_box(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_chunk_sums(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_scale(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_kinetic(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_replica_sums(int n_reps, const Rep *reps, const double *per_particle,

@@ -276,12 +276,33 @@ __device__ double block_sum(const double *x, int off, int n, int stride, int com
     return r;
 }
 
+// One block per reduction chunk: its sums of ke and, under NPT, of ket and
+// the virial trace.
+__global__ void k_chunk_sums(const StepArgs a) {
+    const int c = blockIdx.x;
+    const Rep &rp = a.reps[a.chunk_rep[c]];
+    const int k0 = (c - rp.chunk_off) * SUM_CHUNK;
+    const int off = rp.off + k0, len = min(SUM_CHUNK, rp.n - k0);
+    const double K = block_sum(a.ke, off, len, 1, 0);
+    double Kt = 0.0, vir = 0.0;
+    if (a.npt) {
+        Kt = block_sum(a.ket, off, len, 1, 0);
+        vir = block_sum(a.virial, off, len, 6, 0) + block_sum(a.virial, off, len, 6, 3) +
+              (a.dim == 3 ? block_sum(a.virial, off, len, 6, 5) : 0.0);
+    }
+    if (threadIdx.x == 0) {
+        a.partial[3 * c] = K;
+        a.partial[3 * c + 1] = Kt;
+        a.partial[3 * c + 2] = vir;
+    }
+}
+
 // One block per replica: K = sum of ke, then the second thermostat half step
 // of this step and the first half step of the next one.
 __global__ void k_thermo_end(const StepArgs a) {
     const int r = blockIdx.x;
     const Rep &rp = a.reps[r];
-    double K = block_sum(a.ke, rp.off, rp.n, 1, 0);
+    double K = block_sum(a.partial, rp.chunk_off, rp.n_chunk, 3, 0);
     if (threadIdx.x == 0) {
         Thermo &t = a.thermo[r];
         const double g = (double)rp.g_dof, d = 0.5 * a.dt;
@@ -374,10 +395,9 @@ __device__ void npt_first_half(const StepArgs &a, Thermo &t, const NptConst &c, 
 // the virial trace (fixed order).
 __device__ __forceinline__ void npt_sums(const StepArgs &a, const Rep &rp, double *K, double *Kt,
                                          double *vir) {
-    *K = block_sum(a.ke, rp.off, rp.n, 1, 0);
-    *Kt = block_sum(a.ket, rp.off, rp.n, 1, 0);
-    *vir = block_sum(a.virial, rp.off, rp.n, 6, 0) + block_sum(a.virial, rp.off, rp.n, 6, 3) +
-           (a.dim == 3 ? block_sum(a.virial, rp.off, rp.n, 6, 5) : 0.0);
+    *K = block_sum(a.partial, rp.chunk_off, rp.n_chunk, 3, 0);
+    *Kt = block_sum(a.partial, rp.chunk_off, rp.n_chunk, 3, 1);
+    *vir = block_sum(a.partial, rp.chunk_off, rp.n_chunk, 3, 2);
 }
 
 // One block per replica, end of an NPT step (after the second half kick):
@@ -607,6 +627,11 @@ cudaError_t launch_kinetic(const StepArgs &a, cudaStream_t s) {
 cudaError_t launch_thermo_end(const StepArgs &a, cudaStream_t s) {
     if (a.npt) k_thermo_end_npt<<<a.n_reps, 256, 0, s>>>(a);
     else k_thermo_end<<<a.n_reps, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_sums(const StepArgs &a, cudaStream_t s) {
+    k_chunk_sums<<<a.n_chunks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -44,7 +44,8 @@ constexpr size_t OFF_SHAPE = OFF_VIRIAL + align256(6 * sizeof(double) * MAX_N);
 constexpr size_t OFF_REP = OFF_SHAPE + align256(sizeof(int) * MAX_N);
 constexpr size_t OFF_NN = OFF_REP + align256(sizeof(int) * MAX_N);
 constexpr size_t OFF_DELTA = OFF_NN + align256(sizeof(int) * MAX_N);
-constexpr size_t OFF_NLIST = OFF_DELTA + align256(sizeof(float4) * MAX_N);
+constexpr size_t OFF_POSF = OFF_DELTA + align256(sizeof(float4) * MAX_N);
+constexpr size_t OFF_NLIST = OFF_POSF + align256(sizeof(float4) * MAX_N);
 constexpr size_t OFF_TABLE = OFF_NLIST + align256(sizeof(float4) * (size_t)MAX_N * CAP);
 constexpr size_t OFF_GEOMS = OFF_TABLE + align256(TABLE_BYTES);
 constexpr size_t OFF_ITAB = OFF_GEOMS + align256(sizeof(Geom) * MAX_GEOMS);
@@ -152,6 +153,7 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     int *nn = reinterpret_cast<int *>(b + OFF_NN);
     float4 *delta = reinterpret_cast<float4 *>(b + OFF_DELTA);
     float4 *nlist = reinterpret_cast<float4 *>(b + OFF_NLIST);
+    float4 *posf = reinterpret_cast<float4 *>(b + OFF_POSF);
     void *table = b + OFF_TABLE;
     Geom *geoms = reinterpret_cast<Geom *>(b + OFF_GEOMS);
     int *itab = reinterpret_cast<int *>(b + OFF_ITAB);
@@ -194,6 +196,8 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     na.cell_count = nullptr; na.cell_slots = nullptr;
     na.nlist = nlist; na.nn = nn; na.x_last = xlast; na.status = status; na.half_skin2 = 0.f;
     na.delta = delta;
+    na.posf = posf;
+    NA_CK(launch_cells(na, 0, st));
     NA_CK(launch_nlist(na, st));
     PairArgs pa = {};
     pa.n = n; pa.dim = dim; pa.cap = CAP;
