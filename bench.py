@@ -89,7 +89,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the e2e, FP64 and CPU-baseline measurements")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--decomp", default="auto", choices=["auto", "thread", "warp", "staged"])
+    p.add_argument("--decomp", default="auto", choices=["auto", "thread", "warp", "staged", "split"])
     return p.parse_args()
 
 
@@ -321,11 +321,11 @@ def main():
     if a.decomp == "auto":
         dem.dem_autotune(d.ctx)
     else:
-        d.set_param("decomp", {"thread": 1, "warp": 2, "staged": 3}[a.decomp])
-    decomp_name = {1: "thread", 2: "warp", 3: "staged"}[int(d.get_param("decomp"))]
+        d.set_param("decomp", {"thread": 1, "warp": 2, "staged": 3, "split": 4}[a.decomp])
+    decomp_name = {1: "thread", 2: "warp", 3: "staged", 4: "split"}[int(d.get_param("decomp"))]
     tune = {}
     if a.decomp == "auto":
-        for k, nm in enumerate(["thread64", "thread128", "warp128", "staged128"]):
+        for k, nm in enumerate(["thread64", "thread128", "warp128", "staged128", "split128"]):
             tune[nm] = d.get_param(f"autotune_ms_{k}")
 
     # warm-up
@@ -449,7 +449,7 @@ def measure_extras(a, dem, d, system, run, ens, prec, torch):
             d2.step(k, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
             torch.cuda.synchronize()
             out[name] = {"value": n * k / (time.perf_counter() - t0), "unit": UNIT, "steps": k,
-                         "decomposition": {1: "thread", 2: "warp", 3: "staged"}[
+                         "decomposition": {1: "thread", 2: "warp", 3: "staged", 4: "split"}[
                              int(d2.get_param("decomp"))]}
     # plain FP64 single-system path: one context per replica, launch by launch
     if system.n_replicas > 1:

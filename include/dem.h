@@ -89,6 +89,10 @@ extern "C" {
                                 and (pair, edge) items with the cheap tests,
                                 then the queued survivors (face nearest point,
                                 segment-segment, WCA terms) 32 at a time       */
+#define DEM_DECOMP_SPLIT 4   /* STAGED in two kernels: a list scan writes the
+                                active pairs of every 32 particles to device
+                                memory (N * nlist_cap records), a feature
+                                kernel runs the queues on them                 */
 
 typedef struct dem_ctx dem_ctx;   /* opaque; owned by the library */
 
@@ -255,7 +259,7 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value);
 /* Run every pair-kernel decomposition and block size on the current state
  * and keep the fastest (timed with CUDA events on the context's stream).
  * Candidates, in order: THREAD with 64 and 128 threads per block, WARP,
- * STAGED;
+ * STAGED, SPLIT (-1 when its records do not fit in device memory);
  * their mean times are readable as parameters "autotune_ms_0", ... .
  * Results are identical for every choice up to floating-point summation
  * order; the chosen one is the "decomp" and "block" parameters. */

@@ -411,6 +411,9 @@ struct dem_ctx {
     float4 *nlist = nullptr, *delta = nullptr, *posf = nullptr;
     int *cell_count = nullptr, *cell_slots = nullptr;
     double *energy = nullptr, *virial = nullptr, *ke = nullptr, *ket = nullptr;
+    void *recs = nullptr;             // SPLIT: active-pair records
+    int *rec_count = nullptr;
+    size_t rec_bytes = 0;
     int n_chunks = 0;                 // replica-sum chunks (SUM_CHUNK particles)
     int *chunk_rep = nullptr;
     double *partial = nullptr;        // n_chunks * 3
@@ -629,7 +632,31 @@ PairArgs pair_args(dem_ctx *ctx) {
     a.eps = ctx->eps; a.sigma = ctx->sigma; a.par_eps = ctx->par_eps;
     a.status = ctx->status;
     a.counters = ctx->d_counters;
+    a.recs = ctx->recs;
+    a.rec_count = ctx->rec_count;
     return a;
+}
+
+// SPLIT decomposition: record buffers for the current list capacity (never
+// allocated during a stream capture: every path that launches calls this
+// first).
+int ensure_recs(dem_ctx *ctx, int decomp) {
+    if (decomp != DEM_DECOMP_SPLIT) return DEM_OK;
+    const size_t groups = ((size_t)ctx->N + 31) / 32;
+    const size_t need = groups * 32 * (size_t)ctx->cap * pair_record_bytes(ctx->precision);
+    if (need > ctx->rec_bytes || !ctx->recs) {
+        if (ctx->recs) cudaFree(ctx->recs);
+        ctx->recs = nullptr;
+        ctx->rec_bytes = 0;
+        if (cudaMalloc(&ctx->recs, need) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, DEM_ERR_NOMEM, "SPLIT needs %zu bytes of pair records", need);
+        }
+        ctx->rec_bytes = need;
+        free_graph(ctx);
+    }
+    if (!ctx->rec_count) CK(dalloc(&ctx->rec_count, groups));
+    return DEM_OK;
 }
 
 NlistArgs nlist_args(dem_ctx *ctx) {
@@ -746,7 +773,9 @@ int grow(dem_ctx *ctx, const Status &st, int *grown) {
 // Evaluate forces at the current state; grow and redo on overflow.
 int compute_forces(dem_ctx *ctx) {
     for (int attempt = 0; attempt < 4; ++attempt) {
-        int rc = clear_flags(ctx);
+        int rc = ensure_recs(ctx, ctx->decomp);
+        if (rc) return rc;
+        rc = clear_flags(ctx);
         if (rc) return rc;
         rc = launch_forces(ctx, false);
         if (rc) return rc;
@@ -893,7 +922,7 @@ void dem_destroy(dem_ctx *ctx) {
                     ctx->staging, ctx->red, ctx->scale3, ctx->status, ctx->thermo, ctx->d_reps,
                     ctx->d_shapes, ctx->d_geoms, ctx->d_table, ctx->d_itable, ctx->d_counters,
                     ctx->snap, ctx->snap_thermo, ctx->snap_reps, ctx->ket, ctx->chunk_rep,
-                    ctx->partial, ctx->posf};
+                    ctx->partial, ctx->posf, ctx->recs, ctx->rec_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
@@ -1036,7 +1065,7 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
         ctx->par_eps = value;
     } else if (n == "decomp") {
         int d = (int)value;
-        if (d < DEM_DECOMP_AUTO || d > DEM_DECOMP_STAGED) return set_err(ctx, DEM_ERR_ARG, "bad decomp");
+        if (d < DEM_DECOMP_AUTO || d > DEM_DECOMP_SPLIT) return set_err(ctx, DEM_ERR_ARG, "bad decomp");
         ctx->decomp = d == DEM_DECOMP_AUTO ? DEM_DECOMP_THREAD : d;
     } else if (n == "block") {
         int b = (int)value;
@@ -1214,6 +1243,8 @@ namespace {
 int step_run(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T) {
     int rc;
     for (int attempt = 0; attempt < 4; ++attempt) {
+        rc = ensure_recs(ctx, ctx->decomp);
+        if (rc) return rc;
         rc = snapshot(ctx, false);
         if (rc) return rc;
         rc = clear_flags(ctx);
@@ -1477,7 +1508,8 @@ int dem_autotune(dem_ctx *ctx) {
     if (rc) return rc;
     struct Cand { int decomp, block; };
     const Cand cands[] = {{DEM_DECOMP_THREAD, 64}, {DEM_DECOMP_THREAD, 128},
-                          {DEM_DECOMP_WARP, 128}, {DEM_DECOMP_STAGED, 128}};
+                          {DEM_DECOMP_WARP, 128}, {DEM_DECOMP_STAGED, 128},
+                          {DEM_DECOMP_SPLIT, 128}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1485,6 +1517,10 @@ int dem_autotune(dem_ctx *ctx) {
     Cand pick = cands[0];
     ctx->tune_ms.clear();
     for (const Cand &c : cands) {
+        if (ensure_recs(ctx, c.decomp) != DEM_OK) {   // no room for SPLIT's records
+            ctx->tune_ms.push_back(-1.f);
+            continue;
+        }
         PairArgs pa = pair_args(ctx);
         CK(launch_pair(pa, ctx->precision, c.decomp, c.block, false, ctx->stream));   // warm-up
         CK(cudaEventRecord(e0, ctx->stream));

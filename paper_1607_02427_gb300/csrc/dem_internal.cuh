@@ -137,7 +137,14 @@ struct PairArgs {
     double eps, sigma, par_eps;
     Status *status;
     unsigned long long *counters;  // counting launches only
+    // SPLIT decomposition: active-pair records of each group of 32 particles
+    // (group g at recs + g * 32 * cap records) and their counts
+    void *recs;
+    int *rec_count;
 };
+
+// Bytes of one active-pair record of the SPLIT decomposition.
+size_t pair_record_bytes(int precision);
 
 struct NlistArgs {
     int n, dim, cap, cell_cap;
@@ -189,6 +196,10 @@ size_t pair_smem_bytes(const PairArgs &a, int precision);
 // STAGED decomposition (pair_staged.cu); smem_tables = pair_smem_bytes().
 cudaError_t launch_pair_staged(const PairArgs &a, int precision, bool count, size_t smem_tables,
                                cudaStream_t s);
+// SPLIT decomposition (pair_staged.cu): a scan kernel writes the active pairs,
+// a feature kernel evaluates them.
+cudaError_t launch_pair_split(const PairArgs &a, int precision, bool count, size_t smem_tables,
+                              cudaStream_t s);
 cudaError_t launch_cells(const NlistArgs &a, int n_cells, cudaStream_t s);
 cudaError_t launch_nlist(const NlistArgs &a, cudaStream_t s);
 cudaError_t launch_first_half(const StepArgs &a, cudaStream_t s);

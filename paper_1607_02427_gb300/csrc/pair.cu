@@ -360,6 +360,7 @@ cudaError_t launch_pair(const PairArgs &a, int precision, int decomp, int block,
                         cudaStream_t s) {
     size_t smem = pair_smem_bytes(a, precision);
     if (decomp == DEM_DECOMP_STAGED) return launch_pair_staged(a, precision, count, smem, s);
+    if (decomp == DEM_DECOMP_SPLIT) return launch_pair_split(a, precision, count, smem, s);
     if (block <= 0) block = THREADS;
     if (block > THREADS) block = THREADS;
     switch (precision) {

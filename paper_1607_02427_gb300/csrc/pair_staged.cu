@@ -49,7 +49,8 @@ template <class T> struct SPair {      // a queued active pair
                                        // dl = x_j - x_i in i's frame
     T rc, sig2;
     int gj, owner;                     // j's geometry; the owner's lane
-    unsigned vim, vjm, eim, ejm, fim, fjm, pad0, pad1;
+    unsigned vim, vjm, eim, ejm, fim, fjm;
+    int gi, pad;                       // i's geometry
 };
 template <class T> struct SInfo {      // one particle of the warp
     typename R4T<T>::type row[3];      // (R_i[r][0..2], x[r]); x: FP32 delta_i, FP64 position
@@ -71,17 +72,24 @@ template <class T> struct TermRec {    // a term with r < r_cut
     typename R4T<T>::type q;           // the point on i's feature (i's frame); w: r^2
     typename R4T<T>::type rv;          // i's point minus j's point (i's frame); w: pair
 };
-template <class T> struct StagedSmem {
-    SInfo<T> info[32];
+// Per-warp shared memory of the batch stages and of the list scan.
+template <class T> struct BatchSmem {
     SPair<T> pr[RING];
     union {
         VFItem<T> vf[RING];
         EEItem<T> ee[RING];
     } fq;
     TermRec<T> tq[RING];
-    int offs[32];                      // list offsets of the 32 particles
     int boffs[32];                     // item offsets of the batch's pairs
     unsigned gmask[32];                // per owner: lanes holding its terms
+};
+template <class T> struct ScanSmem {
+    SInfo<T> info[32];
+    int offs[32];                      // list offsets of the 32 particles
+};
+template <class T> struct StagedSmem {
+    BatchSmem<T> b;
+    ScanSmem<T> s;
 };
 
 // Position of the n-th (from 0) set bit of m (n < popc(m)).
@@ -139,7 +147,7 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
     const R4 *tab;
     const Geom *geo;
     const int *itab;
-    StagedSmem<T> &ws;
+    BatchSmem<T> &ws;
     const int lane;
     const T eps, par_eps;
     PathCount pc;
@@ -156,7 +164,7 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
     T crb = T(0), crc = T(0);          // j's edge radius; r_cut
 
     __device__ __forceinline__ Staged(const PairArgs &a_, const R4 *tab_, const Geom *geo_,
-                                      const int *itab_, StagedSmem<T> &ws_, int lane_)
+                                      const int *itab_, BatchSmem<T> &ws_, int lane_)
         : a(a_), tab(tab_), geo(geo_), itab(itab_), ws(ws_), lane(lane_), eps((T)a_.eps),
           par_eps((T)a_.par_eps) {
         if constexpr (COUNT)
@@ -164,9 +172,7 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
     }
 
     __device__ __forceinline__ SPair<T> &pair(int p) { return ws.pr[(ph + p) & (RING - 1)]; }
-    __device__ __forceinline__ const Geom &geom_i(const SPair<T> &P) {
-        return geo[ws.info[P.owner].geom];
-    }
+    __device__ __forceinline__ const Geom &geom_i(const SPair<T> &P) { return geo[P.gi]; }
     __device__ __forceinline__ static bool spheres(const Geom &gi, const Geom &gj) {
         return gi.nv == 1 && gj.nv == 1;
     }
@@ -537,54 +543,132 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
     }
 };
 
+// ---- the list scan (shared by STAGED and the SPLIT scan kernel) ----
+
+// Lane's particle i (or none) into the warp's scan table; returns its list
+// length.
+template <class T>
+__device__ __forceinline__ int scan_particle(const PairArgs &a, ScanSmem<T> &ss, int lane, int i) {
+    if (i >= a.n) return 0;
+    const ShapeDev &shi = a.shapes[a.shape[i]];
+    const M33<T> R = orientation<T>(a, i);
+    SInfo<T> &pi = ss.info[lane];
+    if constexpr (std::is_same<T, float>::value) {
+        const float4 dd = a.delta[i];
+        store_rows(pi.row, R, v3<float>(dd.x, dd.y, dd.z));
+        pi.rnd = shi.rounding_f;
+    } else {
+        const double4_32a xx = a.pos[i];
+        store_rows(pi.row, R, v3<double>(xx.x, xx.y, xx.z));
+        pi.rnd = shi.rounding;
+    }
+    pi.geom = shi.geom;
+    pi.rep = a.rep[i];
+    pi.sc = a.reps[pi.rep].sc;
+    return a.nn[i];
+}
+
+// List entry t of the warp's particles base..base+31: the range test and the
+// pair setup (separating-axis test, feature masks).  Returns whether the pair
+// is active; *pl is the owner's lane, *gi its geometry.
+template <class T, int DIM, bool COUNT>
+__device__ __forceinline__ bool scan_entry(const PairArgs &a, const typename R4T<T>::type *tab,
+                                           const int *itab, const Geom *geo, const ScanSmem<T> &ss,
+                                           int base, int t, T sig_all, PairWork<T> *wk, int *pl,
+                                           int *gi_out, PathCount *pc) {
+    *pl = owner_of(ss.offs, 32, t);
+    const int k = t - ss.offs[*pl];
+    const int i = base + *pl;
+    const SInfo<T> &pi = ss.info[*pl];
+    const Geom &gi = geo[pi.geom];
+    *gi_out = pi.geom;
+    M33<T> Ri;
+    V3<T> xi;
+    load_rows(pi.row, &Ri, &xi);
+    Owner<T> own;
+    own.rp = &a.reps[pi.rep];
+    own.sc = pi.sc;
+    own.R = (T)gi.R;
+    own.rnd = pi.rnd;
+    own.sig_all = sig_all;
+    own.geom = pi.geom;
+    if constexpr (std::is_same<T, float>::value)
+        own.delta = make_float4(xi.x, xi.y, xi.z, 0.f);
+    else
+        own.x = make_double4_32a(xi.x, xi.y, xi.z, 0.0);
+    const float4 e = a.nlist[(size_t)k * a.n + i];
+    bump<COUNT>(pc, C_NEIGH);
+    PairGeom<T> pg;
+    int j;
+    if (!in_range<T>(a, e, own, &j, &pg)) return false;
+    const Geom &gj = geo[pg.gj];
+    bump<COUNT>(pc, C_PAIRS);
+    bump<COUNT>(pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
+    wk->M = mul_tn(Ri, orientation_j<T>(a, j, pg));
+    wk->dl = mul_t(Ri, pg.d);
+    wk->rc = (T)WCA_CUT * pg.sig;
+    wk->sig2 = pg.sig * pg.sig;
+    wk->gj = pg.gj;
+    const bool active = pair_setup<T, COUNT>(tab, itab, gi, gj, wk, pc);
+    if (active) bump<COUNT>(pc, C_ACTIVE);
+    return active;
+}
+
+template <class T>
+__device__ __forceinline__ void store_record(SPair<T> &P, const PairWork<T> &wk, int owner, int gi) {
+    store_rows(P.row, wk.M, wk.dl);
+    P.rc = wk.rc;
+    P.sig2 = wk.sig2;
+    P.gj = wk.gj;
+    P.owner = owner;
+    P.vim = wk.vim; P.vjm = wk.vjm; P.eim = wk.eim; P.ejm = wk.ejm;
+    P.fim = wk.fim; P.fjm = wk.fjm;
+    P.gi = gi;
+    P.pad = 0;
+}
+
+// Shared-memory tables of a pair block: geometry records, geometries, int
+// table; returns the bytes they take (rounded to 128).
+template <class T>
+__device__ __forceinline__ size_t table_layout(const PairArgs &a, unsigned char *smem,
+                                               typename R4T<T>::type **tab, Geom **geo, int **itab) {
+    using R4 = typename R4T<T>::type;
+    *tab = reinterpret_cast<R4 *>(smem);
+    *geo = reinterpret_cast<Geom *>(*tab + a.table_len);
+    *itab = reinterpret_cast<int *>(*geo + a.n_geoms);
+    size_t tb = (size_t)a.table_len * sizeof(R4) + sizeof(Geom) * a.n_geoms +
+                sizeof(int) * a.itable_len;
+    return (tb + 127) & ~(size_t)127;
+}
+
+// ---- STAGED: scan and batches in one kernel ----
 template <class T, bool COMP, int DIM, bool COUNT>
 __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
     k_pair_staged(const PairArgs a) {
     using R4 = typename R4T<T>::type;
     extern __shared__ __align__(32) unsigned char smem[];
-    R4 *tab = reinterpret_cast<R4 *>(smem);
-    Geom *geo = reinterpret_cast<Geom *>(tab + a.table_len);
-    int *itab = reinterpret_cast<int *>(geo + a.n_geoms);
-    size_t tb = (size_t)a.table_len * sizeof(R4) + sizeof(Geom) * a.n_geoms +
-                sizeof(int) * a.itable_len;
-    tb = (tb + 127) & ~(size_t)127;
+    R4 *tab;
+    Geom *geo;
+    int *itab;
+    const size_t tb = table_layout<T>(a, smem, &tab, &geo, &itab);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     StagedSmem<T> &ws = reinterpret_cast<StagedSmem<T> *>(smem + tb)[w];
     stage_tables<T>(a, tab, geo, itab);
-    ws.gmask[lane] = 0u;
+    ws.b.gmask[lane] = 0u;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0 && !COUNT) {
         a.status->maxdisp2 = 0u;
         a.status->rebuild = 0;
     }
     const T sig_all = a.sigma > 0.0 ? (T)a.sigma : T(0);
-    Staged<T, COMP, DIM, COUNT> st(a, tab, geo, itab, ws, lane);
+    Staged<T, COMP, DIM, COUNT> st(a, tab, geo, itab, ws.b, lane);
     const int nwarps = gridDim.x * wpb;
     for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
         const int i_me = base + lane;
-        const bool mine = i_me < a.n;
-        int nn_me = 0;
-        if (mine) {
-            const ShapeDev &shi = a.shapes[a.shape[i_me]];
-            const M33<T> R = orientation<T>(a, i_me);
-            SInfo<T> &pi = ws.info[lane];
-            if constexpr (std::is_same<T, float>::value) {
-                const float4 dd = a.delta[i_me];
-                store_rows(pi.row, R, v3<float>(dd.x, dd.y, dd.z));
-                pi.rnd = shi.rounding_f;
-            } else {
-                const double4_32a xx = a.pos[i_me];
-                store_rows(pi.row, R, v3<double>(xx.x, xx.y, xx.z));
-                pi.rnd = shi.rounding;
-            }
-            pi.geom = shi.geom;
-            pi.rep = a.rep[i_me];
-            pi.sc = a.reps[pi.rep].sc;
-            nn_me = a.nn[i_me];
-        }
+        const int nn_me = scan_particle<T>(a, ws.s, lane, i_me);
         st.S.zero();
         int total;
-        ws.offs[lane] = warp_excl_scan(nn_me, lane, &total);
+        ws.s.offs[lane] = warp_excl_scan(nn_me, lane, &total);
         __syncwarp();
         // one batch call site: batches run when 32 pairs are queued and at
         // the end of the particles' lists
@@ -599,64 +683,131 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             t0 += 32;
             bool active = false;
             PairWork<T> wk;
-            int pl = 0;
-            if (t < total) {
-                pl = owner_of(ws.offs, 32, t);
-                const int k = t - ws.offs[pl];
-                const int i = base + pl;
-                const SInfo<T> &pi = ws.info[pl];
-                const Geom &gi = geo[pi.geom];
-                M33<T> Ri;
-                V3<T> xi;
-                load_rows(pi.row, &Ri, &xi);
-                Owner<T> own;
-                own.rp = &a.reps[pi.rep];
-                own.sc = pi.sc;
-                own.R = (T)gi.R;
-                own.rnd = pi.rnd;
-                own.sig_all = sig_all;
-                own.geom = pi.geom;
-                if constexpr (std::is_same<T, float>::value)
-                    own.delta = make_float4(xi.x, xi.y, xi.z, 0.f);
-                else
-                    own.x = make_double4_32a(xi.x, xi.y, xi.z, 0.0);
-                const float4 e = a.nlist[(size_t)k * a.n + i];
-                bump<COUNT>(&st.pc, C_NEIGH);
-                PairGeom<T> pg;
-                int j;
-                if (in_range<T>(a, e, own, &j, &pg)) {
-                    const Geom &gj = geo[pg.gj];
-                    bump<COUNT>(&st.pc, C_PAIRS);
-                    bump<COUNT>(&st.pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
-                    wk.M = mul_tn(Ri, orientation_j<T>(a, j, pg));
-                    wk.dl = mul_t(Ri, pg.d);
-                    wk.rc = (T)WCA_CUT * pg.sig;
-                    wk.sig2 = pg.sig * pg.sig;
-                    wk.gj = pg.gj;
-                    active = pair_setup<T, COUNT>(tab, itab, gi, gj, &wk, &st.pc);
-                    if (active) bump<COUNT>(&st.pc, C_ACTIVE);
-                }
-            }
+            int pl = 0, gi = 0;
+            if (t < total)
+                active = scan_entry<T, DIM, COUNT>(a, tab, itab, geo, ws.s, base, t, sig_all, &wk,
+                                                   &pl, &gi, &st.pc);
             const unsigned m = __ballot_sync(FULL, active);
-            if (active) {
-                SPair<T> &P = ws.pr[ring_slot(m, lane, st.ph + st.np)];
-                store_rows(P.row, wk.M, wk.dl);
-                P.rc = wk.rc;
-                P.sig2 = wk.sig2;
-                P.gj = wk.gj;
-                P.owner = pl;
-                P.vim = wk.vim; P.vjm = wk.vjm; P.eim = wk.eim; P.ejm = wk.ejm;
-                P.fim = wk.fim; P.fjm = wk.fjm;
-            }
+            if (active) store_record(ws.b.pr[ring_slot(m, lane, st.ph + st.np)], wk, pl, gi);
             st.np += __popc(m);
             __syncwarp();
         }
-        if (mine) {
+        if (i_me < a.n) {
             M33<T> R;
             V3<T> x;
-            load_rows(ws.info[lane].row, &R, &x);
+            load_rows(ws.s.info[lane].row, &R, &x);
             finish_particle(a, i_me, st.S, R);
         }
+        __syncwarp();
+    }
+    if constexpr (COUNT)
+        for (int k = 0; k < NCOUNT; ++k)
+            if (st.pc.v[k]) atomicAdd(a.counters + k, (unsigned long long)st.pc.v[k]);
+}
+
+// ---- SPLIT: a scan kernel writes the active pairs of each group of 32
+// particles to HBM (group g at recs + g 32 cap, in the order STAGED queues
+// them), a feature kernel evaluates them.  The scan is bound by the latency
+// of the neighbour gathers and runs with a small footprint at a higher
+// occupancy; the feature kernel keeps the batch stages. ----
+template <class T> struct ScanBlockSmem {
+    ScanSmem<T> s;
+    SPair<T> stage[32];                // this chunk's active pairs, in ballot order
+};
+
+template <class T, int DIM, bool COUNT>
+__global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
+    using R4 = typename R4T<T>::type;
+    extern __shared__ __align__(32) unsigned char smem[];
+    R4 *tab;
+    Geom *geo;
+    int *itab;
+    const size_t tb = table_layout<T>(a, smem, &tab, &geo, &itab);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    ScanBlockSmem<T> &ws = reinterpret_cast<ScanBlockSmem<T> *>(smem + tb)[w];
+    stage_tables<T>(a, tab, geo, itab);
+    __syncthreads();
+    const T sig_all = a.sigma > 0.0 ? (T)a.sigma : T(0);
+    PathCount pc;
+    if constexpr (COUNT)
+        for (int k = 0; k < NCOUNT; ++k) pc.v[k] = 0;
+    constexpr int QW = sizeof(SPair<T>) / sizeof(uint4);
+    const int nwarps = gridDim.x * wpb;
+    for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
+        const int g = base / 32;
+        const int nn_me = scan_particle<T>(a, ws.s, lane, base + lane);
+        int total;
+        ws.s.offs[lane] = warp_excl_scan(nn_me, lane, &total);
+        __syncwarp();
+        uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<SPair<T> *>(a.recs) +
+                                               (size_t)g * 32 * a.cap);
+        int cnt = 0;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            bool active = false;
+            PairWork<T> wk;
+            int pl = 0, gi = 0;
+            if (t < total)
+                active = scan_entry<T, DIM, COUNT>(a, tab, itab, geo, ws.s, base, t, sig_all, &wk,
+                                                   &pl, &gi, &pc);
+            const unsigned m = __ballot_sync(FULL, active);
+            if (active) store_record(ws.stage[__popc(m & ((1u << lane) - 1u))], wk, pl, gi);
+            __syncwarp();
+            // the chunk's records out, one 16-byte word per lane per round
+            const uint4 *src = reinterpret_cast<const uint4 *>(ws.stage);
+            const int words = __popc(m) * QW;
+            for (int q = lane; q < words; q += 32) out[(size_t)cnt * QW + q] = src[q];
+            cnt += __popc(m);
+            __syncwarp();
+        }
+        if (lane == 0) a.rec_count[g] = cnt;
+    }
+    if constexpr (COUNT)
+        for (int k = 0; k < NCOUNT; ++k)
+            if (pc.v[k]) atomicAdd(a.counters + k, (unsigned long long)pc.v[k]);
+}
+
+template <class T, bool COMP, int DIM, bool COUNT>
+__global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
+    k_pair_apply(const PairArgs a) {
+    using R4 = typename R4T<T>::type;
+    extern __shared__ __align__(32) unsigned char smem[];
+    R4 *tab;
+    Geom *geo;
+    int *itab;
+    const size_t tb = table_layout<T>(a, smem, &tab, &geo, &itab);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    BatchSmem<T> &ws = reinterpret_cast<BatchSmem<T> *>(smem + tb)[w];
+    stage_tables<T>(a, tab, geo, itab);
+    ws.gmask[lane] = 0u;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !COUNT) {
+        a.status->maxdisp2 = 0u;
+        a.status->rebuild = 0;
+    }
+    Staged<T, COMP, DIM, COUNT> st(a, tab, geo, itab, ws, lane);
+    constexpr int QW = sizeof(SPair<T>) / sizeof(uint4);
+    const int nwarps = gridDim.x * wpb;
+    for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
+        const int g = base / 32;
+        const int cnt = a.rec_count[g];
+        const uint4 *in = reinterpret_cast<const uint4 *>(reinterpret_cast<const SPair<T> *>(a.recs) +
+                                                          (size_t)g * 32 * a.cap);
+        st.S.zero();
+        for (int b0 = 0; b0 < cnt; b0 += 32) {
+            const int nb = cnt - b0 < 32 ? cnt - b0 : 32;
+            // records b0.. into the ring from slot ph (the ring is empty here)
+            uint4 *dst = reinterpret_cast<uint4 *>(ws.pr);
+            for (int q = lane; q < nb * QW; q += 32) {
+                const int r = q / QW, c = q - r * QW;
+                dst[(size_t)((st.ph + r) & (RING - 1)) * QW + c] = in[(size_t)(b0 + r) * QW + c];
+            }
+            __syncwarp();
+            st.np = nb;
+            st.batch(nb);
+        }
+        const int i_me = base + lane;
+        if (i_me < a.n) finish_particle(a, i_me, st.S, orientation<T>(a, i_me));
         __syncwarp();
     }
     if constexpr (COUNT)
@@ -687,6 +838,36 @@ cudaError_t launch_prec(const PairArgs &a, bool count, size_t smem_tables, cudaS
     return launch_dim<T, COMP, 3>(a, count, smem_tables, s);
 }
 
+template <class T, bool COMP, int DIM>
+cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
+    const size_t t = (smem_tables + 127) & ~(size_t)127;
+    const size_t smem1 = t + (SBLOCK / 32) * sizeof(ScanBlockSmem<T>);
+    const size_t smem2 = t + (SBLOCK / 32) * sizeof(BatchSmem<T>);
+    const long long need = (a.n + SBLOCK - 1) / SBLOCK;   // 32 particles per warp
+    auto launch = [&](auto kernel, size_t smem) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const long long cap = (long long)blocks_per_sm(kernel, SBLOCK, smem) * sm_count();
+        int grid = (int)(need < cap ? need : cap);
+        if (grid < 1) grid = 1;
+        kernel<<<grid, SBLOCK, smem, s>>>(a);
+    };
+    if (count) {
+        launch(k_pair_scan<T, DIM, true>, smem1);
+        launch(k_pair_apply<T, COMP, DIM, true>, smem2);
+    } else {
+        launch(k_pair_scan<T, DIM, false>, smem1);
+        launch(k_pair_apply<T, COMP, DIM, false>, smem2);
+    }
+    return cudaGetLastError();
+}
+
+template <class T, bool COMP>
+cudaError_t launch_split_prec(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
+    if (a.dim == 2) return launch_split_dim<T, COMP, 2>(a, count, smem_tables, s);
+    return launch_split_dim<T, COMP, 3>(a, count, smem_tables, s);
+}
+
 }  // namespace
 
 cudaError_t launch_pair_staged(const PairArgs &a, int precision, bool count, size_t smem_tables,
@@ -695,6 +876,19 @@ cudaError_t launch_pair_staged(const PairArgs &a, int precision, bool count, siz
         case DEM_FP64: return launch_prec<double, false>(a, count, smem_tables, s);
         case DEM_FP32: return launch_prec<float, false>(a, count, smem_tables, s);
         default: return launch_prec<float, true>(a, count, smem_tables, s);
+    }
+}
+
+size_t pair_record_bytes(int precision) {
+    return precision == DEM_FP64 ? sizeof(SPair<double>) : sizeof(SPair<float>);
+}
+
+cudaError_t launch_pair_split(const PairArgs &a, int precision, bool count, size_t smem_tables,
+                              cudaStream_t s) {
+    switch (precision) {
+        case DEM_FP64: return launch_split_prec<double, false>(a, count, smem_tables, s);
+        case DEM_FP32: return launch_split_prec<float, false>(a, count, smem_tables, s);
+        default: return launch_split_prec<float, true>(a, count, smem_tables, s);
     }
 }
 

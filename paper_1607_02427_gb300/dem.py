@@ -29,7 +29,7 @@ DEM_ERR_NOMEM = -8
 
 DEM_FP64, DEM_FP32, DEM_FP32_COMP = 0, 1, 2
 DEM_NVE, DEM_NVT, DEM_NPT = 0, 1, 2
-DEM_DECOMP_AUTO, DEM_DECOMP_THREAD, DEM_DECOMP_WARP, DEM_DECOMP_STAGED = 0, 1, 2, 3
+DEM_DECOMP_AUTO, DEM_DECOMP_THREAD, DEM_DECOMP_WARP, DEM_DECOMP_STAGED, DEM_DECOMP_SPLIT = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": DEM_FP64, "fp32": DEM_FP32, "fp32c": DEM_FP32_COMP}
 
 # Every symbol include/dem.h declares (checked by the CPU tests).

@@ -64,7 +64,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("decomp", [1, 3], ids=["thread", "staged"])
+@pytest.mark.parametrize("decomp", [1, 3, 4], ids=["thread", "staged", "split"])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-9), (2, 1e-4), (1, 1e-4)],
                          ids=["fp64", "fp32c", "fp32"])
 @pytest.mark.parametrize("name", list(CASES))

@@ -67,7 +67,7 @@ def system(name):
     return _cache[name]
 
 
-DECOMPS = {"thread": 1, "warp": 2, "staged": 3}
+DECOMPS = {"thread": 1, "warp": 2, "staged": 3, "split": 4}
 
 
 @pytest.mark.parametrize("decomp", list(DECOMPS))
@@ -101,8 +101,8 @@ def test_autotune_keeps_results(dem):
     with dem.DEM(s, dem.DEM_FP32_COMP) as d:
         f0, _ = d.forces()
         dem.dem_autotune(d.ctx)
-        assert d.get_param("decomp") in (1.0, 2.0, 3.0)
-        assert d.get_param("autotune_ms_3") > 0
+        assert d.get_param("decomp") in (1.0, 2.0, 3.0, 4.0)
+        assert d.get_param("autotune_ms_4") > 0
         f1, _ = d.forces()
         d.step(5, 1e-3, dem.DEM_NVE)
     scale = np.abs(f0).max()
