@@ -73,8 +73,8 @@ template <class T> struct TermRec {    // a term with r < r_cut
     typename R4T<T>::type rv;          // i's point minus j's point (i's frame); w: pair
 };
 // Per-warp shared memory of the batch stages and of the list scan.
-template <class T> struct BatchSmem {
-    SPair<T> pr[RING];
+template <class T, int PR> struct BatchSmem {   // PR: pair ring entries (a power of 2)
+    SPair<T> pr[PR];
     union {
         VFItem<T> vf[RING];
         EEItem<T> ee[RING];
@@ -88,7 +88,7 @@ template <class T> struct ScanSmem {
     int offs[32];                      // list offsets of the 32 particles
 };
 template <class T> struct StagedSmem {
-    BatchSmem<T> b;
+    BatchSmem<T, RING> b;
     ScanSmem<T> s;
 };
 
@@ -141,13 +141,13 @@ template <class T> __device__ __forceinline__ V3<T> pair_dl(const SPair<T> &P) {
 // must share the instruction cache).  batch() is a loop whose body does one
 // action per turn: consumers first, so that no ring reaches 64 entries,
 // then one step of the current producer.
-template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
+template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged {
     using R4 = typename R4T<T>::type;
     const PairArgs &a;
     const R4 *tab;
     const Geom *geo;
     const int *itab;
-    BatchSmem<T> &ws;
+    BatchSmem<T, PR> &ws;
     const int lane;
     const T eps, par_eps;
     PathCount pc;
@@ -164,14 +164,14 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
     T crb = T(0), crc = T(0);          // j's edge radius; r_cut
 
     __device__ __forceinline__ Staged(const PairArgs &a_, const R4 *tab_, const Geom *geo_,
-                                      const int *itab_, BatchSmem<T> &ws_, int lane_)
+                                      const int *itab_, BatchSmem<T, PR> &ws_, int lane_)
         : a(a_), tab(tab_), geo(geo_), itab(itab_), ws(ws_), lane(lane_), eps((T)a_.eps),
           par_eps((T)a_.par_eps) {
         if constexpr (COUNT)
             for (int k = 0; k < NCOUNT; ++k) pc.v[k] = 0;
     }
 
-    __device__ __forceinline__ SPair<T> &pair(int p) { return ws.pr[(ph + p) & (RING - 1)]; }
+    __device__ __forceinline__ SPair<T> &pair(int p) { return ws.pr[(ph + p) & (PR - 1)]; }
     __device__ __forceinline__ const Geom &geom_i(const SPair<T> &P) { return geo[P.gi]; }
     __device__ __forceinline__ static bool spheres(const Geom &gi, const Geom &gj) {
         return gi.nv == 1 && gj.nv == 1;
@@ -538,7 +538,7 @@ template <class T, bool COMP, int DIM, bool COUNT> struct Staged {
             if (DIM == 3 && phase == 2) edge_step();
             else vertex_step();
         }
-        ph = (ph + nb) & (RING - 1);
+        ph = (ph + nb) & (PR - 1);
         np -= nb;
     }
 };
@@ -767,8 +767,10 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
             if (pc.v[k]) atomicAdd(a.counters + k, (unsigned long long)pc.v[k]);
 }
 
+constexpr int APPLY_PR = 32;   // the feature kernel holds one batch of records at a time
+
 template <class T, bool COMP, int DIM, bool COUNT>
-__global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
+__global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
     k_pair_apply(const PairArgs a) {
     using R4 = typename R4T<T>::type;
     extern __shared__ __align__(32) unsigned char smem[];
@@ -777,7 +779,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
     int *itab;
     const size_t tb = table_layout<T>(a, smem, &tab, &geo, &itab);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    BatchSmem<T> &ws = reinterpret_cast<BatchSmem<T> *>(smem + tb)[w];
+    BatchSmem<T, APPLY_PR> &ws = reinterpret_cast<BatchSmem<T, APPLY_PR> *>(smem + tb)[w];
     stage_tables<T>(a, tab, geo, itab);
     ws.gmask[lane] = 0u;
     __syncthreads();
@@ -785,7 +787,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
         a.status->maxdisp2 = 0u;
         a.status->rebuild = 0;
     }
-    Staged<T, COMP, DIM, COUNT> st(a, tab, geo, itab, ws, lane);
+    Staged<T, COMP, DIM, COUNT, APPLY_PR> st(a, tab, geo, itab, ws, lane);
     constexpr int QW = sizeof(SPair<T>) / sizeof(uint4);
     const int nwarps = gridDim.x * wpb;
     for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             uint4 *dst = reinterpret_cast<uint4 *>(ws.pr);
             for (int q = lane; q < nb * QW; q += 32) {
                 const int r = q / QW, c = q - r * QW;
-                dst[(size_t)((st.ph + r) & (RING - 1)) * QW + c] = in[(size_t)(b0 + r) * QW + c];
+                dst[(size_t)((st.ph + r) & (APPLY_PR - 1)) * QW + c] = in[(size_t)(b0 + r) * QW + c];
             }
             __syncwarp();
             st.np = nb;
@@ -842,7 +844,7 @@ template <class T, bool COMP, int DIM>
 cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
     const size_t t = (smem_tables + 127) & ~(size_t)127;
     const size_t smem1 = t + (SBLOCK / 32) * sizeof(ScanBlockSmem<T>);
-    const size_t smem2 = t + (SBLOCK / 32) * sizeof(BatchSmem<T>);
+    const size_t smem2 = t + (SBLOCK / 32) * sizeof(BatchSmem<T, APPLY_PR>);
     const long long need = (a.n + SBLOCK - 1) / SBLOCK;   // 32 particles per warp
     auto launch = [&](auto kernel, size_t smem) {
         if (smem > 48 * 1024)
