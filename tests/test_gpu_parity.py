@@ -38,6 +38,9 @@ def _systems():
         [W.polygon(5, 0.7, 0.1), W.rod2d(1.0, 0.12), W.square(1.0, 0.15), W.disk(0.2, 0.02)],
         np.arange(200) % 4, [30.0, 30.0], 2)
     out["disks"] = lambda: _periodic_cluster([W.disk(0.25)], np.zeros(400, int), [25.0, 25.0], 3)
+    # 32 vertices and 32 edges: every bit of the feature masks in use
+    out["poly32"] = lambda: _periodic_cluster([W.polygon(32, 0.8, 0.1)], np.zeros(200, int),
+                                              [40.0, 40.0], 11)
     out["cubes"] = lambda: _periodic_cluster([W.cube(1.0, 0.15)], np.zeros(333, int),
                                              [14.0, 14.0, 14.0], 4, sigma=0.3)
     out["tets"] = lambda: _periodic_cluster([W.tetrahedron(1.0, 0.15)], np.zeros(300, int),

@@ -85,3 +85,20 @@ def test_shape_validation(dem, bad):
         sh["rounding"] = 0.0
     with pytest.raises(dem.DemError):
         dem.dem_shape_info(sh)
+
+
+@pytest.mark.parametrize("sizes", [[3, 0, 2], [0], []])
+def test_create_rejects_empty_replicas(dem, sizes):
+    """Empty inputs are refused during validation, before any device work."""
+    box = np.full((max(len(sizes), 1), 3), 10.0)
+    with pytest.raises(dem.DemError) as e:
+        dem.dem_create([W.cube(1.0, 0.15)], 1.0, 0.0, box, np.asarray(sizes, np.int32),
+                       dem.DEM_FP32_COMP)
+    assert e.value.code == dem.DEM_ERR_ARG
+
+
+def test_create_rejects_bad_box(dem):
+    with pytest.raises(dem.DemError) as e:
+        dem.dem_create([W.cube(1.0, 0.15)], 1.0, 0.0, np.array([[10.0, -1.0, 10.0]]),
+                       np.array([4], np.int32), dem.DEM_FP32_COMP)
+    assert e.value.code == dem.DEM_ERR_ARG
