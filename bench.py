@@ -20,6 +20,7 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -267,21 +268,27 @@ def oracle_sample(system, target_particles=3000, max_step_s=None, run=None):
 
 
 def time_oracle(system, run, seconds, steps=None):
+    """The FP64 oracle on a bounded sample of the workload: chunks of steps
+    until ``seconds`` have passed (or exactly ``steps``), one thread."""
     import oracle
     oracle.build()
     sample, nrep = oracle_sample(system)
     ens = run["ensemble"]
+    th = None
+    done, chunk = 0, 5
     t0 = time.perf_counter()
-    oracle.run(sample, 1, run["dt"], ensemble=ens, kT=run["kT"], tau=run["tau"])
-    one = time.perf_counter() - t0
-    if steps is None:
-        steps = max(1, int(seconds / max(one, 1e-6)))
-    t0 = time.perf_counter()
-    oracle.run(sample, steps, run["dt"], ensemble=ens, kT=run["kT"], tau=run["tau"])
+    while (steps is None and time.perf_counter() - t0 < seconds) or (steps is not None and done < steps):
+        k = chunk if steps is None else min(chunk, steps - done)
+        st, _ = oracle.run(sample, k, run["dt"], ensemble=ens, kT=run["kT"], tau=run["tau"],
+                           thermo=th)
+        sample = dataclasses.replace(sample, pos=st["pos"], orient=st["orient"], vel=st["vel"],
+                                     angmom=st["angmom"])
+        th = st["thermo"]
+        done += k
     dt = time.perf_counter() - t0
-    return {"value": sample.n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": sample.n * done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{nrep} replicas ({sample.n} particles, first replicas of the workload, "
-                      f"generator-made start at target density), {steps} FP64 steps, "
+                      f"generator-made start at target density), {done} FP64 steps, "
                       f"single thread, {dt:.1f} s"}
 
 
@@ -333,6 +340,7 @@ def main():
     d.set_param("profile", 1)
     d.step(1, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])   # capture the profiled graph
     d.set_param("profile", 1)                                      # reset the totals
+    rb0 = int(d.counters()[13])
     l0 = d.get_param("launches")
 
     # timed region
@@ -351,6 +359,7 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     launches = int(d.get_param("launches") - l0)
+    rebuilds = int(d.counters()[13]) - rb0
     pair_ms = d.get_param("pair_ms_total") / max(1.0, d.get_param("pair_launches"))
     d.set_param("profile", 0)
     t_max, n_total = reduce_over_ranks(dist, ms, system.n, "cuda")
@@ -398,6 +407,7 @@ def main():
             "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max clock",
         },
         "gpu_launches": launches,
+        "list_rebuilds": rebuilds,
         "clocks": clocks,
     }
     if "e2e" in extras:
@@ -480,6 +490,36 @@ def _with_state(system, st):
                                target_box=None)
 
 
+def reference_sample(system, run, budget):
+    """The workload's first replica at its target density, halved (same shapes,
+    same density) until one oracle step of it, measured after the lattice
+    start has relaxed for a few steps, fits ``budget`` seconds."""
+    import oracle
+    from paper_1607_02427_gb300 import workloads as W
+
+    def relaxed_cost(smp):
+        st, _ = oracle.run(smp, 2, run["dt"], ensemble=run["ensemble"], kT=run["kT"],
+                           tau=run["tau"])
+        smp = dataclasses.replace(smp, pos=st["pos"], orient=st["orient"], vel=st["vel"],
+                                  angmom=st["angmom"])
+        t0 = time.perf_counter()
+        oracle.run(smp, 3, run["dt"], ensemble=run["ensemble"], kT=run["kT"], tau=run["tau"])
+        return smp, (time.perf_counter() - t0) / 3
+
+    rep = system.replica(0)
+    n = min(rep.n, 4096)
+    smp = rep if rep.n == n else W.sample_like(system, n)
+    smp = W.slab_lattice_start(smp) if smp.dim == 3 else smp
+    smp, cost = relaxed_cost(smp)
+    what = "the first replica" if smp.n == rep.n else f"a sample like the first replica"
+    while cost > budget and smp.n > 16:
+        smp = W.sample_like(system, max(8, smp.n // 2))
+        smp = W.slab_lattice_start(smp) if smp.dim == 3 else smp
+        smp, cost = relaxed_cost(smp)
+        what = "a sample like the first replica"
+    return smp, what, cost
+
+
 def reference_arm(a, world, rank):
     """The FP64 CPU oracle on a bounded sample of the workload, per step."""
     if rank != 0:
@@ -489,16 +529,21 @@ def reference_arm(a, world, rank):
     system, run = make_workload(a.workload, 0, a.replicas, getattr(a, "n", 0))
     # each step a bounded sample: the whole run within about two minutes
     budget = 120.0 / max(1, a.steps + a.warmup)
-    sample, nrep = oracle_sample(system, max_step_s=budget, run=run)
+    sample, nrep, per_step = reference_sample(system, run, budget)
+    th = None
     for _ in range(a.warmup):
-        oracle.run(sample, 1, run["dt"], ensemble=run["ensemble"], kT=run["kT"], tau=run["tau"])
+        st, _ = oracle.run(sample, 1, run["dt"], ensemble=run["ensemble"], kT=run["kT"],
+                           tau=run["tau"], thermo=th)
+        sample = dataclasses.replace(sample, pos=st["pos"], orient=st["orient"], vel=st["vel"],
+                                     angmom=st["angmom"])
+        th = st["thermo"]
     t0 = time.perf_counter()
     steps = a.steps
-    state = sample
-    oracle.run(state, steps, run["dt"], ensemble=run["ensemble"], kT=run["kT"], tau=run["tau"])
+    oracle.run(sample, steps, run["dt"], ensemble=run["ensemble"], kT=run["kT"], tau=run["tau"],
+               thermo=th)
     dt = time.perf_counter() - t0
     value = sample.n * steps / dt
-    desc = (f"{nrep} replicas ({sample.n} particles) of {system.name}, FP64 oracle, "
+    desc = (f"{nrep} ({sample.n} particles) of {system.name}, FP64 oracle, "
             f"single thread, {steps} steps")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": steps, "warmup": a.warmup,

@@ -190,7 +190,11 @@ __global__ void k_first_half(const StepArgs a) {
             free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
             free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
         }
-        const double inq = rsqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        // renormalise: |q|^2 = 1 + e with |e| ~ 1e-10 per step, and
+        // 1/sqrt(1 + e) = 1 - e/2 + 3e^2/8 - ... (remainder below 5|e|^3/16,
+        // < 3e-18 for |e| < 2e-6; otherwise the general rsqrt)
+        const double qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w, e2 = qq - 1.0;
+        const double inq = fabs(e2) < 2e-6 ? fma(fma(0.375, e2, -0.5), e2, 1.0) : rsqrt(qq);
         q.x *= inq; q.y *= inq; q.z *= inq; q.w *= inq;
         a.pos[i] = x;
         a.vel[i] = v;
