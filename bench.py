@@ -80,6 +80,16 @@ def parse():
     p.add_argument("--workload", default="batched",
                    choices=["batched", "cubes", "large", "squares", "octahedra", "spheres",
                             "cubes_fluid", "icosahedra"])
+    p.add_argument("--energy-drift", action="store_true",
+                   help="instead of the throughput line: NVE energy drift and short-term "
+                        "fluctuation of the Section 'Energy Conservation' fluids per precision")
+    p.add_argument("--drift-steps", type=int, default=100000)
+    p.add_argument("--drift-set", default="all", choices=["all", "fluids", "configs"],
+                   help="--energy-drift: the Section 'Energy Conservation' fluids, the "
+                        "bench workloads in their own ensembles, or both")
+    p.add_argument("--drift-budget", type=float, default=100.0,
+                   help="--energy-drift on the bench workloads: seconds per workload and "
+                        "precision; a run stops early at this budget and says so")
     p.add_argument("--n", type=int, default=0,
                    help="particles of the spheres / cubes_fluid / icosahedra workloads "
                         "(the paper's table uses 256, 4096 and 65536; default 65536)")
@@ -304,6 +314,8 @@ def main():
 
     if a.impl == "reference":
         return reference_arm(a, world, rank)
+    if a.energy_drift:
+        return energy_drift(a, rank)
 
     import torch
     dist = None
@@ -488,6 +500,132 @@ def _with_state(system, st):
                                angmom=st["angmom"], box=system.target_box
                                if system.target_box is not None else system.box,
                                target_box=None)
+
+
+def energy_drift(a, rank):
+    """Section "Energy Conservation": fluids of squares (edge 4.24 sigma, 2D)
+    and tetrahedra (edge 8.49 sigma, 3D) thermalised at T* = 1 (NVT, dt =
+    0.005 tau), then from that one state, in each precision:
+
+    * short term: sigma(E/N), the standard deviation of the total energy per
+      particle sampled every step over 10 tau of NVE, for each dt of the
+      sweep (the paper's fluctuation-versus-timestep figure);
+    * long term: the drift of E/N over --drift-steps NVE steps at the
+      fluid's production dt (least-squares slope, epsilon per tau).
+
+    Squares run at the paper's dt = 0.01 tau.  Tetrahedra of unit mass and
+    uniform-solid inertia are unstable at dt >= 0.008 tau (a tip contact has
+    an effective mass of about 0.12 m; the oracle shows the same growth), so
+    they run at 0.005 tau.  One JSON line; the paper's FP32 drifts beside."""
+    if rank != 0:
+        return
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1607_02427_gb300 import dem
+    from paper_1607_02427_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    fluids = {"squares": dict(system=W.config_energy_drift("square", 16, 0.5), dt=0.01,
+                              sweep=[0.001, 0.002, 0.005, 0.01], paper_fp32=1.4e-5),
+              "tetrahedra": dict(system=W.config_energy_drift("tetrahedron", 8, 0.4), dt=0.005,
+                                 sweep=[0.001, 0.002, 0.005], paper_fp32=6.3e-4)}
+    precs = (("fp32", dem.DEM_FP32), ("fp32c", dem.DEM_FP32_COMP), ("fp64", dem.DEM_FP64))
+    out = {}
+    if a.drift_set == "configs":
+        fluids = {}
+    for name, f in fluids.items():
+        s = f["system"]
+        d = prepare(dem, s, dict(dt=0.005, ensemble="nvt", kT=1.0, tau=0.5),
+                    dem.DEM_FP64, 3000, 4000)
+        try:
+            s0 = _with_state(s, d.state())
+        finally:
+            d.close()
+        res = {"particles": s.n, "dt": f["dt"], "paper_fp32_drift_per_tau": f["paper_fp32"]}
+        for pname, prec in precs:
+            r = {"sigma_E_per_N_10tau": {}}
+            for dt in f["sweep"]:
+                with dem.DEM(s0, prec) as d:
+                    dem.dem_autotune(d.ctx)
+                    e = [d.energy()[2][0]]
+                    for _ in range(int(round(10.0 / dt))):
+                        d.step(1, dt, dem.DEM_NVE)
+                        e.append(d.energy()[2][0])
+                r["sigma_E_per_N_10tau"][str(dt)] = float(np.std(np.array(e) / s.n))
+            dt, every = f["dt"], 100
+            with dem.DEM(s0, prec) as d:
+                dem.dem_autotune(d.ctx)
+                t, e = [], []
+                t0 = time.perf_counter()
+                done = 0
+                while True:
+                    t.append(done * dt)
+                    e.append(d.energy()[2][0] / s.n)
+                    if done >= a.drift_steps:
+                        break
+                    d.step(every, dt, dem.DEM_NVE)
+                    done += every
+                wall = time.perf_counter() - t0
+            t, e = np.array(t), np.array(e)
+            slope = float(np.polyfit(t, e, 1)[0])
+            r.update(drift_per_tau=slope, drift_per_1e5_steps=slope * 1e5 * dt,
+                     E_per_N_start=float(e[0]), E_per_N_end=float(e[-1]), steps=done,
+                     wall_s=round(wall, 2))
+            res[pname] = r
+            print(f"[drift] {name} {pname}: {json.dumps(r)}", file=sys.stderr, flush=True)
+        out[name] = res
+    workloads = {} if a.drift_set == "fluids" else workload_drifts(a, dem, precs)
+    print(json.dumps({"metric": "energy drift of the conserved quantity per particle "
+                                "(epsilon per tau) and sigma(E/N) over 10 tau",
+                      "unit": "epsilon/tau", "data": "synthetic", "fluids": out,
+                      "workloads": workloads}))
+
+
+# workload, steps stated for it (its ensemble and dt come from make_workload)
+DRIFT_WORKLOADS = (("squares", 1000), ("cubes", 10000), ("octahedra", 100000),
+                   ("batched", 10000), ("large", 1000))
+
+
+def workload_drifts(a, dem, precs):
+    """The bench workloads in their own ensemble and dt (NVE: K + U; NVT: the
+    Nose-Hoover conserved quantity), from one prepared state per workload, in
+    each precision: the least-squares slope of H/N over the workload's stated
+    steps (fewer when --drift-budget runs out first; the steps run are
+    reported), about 100 samples, and that slope per 10^5 steps."""
+    out = {}
+    for name, steps in DRIFT_WORKLOADS:
+        system, run = make_workload(name, 0, a.replicas)
+        ens = dem.DEM_NVT if run["ensemble"] == "nvt" else dem.DEM_NVE
+        d = prepare(dem, system, run, dem.DEM_FP32_COMP, a.compress_steps, a.equil_steps)
+        try:
+            s0 = _with_state(system, d.state())
+        finally:
+            d.close()
+        dt, n = run["dt"], s0.n
+        res = {"particles": n, "replicas": len(s0.replica_sizes), "ensemble": run["ensemble"],
+               "dt": dt, "steps_stated": steps}
+        every = max(1, steps // 100)
+        for pname, prec in precs:
+            with dem.DEM(s0, prec) as d:
+                dem.dem_autotune(d.ctx)
+                t, e = [], []
+                t0 = time.perf_counter()
+                done = 0
+                while True:
+                    t.append(done * dt)
+                    e.append(float(np.sum(d.energy()[2])) / n)
+                    if done >= steps or time.perf_counter() - t0 > a.drift_budget:
+                        break
+                    d.step(every, dt, ens, kT=run["kT"], tau_T=run["tau"])
+                    done += every
+                wall = time.perf_counter() - t0
+            slope = float(np.polyfit(np.array(t), np.array(e), 1)[0])
+            r = dict(drift_per_tau=slope, drift_per_1e5_steps=slope * 1e5 * dt,
+                     H_per_N_start=e[0], H_per_N_end=e[-1], steps=done, wall_s=round(wall, 2))
+            res[pname] = r
+            print(f"[drift] {name} {pname}: {json.dumps(r)}", file=sys.stderr, flush=True)
+        out[name] = res
+    return out
 
 
 def reference_sample(system, run, budget):

@@ -467,6 +467,34 @@ def config_paper_table(shape: str = "icosahedron", n: int = 65536, phi: float = 
                    params=dict(dt=1e-3, ensemble="nvt", kT=kT, tau_T=0.5))
 
 
+def config_energy_drift(shape: str = "tetrahedron", n_side: int = 8, phi: float = 0.4,
+                        kT: float = 1.0, seed_index: int = 6) -> System:
+    """The fluids of Section "Energy Conservation", in reduced units with
+    sigma = 1 (rounding 0.5): squares of edge 4.24 sigma (2D, n_side^2
+    particles on a square lattice) or tetrahedra of edge 8.49 sigma (3D,
+    n_side^3 particles compressed from the safe lattice spacing), at packing
+    fraction ``phi`` of the rounded shapes (the paper gives no density;
+    0.5 for squares and 0.4 for tetrahedra are this reading's fluids)."""
+    rng = np.random.default_rng(np.random.SeedSequence(BASE_SEED + seed_index))
+    if shape == "square":
+        sh = square(4.24, 0.5)
+        n = n_side * n_side
+        L = math.sqrt(n * outer_measure(sh) / phi)
+        s = L / n_side
+        assert s >= safe_spacing(sh), "square lattice start would overlap"
+        pos = sc_sites([n_side, n_side], [s, s])
+        return _finish(rng, 2, [sh], np.zeros(n, np.int32), pos, [[L, L]], [n], kT,
+                       epsilon=1.0, sigma=0.0, name=f"drift_squares_N{n}_phi{phi:.2f}",
+                       params=dict(dt=0.01, ensemble="nve", kT=kT))
+    sh = tetrahedron(8.49, 0.5)
+    pos, start, target = _compressible_sc(rng, sh, [n_side] * 3, phi)
+    n = len(pos)
+    return _finish(rng, 3, [sh], np.zeros(n, np.int32), pos, [start], [n], kT,
+                   epsilon=1.0, sigma=0.0, target_box=target.reshape(1, 3),
+                   name=f"drift_tetrahedra_N{n}_phi{phi:.2f}",
+                   params=dict(dt=0.01, ensemble="nve", kT=kT))
+
+
 def sample_like(system: System, n_target: int = 512, kT: float = 1.0, seed: int = 0) -> System:
     """A small system like replica 0 of ``system``: the same shapes (drawn in
     the replica's proportions) at its target density, on m^d simple-cubic
