@@ -5,8 +5,8 @@
  * arXiv:1607.02427.
  *
  * What the library computes (Section "Model"):
- *   Each particle is an inner convex polygon (2D) or polyhedron (3D) rounded
- *   by a disk/sphere of radius sigma/2.  Particles i and j interact through
+ *   Each particle is an inner polygon (2D) or polyhedron (3D), convex or
+ *   concave, rounded by a disk/sphere of radius sigma/2.  Particles i and j interact through
  *   the WCA potential (Eq. LJ, Eq. WCA; r_cut = 2^(1/6) sigma) evaluated at
  *   the nearest-point distance of every feature pair:
  *     3D (Eq. DEM):    all edge-edge pairs, all vertex(i)-face(j) pairs and
@@ -103,18 +103,25 @@ typedef struct dem_ctx dem_ctx;   /* opaque; owned by the library */
  *   verts          n_verts * dim body-frame coordinates, centred on the
  *                  centre of mass, in principal axes
  *   n_faces        3D: number of faces (0 for a sphere, else >= 4);
- *                  2D: ignored (the polygon is the vertex loop, counter-
- *                  clockwise; 2 vertices make one edge)
+ *                  2D: ignored (the polygon is the vertex loop: simple and
+ *                  counter-clockwise, convex or not; 2 vertices make one edge)
  *   face_offsets   3D: n_faces + 1 offsets into face_verts
  *   face_verts     3D: vertex indices of each face, counter-clockwise seen
- *                  from outside; faces must be convex and planar
+ *                  from outside; each face must be convex and planar, and
+ *                  the faces must close the surface (every edge bounds two
+ *                  faces, traversed in opposite directions)
  *   rounding_radius  sigma/2 of the shape (> 0)
  *   mass           > 0
  *   inertia        3D: 3 principal moments, 2D: 1 (I_z); NULL derives them
  *                  for a uniform-density inner solid of the given mass.
- * The inner shape must be convex.  3D edges are derived from the faces.  A
- * shape has at most 32 vertices, 32 edges, 32 faces and 12 vertices per
- * face. */
+ * The inner shape may be concave (Section "Model"); only its faces must be
+ * convex, because the nearest point on a face is found by its edge tests.
+ * A self-intersecting 3D surface is not detected and is the caller's
+ * responsibility.  3D edges are derived from the faces.  A shape has at
+ * most 32 vertices, 32 edges, 32 faces and 12 vertices per face.
+ * Rejected with DEM_ERR_ARG: a 2D polygon with clockwise order, meeting
+ * non-neighbour edges or a fold; a 3D face that is not planar or convex; an
+ * open or inconsistently oriented surface; a non-positive enclosed volume. */
 typedef struct dem_shape {
     int dim;
     int n_verts;

@@ -50,6 +50,25 @@ static D3 crossp(D3 a, D3 b) {
 }
 static double norm(D3 a) { return sqrt(dotp(a, a)); }
 
+// Whether the closed 2D segments ab and cd share a point (crossing, touching
+// or overlapping), with a tolerance relative to their lengths.
+static bool segments_meet_2d(D3 a, D3 b, D3 c, D3 d) {
+    auto orient = [](D3 p, D3 q, D3 r) {
+        return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x);
+    };
+    const double tol = 1e-12 * std::max(dotp(sub(b, a), sub(b, a)), dotp(sub(d, c), sub(d, c)));
+    auto sgn = [&](double v) { return v > tol ? 1 : (v < -tol ? -1 : 0); };
+    auto within = [](D3 p, D3 q, D3 r) {   // r on the line pq: inside the box of pq?
+        return std::min(p.x, q.x) <= r.x && r.x <= std::max(p.x, q.x) &&
+               std::min(p.y, q.y) <= r.y && r.y <= std::max(p.y, q.y);
+    };
+    const int o1 = sgn(orient(a, b, c)), o2 = sgn(orient(a, b, d));
+    const int o3 = sgn(orient(c, d, a)), o4 = sgn(orient(c, d, b));
+    if (o1 * o2 < 0 && o3 * o4 < 0) return true;
+    return (o1 == 0 && within(a, b, c)) || (o2 == 0 && within(a, b, d)) ||
+           (o3 == 0 && within(c, d, a)) || (o4 == 0 && within(c, d, b));
+}
+
 // Validate one shape, derive its geometry (edges, circumradius) and, when
 // not given, the principal moments of the uniform inner solid.  The
 // integrals use the divergence theorem over a fan of simplices from the
@@ -89,13 +108,30 @@ static int preprocess_shape(const dem_shape &s, HostGeom *g, HostShape *h, std::
         if (nv == 2) g->edges.push_back({0, 1});
         if (nv >= 3) {
             for (int k = 0; k < nv; ++k) g->edges.push_back({k, (k + 1) % nv});
-            // counter-clockwise and convex: every turn is a left turn
+            // simple (no two edges meet except neighbours at their shared
+            // vertex) and counter-clockwise (positive area); it may be concave
+            double area2 = 0.0;
             for (int k = 0; k < nv; ++k) {
-                D3 a = d3(&g->v[3 * k]), b = d3(&g->v[3 * ((k + 1) % nv)]),
-                   c = d3(&g->v[3 * ((k + 2) % nv)]);
-                if (crossp(sub(b, a), sub(c, b)).z <= 0.0)
-                    return fail("2D polygon must be convex and counter-clockwise");
+                D3 a = d3(&g->v[3 * k]), b = d3(&g->v[3 * ((k + 1) % nv)]);
+                area2 += a.x * b.y - a.y * b.x;
+                if (!(norm(sub(b, a)) > 0.0)) return fail("2D polygon has a zero-length edge");
             }
+            if (!(area2 > 0.0)) return fail("2D polygon must be counter-clockwise (positive area)");
+            // no vertex where the boundary folds back on itself
+            for (int k = 0; k < nv; ++k) {
+                D3 m = d3(&g->v[3 * k]);
+                D3 u = sub(d3(&g->v[3 * ((k + nv - 1) % nv)]), m), w = sub(d3(&g->v[3 * ((k + 1) % nv)]), m);
+                if (fabs(u.x * w.y - u.y * w.x) <= 1e-12 * norm(u) * norm(w) && dotp(u, w) > 0.0)
+                    return fail("2D polygon folds back on itself at vertex %d", k);
+            }
+            // no two edges that are not neighbours meet
+            for (int k = 0; k < nv; ++k)
+                for (int l = k + 2; l < nv; ++l) {
+                    if (k == 0 && l == nv - 1) continue;
+                    if (segments_meet_2d(d3(&g->v[3 * k]), d3(&g->v[3 * ((k + 1) % nv)]),
+                                         d3(&g->v[3 * l]), d3(&g->v[3 * ((l + 1) % nv)])))
+                        return fail("2D polygon must be simple (edges %d and %d meet)", k, l);
+                }
             for (int k = 0; k < nv; ++k) {
                 D3 a = d3(&g->v[3 * k]), b = d3(&g->v[3 * ((k + 1) % nv)]);
                 double det = a.x * b.y - a.y * b.x;
@@ -146,10 +182,27 @@ static int preprocess_shape(const dem_shape &s, HostGeom *g, HostShape *h, std::
                 }
             if ((int)g->edges.size() > MAX_EDGES) return fail("more than %d edges", MAX_EDGES);
             if ((int)g->faces.size() > MAX_FACES) return fail("more than %d faces", MAX_FACES);
-            // faces planar, convex, counter-clockwise seen from outside
-            D3 vc = {0, 0, 0};
-            for (int k = 0; k < nv; ++k) vc = add(vc, d3(&g->v[3 * k]));
-            vc = scl(vc, 1.0 / nv);
+            // a closed surface with consistently oriented faces: every
+            // directed face edge a->b appears once, and b->a once on another face
+            {
+                std::vector<std::pair<int, int>> directed;
+                for (auto &loop : g->faces)
+                    for (size_t k = 0; k < loop.size(); ++k)
+                        directed.push_back({loop[k], loop[(k + 1) % loop.size()]});
+                std::sort(directed.begin(), directed.end());
+                for (size_t k = 0; k + 1 < directed.size(); ++k)
+                    if (directed[k] == directed[k + 1])
+                        return fail("faces are not consistently oriented (an edge is traversed "
+                                    "twice in the same direction)");
+                for (auto &e : directed)
+                    if (!std::binary_search(directed.begin(), directed.end(),
+                                            std::make_pair(e.second, e.first)))
+                        return fail("polyhedron is not closed (edge %d-%d bounds one face)",
+                                    e.first, e.second);
+            }
+            // faces planar and convex (the nearest point on a face relies on
+            // it; the polyhedron itself may be concave), counter-clockwise seen
+            // from outside (the enclosed volume is positive; checked below)
             double scale = g->R > 0 ? g->R : 1.0;
             for (auto &loop : g->faces) {
                 size_t m = loop.size();
@@ -163,8 +216,6 @@ static int preprocess_shape(const dem_shape &s, HostGeom *g, HostShape *h, std::
                 for (size_t k = 0; k < m; ++k)
                     if (fabs(dotp(sub(d3(&g->v[3 * loop[k]]), a0), n)) > 1e-9 * scale)
                         return fail("face is not planar");
-                if (dotp(sub(a0, vc), n) <= 0.0)
-                    return fail("face normal points inward (faces must be counter-clockwise from outside)");
                 for (size_t k = 0; k < m; ++k) {
                     D3 p = d3(&g->v[3 * loop[k]]), q = d3(&g->v[3 * loop[(k + 1) % m]]),
                        r = d3(&g->v[3 * loop[(k + 2) % m]]);
@@ -195,6 +246,8 @@ static int preprocess_shape(const dem_shape &s, HostGeom *g, HostShape *h, std::
             }
         }
     }
+    if (s.dim == 3 && nv > 1 && !(vol > 0.0))
+        return fail("faces must be counter-clockwise seen from outside (enclosed volume <= 0)");
     h->R = g->R;
     h->rounding = s.rounding_radius;
     h->mass = s.mass;

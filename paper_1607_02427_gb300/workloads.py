@@ -9,7 +9,8 @@ it does hold is input data and input recipes:
 
 * shape tables in each shape's principal-axis body frame (vertices, convex
   faces listed counter-clockwise seen from outside, rounding radius, mass,
-  principal moments of inertia of the uniform inner solid in closed form);
+  principal moments of inertia of the uniform inner solid in closed form),
+  convex or concave (the L-shaped hexagon, the dented cube);
 * the outer (rounded) volume or area of each shape in closed form, which
   turns a packing fraction into a box size (Steiner's formula for the
   parallel body at distance equal to the rounding radius);
@@ -175,6 +176,82 @@ def icosahedron(edge: float = 1.0, rounding: float = 0.15):
     i0 = edge * edge * p * p / 10.0
     return _shape(3, verts, faces, rounding, [i0] * 3, vol, 5 * math.sqrt(3) * edge ** 2,
                   30 * edge * (math.pi - dihedral) / 2, "icosahedron")
+
+
+# ---- concave shapes (Section "Model": the inner shape may be concave) -------
+#
+# Mass properties of a general polygon or polyhedron (uniform density, m = 1)
+# from the divergence theorem: shoelace sums over the edges in 2D, signed
+# tetrahedra (origin, face fan triangle) in 3D.  These size and centre the
+# input shapes only.
+
+def polygon_mass_properties(verts):
+    """Area, centroid and polar moment about the centroid (per unit mass) of
+    a simple counter-clockwise polygon."""
+    v = np.asarray(verts, np.float64)
+    w = np.roll(v, -1, axis=0)
+    cr = v[:, 0] * w[:, 1] - w[:, 0] * v[:, 1]
+    area = cr.sum() / 2.0
+    cen = ((v + w) * cr[:, None]).sum(0) / (6.0 * area)
+    sx = v[:, 0] ** 2 + v[:, 0] * w[:, 0] + w[:, 0] ** 2
+    sy = v[:, 1] ** 2 + v[:, 1] * w[:, 1] + w[:, 1] ** 2
+    j0 = (cr * (sx + sy)).sum() / 12.0           # integral of x^2 + y^2 about the origin
+    return float(area), cen, float(j0 / area - cen @ cen)
+
+
+def polyhedron_mass_properties(verts, faces):
+    """Volume, centroid and inertia tensor about the centroid (per unit mass)
+    of a closed polyhedron with faces counter-clockwise seen from outside."""
+    v = np.asarray(verts, np.float64)
+    vol, first, second = 0.0, np.zeros(3), np.zeros((3, 3))
+    for f in faces:
+        for k in range(1, len(f) - 1):
+            a, b, c = v[f[0]], v[f[k]], v[f[k + 1]]
+            det = float(a @ np.cross(b, c))
+            s = a + b + c
+            vol += det / 6.0
+            first += det / 24.0 * s
+            second += det / 120.0 * (np.outer(a, a) + np.outer(b, b) + np.outer(c, c)
+                                     + np.outer(s, s))
+    cen = first / vol
+    cov = second / vol - np.outer(cen, cen)      # integral of x x^T per unit mass
+    return vol, cen, np.trace(cov) * np.eye(3) - cov
+
+
+def l_shape2d(arm: float = 1.0, rounding: float = 0.15):
+    """L-shaped hexagon (2D, one reflex vertex): the 2a x 2a square minus its
+    upper-right a x a quarter, centred on its centroid (5a/6, 5a/6 from the
+    outer corner); I_z = 11 m a^2 / 18.  Packing fractions of this shape count
+    its rounded convex hull (the pentagon with the notch filled in)."""
+    a = arm
+    raw = np.array([(0, 0), (2 * a, 0), (2 * a, a), (a, a), (a, 2 * a), (0, 2 * a)], np.float64)
+    area, cen, iz = polygon_mass_properties(raw)
+    hull_area = 3.5 * a * a
+    hull_perimeter = 6 * a + math.sqrt(2) * a
+    sh = _shape(2, raw - cen, None, rounding, [iz], hull_area, hull_perimeter, 0.0, "lshape")
+    sh["area"] = area
+    sh["reflex_vertex"] = 3
+    return sh
+
+
+def dented_cube(edge: float = 1.0, depth: float = 0.5, rounding: float = 0.15):
+    """Cube whose top face is pushed in to a square pyramid of the given
+    depth (concave; 9 vertices, 16 edges, 9 convex faces: the bottom, four
+    sides and four triangles meeting at the apex on the axis).  Centred on
+    its centre of mass; principal axes x, y, z by the four-fold symmetry.
+    Packing fractions of this shape count its rounded convex hull (the cube)."""
+    h = 0.5 * edge
+    raw = [(-h, -h, -h), (h, -h, -h), (h, h, -h), (-h, h, -h),
+           (-h, -h, h), (h, -h, h), (h, h, h), (-h, h, h), (0.0, 0.0, h - depth)]
+    faces = [(0, 3, 2, 1), (0, 1, 5, 4), (2, 3, 7, 6), (0, 4, 7, 3), (1, 2, 6, 5),
+             (4, 5, 8), (5, 6, 8), (6, 7, 8), (7, 4, 8)]
+    vol, cen, inertia = polyhedron_mass_properties(raw, faces)
+    a2 = edge * edge
+    sh = _shape(3, np.asarray(raw) - cen, faces, rounding, np.diag(inertia), edge ** 3, 6 * a2,
+                12 * edge * (math.pi / 2) / 2, "dented_cube")
+    sh["volume"] = vol
+    sh["apex"] = 8
+    return sh
 
 
 def circumradius(shape) -> float:

@@ -71,3 +71,82 @@ SHAPES_3D = {
     "prism": lambda: W.triangular_prism(1.0, 1.0, 0.15),
     "icosahedron": lambda: W.icosahedron(0.8, 0.15),
 }
+
+
+def nest_guests(s, hosts, guest, local_points, seed, gap_min=0.8):
+    """Append one-vertex guests (disks or spheres) at ``local_points`` (body
+    frame of each host: e.g. inside an L-shape's notch or a dented cube's
+    dent, within r_cut of the concave features).  A guest is kept only when,
+    along the centre line to every particle but its host, the separating-axis
+    gap is at least gap_min * sigma_ij.  Returns a new one-replica system."""
+    rng = np.random.default_rng(seed)
+    dim = s.dim
+    box = s.box[0]
+    shapes = list(s.shapes) + [guest]
+    gid = len(shapes) - 1
+    pos, orient = [s.pos.copy()], [s.orient.copy()]
+    ids = [s.shape_id.copy()]
+    rnd = np.array([shapes[k]["rounding"] for k in s.shape_id])
+    added = []
+    for h in hosts:
+        lp = np.asarray(local_points[int(rng.integers(len(local_points)))], float)
+        if dim == 3:
+            x = s.pos[h] + rotmat(s.orient[h]) @ lp
+        else:
+            c, sn = np.cos(s.orient[h, 0]), np.sin(s.orient[h, 0])
+            x = s.pos[h] + np.array([c * lp[0] - sn * lp[1], sn * lp[0] + c * lp[1]])
+        x = np.mod(x, box)
+        cand = np.concatenate([s.pos] + [np.array(added).reshape(-1, dim)], 0)
+        cand_ids = np.concatenate([s.shape_id, np.full(len(added), gid, np.int32)])
+        ok = True
+        for k in range(len(cand)):
+            if k == h:
+                continue
+            d = x - cand[k]
+            d -= box * np.round(d / box)
+            dist = np.linalg.norm(d)
+            if dist == 0.0:
+                ok = False
+                break
+            e = d / dist
+            sh_k = shapes[int(cand_ids[k])]
+            sig = sh_k["rounding"] + guest["rounding"] if s.sigma <= 0 else s.sigma
+            o_k = s.orient[k] if k < s.n else (np.array([1.0, 0, 0, 0]) if dim == 3 else np.array([0.0]))
+            g = dist - W._support(sh_k, o_k, e)
+            if g < gap_min * sig:
+                ok = False
+                break
+        if ok:
+            added.append(x)
+    m = len(added)
+    if m == 0:
+        raise RuntimeError("no guest could be placed")
+    rng2 = np.random.default_rng(seed + 1)
+    g_or = (np.tile([1.0, 0, 0, 0], (m, 1)) if dim == 3 else np.zeros((m, 1)))
+    n = s.n + m
+    out = W.System(dim, shapes, np.concatenate(ids + [np.full(m, gid, np.int32)]),
+                   np.concatenate(pos + [np.array(added)], 0), np.concatenate(orient + [g_or], 0),
+                   np.zeros((n, dim)), np.zeros((n, 3 if dim == 3 else 1)), s.box.copy(),
+                   np.array([n], np.int32), s.epsilon, s.sigma, name=s.name + "+nested")
+    out.vel = W.maxwell_velocities(rng2, [n], dim, 1.0, out.masses())
+    out.angmom = W.thermal_angmom(rng2, out.inertia(), out.orient, dim, 1.0)
+    return out
+
+
+def notch_points(L, sigma, fracs=((0.85, 0.95), (0.9, 0.8), (0.97, 0.88))):
+    """Body-frame points in an L-shape's notch at fractions of r_cut from the
+    two edges that meet at the reflex vertex."""
+    rc = 2.0 ** (1.0 / 6.0) * sigma
+    c = L["verts"][L["reflex_vertex"]]
+    return [c + rc * np.array(f) for f in fracs]
+
+
+def dent_points(D, sigma, fracs=(0.82, 0.9, 0.97)):
+    """Body-frame points on a dented cube's axis above the apex, the four dent
+    faces at fractions of r_cut."""
+    rc = 2.0 ** (1.0 / 6.0) * sigma
+    apex = D["verts"][D["apex"]]
+    t = 0.5 * (D["verts"][:, 0].max() - D["verts"][:, 0].min())
+    depth = D["verts"][4, 2] - apex[2]
+    k = np.hypot(depth, t) / t           # axial height per unit face distance
+    return [apex + np.array([0.0, 0.0, f * rc * k]) for f in fracs]

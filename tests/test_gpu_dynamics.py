@@ -19,6 +19,7 @@ import pytest
 import oracle
 from paper_1607_02427_gb300 import workloads as W
 from tests.gpu_common import load_dem
+from tests.helpers import dent_points, nest_guests, notch_points
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +62,13 @@ CASES = {
     "squares_nve": (lambda: _cluster([W.square(1.0, 0.15)], 80, [16.0, 16.0], 34, sigma=0.3), "nve"),
     "polys_nvt": (lambda: _cluster([W.polygon(6, 0.6, 0.12), W.square(0.9, 0.1)], 80,
                                    [16.0, 16.0], 35), "nvt"),
+    # concave inner shapes (Section "Model")
+    "dented_nvt": (lambda: nest_guests(_cluster([W.dented_cube(1.0, 0.6, 0.12)], 50, [9.0] * 3, 36),
+                                       range(0, 50, 2), W.sphere(0.15, 0.009),
+                                       dent_points(W.dented_cube(1.0, 0.6, 0.12), 0.27), 36), "nvt"),
+    "lshapes_nve": (lambda: nest_guests(_cluster([W.l_shape2d(0.6, 0.12)], 70, [16.0, 16.0], 37),
+                                        range(0, 70, 2), W.disk(0.15, 0.01),
+                                        notch_points(W.l_shape2d(0.6, 0.12), 0.27), 37), "nve"),
 }
 
 

@@ -3,7 +3,7 @@ FP64 oracle, element by element, through the C ABI.
 
 Inputs: seeded contact-rich random clusters in periodic boxes (2D squares,
 mixed polygons / rods / disks, 3D cubes, tetrahedra, octahedra, prisms,
-spheres and mixtures), sizes that span several thread blocks with a ragged
+spheres and mixtures, and the concave L-shaped hexagon and dented cube), sizes that span several thread blocks with a ragged
 tail, multi-replica batches mixing cell-list and all-pairs replicas, and
 edge cases (a lone particle, particles with no contacts, a tiny neighbour
 list that must grow).  Tolerances and error measures: tests/gpu_common.py.
@@ -13,6 +13,7 @@ import pytest
 
 from paper_1607_02427_gb300 import workloads as W
 from tests.gpu_common import TOL, assert_parity, compare_forces, load_dem
+from tests.helpers import dent_points, nest_guests, notch_points
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +54,17 @@ def _systems():
                                                [9.0, 9.0, 9.0], 8)
     out["icosas"] = lambda: _periodic_cluster([W.icosahedron(0.8, 0.15)], np.zeros(250, int),
                                               [12.0, 12.0, 12.0], 10)
+    # concave inner shapes (Section "Model"): the L-shaped hexagon with disks,
+    # the dented cube with cubes and spheres
+    # (disks / spheres nested in the notches / dents, within r_cut of the
+    # concave features)
+    L, D = W.l_shape2d(0.6, 0.12), W.dented_cube(1.0, 0.6, 0.12)
+    out["lshapes"] = lambda: nest_guests(
+        _periodic_cluster([L], np.zeros(180, int), [30.0, 30.0], 12),
+        range(0, 180, 2), W.disk(0.15, 0.01), notch_points(L, 0.27), 12)
+    out["dented"] = lambda: nest_guests(
+        _periodic_cluster([D, W.cube(0.9, 0.1)], np.arange(220) % 2, [14.0, 14.0, 14.0], 13),
+        range(0, 220, 2), W.sphere(0.15, 0.009), dent_points(D, 0.27), 13)
     out["mixed3d"] = lambda: _periodic_cluster(
         [W.cube(1.0, 0.15), W.tetrahedron(1.0, 0.1), W.triangular_prism(1.0, 1.0, 0.2),
          W.sphere(0.3, 0.036), W.octahedron(0.9, 0.12)], np.arange(290) % 5,

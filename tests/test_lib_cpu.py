@@ -70,20 +70,65 @@ def test_shape_info_2d(dem):
                                                         rel=1e-12)
 
 
-@pytest.mark.parametrize("bad", ["inward", "nonconvex", "offcentre", "rounding"])
+def test_shape_info_concave(dem):
+    """Concave shapes (Section "Model"): the library's derived mass
+    properties equal the closed forms (L-shape: area 3 a^2, I_z = 11 a^2/18;
+    dented cube: volume a^3 - a^2 h / 3, I_zz = (a^5/6 - a^4 h/30) / V)."""
+    L = dict(W.l_shape2d(1.0, 0.15), inertia=None)
+    info = dem.dem_shape_info(L)
+    assert info[1] == 6
+    assert info[2] == pytest.approx(11 / 18, rel=1e-12)
+    assert info[5] == pytest.approx(3.0, rel=1e-12)
+    a, h = 1.0, 0.5
+    D = W.dented_cube(a, h, 0.15)
+    info = dem.dem_shape_info(dict(D, inertia=None))
+    V = a ** 3 - a * a * h / 3
+    assert info[1] == 16
+    assert info[5] == pytest.approx(V, rel=1e-12)
+    assert info[4] == pytest.approx((a ** 5 / 6 - a ** 4 * h / 30) / V, rel=1e-12)
+    np.testing.assert_allclose(info[2:5], D["inertia"], rtol=1e-12)
+    assert info[6] < 1e-12
+
+
+@pytest.mark.parametrize("bad", ["inward", "flipped_face", "open", "nonplanar", "nonconvex_face",
+                                 "bowtie", "clockwise", "fold", "offcentre", "rounding"])
 def test_shape_validation(dem, bad):
     sh = W.cube(1.0, 0.15)
     sh = dict(sh, inertia=None)
     if bad == "inward":
         sh["faces"] = [list(reversed(f)) for f in sh["faces"]]
-    elif bad == "nonconvex":
-        sh = dict(W.square(1.0, 0.15), inertia=None)
-        sh["verts"] = np.array([[-.5, -.5], [.5, -.5], [0, -.3], [-.5, .5]])
+    elif bad == "flipped_face":
+        sh["faces"] = [list(reversed(f)) if k == 2 else f for k, f in enumerate(sh["faces"])]
+    elif bad == "open":
+        sh = dict(W.dented_cube(1.0, 0.5, 0.15))
+        sh["faces"] = sh["faces"][:-1]
+    elif bad == "nonplanar":
+        sh["verts"] = sh["verts"].copy()
+        sh["verts"][6, 2] += 0.05
+        sh["inertia"] = [1 / 6] * 3
+    elif bad == "nonconvex_face":
+        # a dart-shaped top face: the nearest point on a face needs convex faces
+        v = np.array([[-1, -1, 0], [1, -1, 0], [0, -0.2, 0], [-1, 1, 0], [0, 0, -1.0]])
+        sh = dict(dim=3, verts=v, faces=[[0, 1, 2, 3], [0, 4, 1], [1, 4, 2], [2, 4, 3], [3, 4, 0]],
+                  rounding=0.1, mass=1.0, inertia=[1.0, 1.0, 1.0])
+    elif bad == "bowtie":
+        sh = dict(W.square(1.0, 0.15), inertia=[1.0])
+        sh["verts"] = np.array([[-.5, -.5], [.5, .5], [.5, -.5], [-.5, .5], [-.6, 0.0]])
+    elif bad == "clockwise":
+        sh = dict(W.l_shape2d(1.0, 0.15))
+        sh["verts"] = sh["verts"][::-1].copy()
+    elif bad == "fold":
+        sh = dict(W.square(1.0, 0.15), inertia=[1.0])
+        sh["verts"] = np.array([[-.5, -.5], [.5, -.5], [.5, .5], [.5, 0.0], [-.5, .5]])
     elif bad == "offcentre":
         sh["verts"] = sh["verts"] + 0.1
     elif bad == "rounding":
         sh["rounding"] = 0.0
-    with pytest.raises(dem.DemError):
+    reason = {"inward": "enclosed volume", "flipped_face": "consistently oriented",
+              "open": "not closed", "nonplanar": "not planar", "nonconvex_face": "not convex",
+              "bowtie": "simple", "clockwise": "counter-clockwise", "fold": "folds back",
+              "offcentre": "centred", "rounding": "rounding"}[bad]
+    with pytest.raises(dem.DemError, match=reason):
         dem.dem_shape_info(sh)
 
 

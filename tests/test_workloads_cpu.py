@@ -75,6 +75,50 @@ def test_outer_volume_monte_carlo():
     assert abs(got - want) < 4 * se, (got, want, se)
 
 
+# ---- mass properties of general polygons and polyhedra ------------------------
+
+@pytest.mark.parametrize("mk,I", [
+    (lambda: W.cube(1.0), [1 / 6] * 3),
+    (lambda: W.tetrahedron(1.0), [1 / 20] * 3),
+    (lambda: W.octahedron(1.0), [1 / 5] * 3),
+    (lambda: W.triangular_prism(1.0, 1.0), [1 / 24 + 1 / 12, 1 / 24 + 1 / 12, 1 / 12]),
+])
+def test_polyhedron_mass_properties_closed_forms(mk, I):
+    sh = mk()
+    vol, cen, inertia = W.polyhedron_mass_properties(sh["verts"], sh["faces"])
+    assert vol == pytest.approx(sh["inner_measure"], rel=1e-12)
+    assert np.abs(cen).max() < 1e-12
+    np.testing.assert_allclose(inertia, np.diag(I), atol=1e-12)
+
+
+def test_polygon_mass_properties_closed_forms():
+    for sh in (W.square(1.3), W.polygon(7, 0.9)):
+        area, cen, iz = W.polygon_mass_properties(sh["verts"])
+        assert area == pytest.approx(sh["inner_measure"], rel=1e-12)
+        assert np.abs(cen).max() < 1e-12
+        assert iz == pytest.approx(sh["inertia"][0], rel=1e-12)
+
+
+def test_concave_shapes_centred():
+    """The L-shape (I_z = 11 a^2 / 18, area 3 a^2) and the dented cube
+    (volume a^3 - a^2 h / 3; centroid shift (a^2 h / 3)(a/2 - h/4) / V;
+    I_zz = (a^5/6 - a^4 h / 30) / V) in closed form, centred."""
+    a = 0.8
+    L = W.l_shape2d(a, 0.1)
+    area, cen, iz = W.polygon_mass_properties(L["verts"])
+    assert area == pytest.approx(3 * a * a, rel=1e-12) and np.abs(cen).max() < 1e-12
+    assert iz == pytest.approx(11 * a * a / 18, rel=1e-12) == L["inertia"][0]
+    a, h = 1.2, 0.4
+    D = W.dented_cube(a, h, 0.1)
+    V = a ** 3 - a * a * h / 3
+    vol, cen, inertia = W.polyhedron_mass_properties(D["verts"], D["faces"])
+    assert vol == pytest.approx(V, rel=1e-12) and np.abs(cen).max() < 1e-12
+    shift = (a * a * h / 3) * (a / 2 - h / 4) / V
+    assert D["verts"][0, 2] == pytest.approx(-a / 2 + shift, rel=1e-12)
+    assert inertia[2, 2] == pytest.approx((a ** 5 / 6 - a ** 4 * h / 30) / V, rel=1e-12)
+    assert np.abs(inertia - np.diag(np.diag(inertia))).max() < 1e-12
+
+
 # ---- the named workloads ----------------------------------------------------
 
 def _phi(system, k=0):
