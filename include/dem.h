@@ -157,8 +157,11 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
  *             2D: N angles
  *   vel       N * dim
  *   angmom    3D: N * 3 world-frame angular momenta; 2D: N values of L_z
- * Rebuilds the neighbour list, evaluates forces, and resets the thermostat
- * variables to zero.  Errors: DEM_ERR_ARG, DEM_ERR_BOX (a box edge below
+ * Evaluates forces and resets the thermostat variables to zero.  The
+ * neighbour list is rebuilt when any shape id differs from the previous
+ * call's, or when a particle lies more than skin/2 from its position at the
+ * last build (the test a step makes); otherwise the list is kept, which is
+ * exact: it holds every pair within the interaction range.  Errors: DEM_ERR_ARG, DEM_ERR_BOX (a box edge below
  * twice the neighbour-list cutoff R_i + R_j + r_cut + skin of the replica's
  * largest shapes), DEM_ERR_CUDA, DEM_ERR_NONFINITE. */
 int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const double *orient,

@@ -439,6 +439,7 @@ struct dem_ctx {
     std::vector<double> box;   // R * 3
     std::vector<Rep> reps;
     std::vector<int> shape_host;
+    std::vector<int> ids_in;          // dem_set_state: device shape ids copied to the host
     int n_cells = 0;
     // parameters
     double skin = -1, par_eps = 1e-6;
@@ -1184,19 +1185,32 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
         return set_err(ctx, DEM_ERR_ARG, "dem_set_state: all arrays are required");
     const size_t n = ctx->N;
     const int dim = ctx->dim;
-    ctx->shape_host.resize(n);
+    const int *ids = shape_id;
     if (device_ptrs) {
-        CK(cudaMemcpyAsync(ctx->shape_host.data(), shape_id, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->ids_in.resize(n);
+        CK(cudaMemcpyAsync(ctx->ids_in.data(), shape_id, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
-    } else {
-        memcpy(ctx->shape_host.data(), shape_id, sizeof(int) * n);
+        ids = ctx->ids_in.data();
     }
-    for (size_t i = 0; i < n; ++i)
-        if (ctx->shape_host[i] < 0 || ctx->shape_host[i] >= ctx->n_shapes)
+    // The same shape of every particle keeps the replica tables, the cell grid
+    // and the neighbour list: the list stays valid while every particle is
+    // within skin/2 of its position at the build, which the device tests
+    // below as in a step.  New shapes rebuild everything.  (One pass: range
+    // check and comparison.)
+    bool same_shapes = ctx->have_state && ctx->shape_host.size() == n;
+    for (size_t i = 0; i < n; ++i) {
+        const int v = ids[i];
+        if (v < 0 || v >= ctx->n_shapes)
             return set_err(ctx, DEM_ERR_ARG, "shape_id[%zu] out of range", i);
-    CK(cudaMemcpyAsync(ctx->shape, ctx->shape_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
-    int rc = setup_replicas(ctx);
-    if (rc) return rc;
+        same_shapes = same_shapes && v == ctx->shape_host[i];
+    }
+    int rc = DEM_OK;
+    if (!same_shapes) {
+        ctx->shape_host.assign(ids, ids + n);
+        CK(cudaMemcpyAsync(ctx->shape, ctx->shape_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+        rc = setup_replicas(ctx);
+        if (rc) return rc;
+    }
     const int odim = dim == 3 ? 4 : 1, adim = dim == 3 ? 3 : 1;
     const double *src[4] = {pos, orient, vel, angmom};
     const int widths[4] = {dim, odim, dim, adim};
@@ -1221,8 +1235,13 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
     CK(launch_prepare_state((int)n, dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom, ctx->rep,
                             ctx->d_reps, 1, ctx->stream));
     CK(cudaMemsetAsync(ctx->thermo, 0, sizeof(Thermo) * ctx->R, ctx->stream));
-    rc = force_rebuild(ctx);
-    if (rc) return rc;
+    if (same_shapes) {
+        StepArgs da = step_args(ctx, 0.0, DEM_NVE, 1.0, 1.0);
+        CK(launch_displacement(da, ctx->stream));
+    } else {
+        rc = force_rebuild(ctx);
+        if (rc) return rc;
+    }
     ctx->have_state = true;
     rc = compute_forces(ctx);
     if (rc) return rc;

@@ -203,6 +203,8 @@ cudaError_t launch_pair_split(const PairArgs &a, int precision, bool count, size
 cudaError_t launch_cells(const NlistArgs &a, int n_cells, cudaStream_t s);
 cudaError_t launch_nlist(const NlistArgs &a, cudaStream_t s);
 cudaError_t launch_first_half(const StepArgs &a, cudaStream_t s);
+// the rebuild test and the FP32 deltas for positions set from outside
+cudaError_t launch_displacement(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_second_half(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_thermo_begin(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_thermo_end(const StepArgs &a, cudaStream_t s);

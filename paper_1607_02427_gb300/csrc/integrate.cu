@@ -150,6 +150,36 @@ __device__ __forceinline__ double nh_rate(double K, double g, double kT, double 
     return (2.0 * K / (g * kT) - 1.0) / (tau * tau);
 }
 
+// Displacement of particle i (at x) since the list build, whose position
+// scales with the box (sc = 1 unless a barostat moved it): stored as the FP32
+// delta that the pair kernels add to the list separations.  Returns the
+// squared displacement for the rebuild test (skin/2)^2, padded by disp_pad
+// when the box has shrunk since the build.
+__device__ __forceinline__ float since_build(const StepArgs &a, const Rep &rp, int i,
+                                             const double4_32a &x) {
+    const double4_32a x0 = a.x_last[i];
+    const double sc = rp.sc_d;
+    double dx = x.x - sc * x0.x, dy = x.y - sc * x0.y, dz = x.z - sc * x0.z;
+    dx -= rp.L[0] * rint(dx * rp.inv_L[0]);
+    dy -= rp.L[1] * rint(dy * rp.inv_L[1]);
+    if (a.dim == 3) dz -= rp.L[2] * rint(dz * rp.inv_L[2]); else dz = 0.0;
+    double d2 = dx * dx + dy * dy + dz * dz;
+    if (rp.disp_pad > 0.f) {
+        const double d = sqrt(d2) + (double)rp.disp_pad;
+        d2 = d * d;
+    }
+    a.delta[i] = make_float4((float)dx, (float)dy, (float)dz, __int_as_float(a.shape[i]));
+    return (float)d2;
+}
+
+// Warp max, one atomic per warp (non-negative floats order like their bits);
+// every lane of the warp calls it.
+__device__ __forceinline__ void max_to_status(const StepArgs &a, float dmax) {
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0 && dmax > 0.f)
+        atomicMax(&a.status->maxdisp2, __float_as_uint(dmax));
+}
+
 __global__ void k_first_half(const StepArgs a) {
     float dmax = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
@@ -201,26 +231,18 @@ __global__ void k_first_half(const StepArgs a) {
         a.angmom[i] = L;
         a.quat[i] = q;
         a.quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
-        // displacement since the list build; the build position scales with
-        // the box (sc = 1 unless a barostat moved it)
-        double4_32a x0 = a.x_last[i];
-        const double sc = rp.sc_d;
-        double dx = x.x - sc * x0.x, dy = x.y - sc * x0.y, dz = x.z - sc * x0.z;
-        dx -= rp.L[0] * rint(dx * rp.inv_L[0]);
-        dy -= rp.L[1] * rint(dy * rp.inv_L[1]);
-        if (a.dim == 3) dz -= rp.L[2] * rint(dz * rp.inv_L[2]); else dz = 0.0;
-        double d2 = dx * dx + dy * dy + dz * dz;
-        if (rp.disp_pad > 0.f) {
-            const double d = sqrt(d2) + (double)rp.disp_pad;
-            d2 = d * d;
-        }
-        dmax = fmaxf(dmax, (float)d2);
-        a.delta[i] = make_float4((float)dx, (float)dy, (float)dz, __int_as_float(a.shape[i]));
+        dmax = fmaxf(dmax, since_build(a, rp, i, x));
     }
-    // warp max, one atomic per warp (non-negative floats order like their bits)
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    if ((threadIdx.x & 31) == 0 && dmax > 0.f)
-        atomicMax(&a.status->maxdisp2, __float_as_uint(dmax));
+    max_to_status(a, dmax);
+}
+
+// The rebuild test after positions were replaced from outside (state upload):
+// the displacement of every particle since the list build, as in a step.
+__global__ void k_displacement(const StepArgs a) {
+    float dmax = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
+        dmax = fmaxf(dmax, since_build(a, a.reps[a.rep[i]], i, a.pos[i]));
+    max_to_status(a, dmax);
 }
 
 __device__ __forceinline__ double kinetic_of(const ShapeDev &sh, const double4_32a &v,
@@ -618,6 +640,10 @@ inline int grid_for(int n, int block) {
 
 cudaError_t launch_first_half(const StepArgs &a, cudaStream_t s) {
     k_first_half<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_displacement(const StepArgs &a, cudaStream_t s) {
+    k_displacement<<<grid_for(a.n, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_second_half(const StepArgs &a, cudaStream_t s) {

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from paper_1607_02427_gb300 import workloads as W
-from tests.gpu_common import TOL, assert_parity, compare_forces, load_dem
+from tests.gpu_common import TOL, assert_parity, compare_forces, force_errors, load_dem
 from tests.helpers import dent_points, nest_guests, notch_points
 
 pytestmark = pytest.mark.gpu
@@ -207,3 +207,49 @@ def test_state_roundtrip(dem):
     qn = s.orient / np.linalg.norm(s.orient, axis=1, keepdims=True)
     np.testing.assert_allclose(st["orient"], qn, atol=1e-15)
     np.testing.assert_allclose(st["angmom"], s.angmom, atol=1e-13)
+
+
+def _ctx_errors(d, system):
+    """Errors of a live context's current outputs against the oracle."""
+    import oracle
+    f, t = d.forces()
+    U, _, _ = d.energy()
+    out = dict(force=f, torque=t, U=U, W=d.virial(), energy=d.particle_energy(), counts=None)
+    return force_errors(system, oracle.forces(system), out)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=[PNAMES[p] for p in PRECISIONS])
+def test_set_state_keeps_valid_list(dem, precision):
+    """A state upload with the same shapes keeps the neighbour list while
+    every particle is within skin/2 of its position at the build, and
+    rebuilds it otherwise; new shape ids rebuild everything.  Forces match
+    the oracle in every case."""
+    s = system("cubes")
+    rng = np.random.default_rng(41)
+    with dem.DEM(s, precision) as d:
+        skin = d.get_param("skin")
+        rb = lambda: int(d.counters()[13])
+        r0 = rb()
+        # small moves: the list stays
+        small = s.pos + rng.uniform(-1, 1, s.pos.shape) * 0.2 * skin / np.sqrt(3)
+        t = W.System(s.dim, s.shapes, s.shape_id, np.mod(small, s.box[0]), s.orient, s.vel,
+                     s.angmom, s.box, s.replica_sizes, s.epsilon, s.sigma)
+        dem.dem_set_state(d.ctx, t.shape_id, t.pos, t.orient, t.vel, t.angmom)
+        assert rb() == r0, "a valid list must be kept"
+        assert_parity(_ctx_errors(d, t), precision, "set_state small move")
+        # one particle beyond skin/2: rebuilt
+        big = small.copy()
+        big[7] += 0.8 * skin
+        t.pos = np.mod(big, s.box[0])
+        dem.dem_set_state(d.ctx, t.shape_id, t.pos, t.orient, t.vel, t.angmom)
+        assert rb() == r0 + 1, "the list must be rebuilt"
+        assert_parity(_ctx_errors(d, t), precision, "set_state large move")
+    # new shape ids: full setup (a cube becomes a smaller cube)
+    s2 = system("dented")
+    with dem.DEM(s2, precision) as d:
+        ids = s2.shape_id.copy()
+        ids[ids == 0] = 1            # dented cubes become cubes
+        t = W.System(s2.dim, s2.shapes, ids, s2.pos, s2.orient, s2.vel, s2.angmom, s2.box,
+                     s2.replica_sizes, s2.epsilon, s2.sigma)
+        dem.dem_set_state(d.ctx, t.shape_id, t.pos, t.orient, t.vel, t.angmom)
+        assert_parity(_ctx_errors(d, t), precision, "set_state new shapes")
