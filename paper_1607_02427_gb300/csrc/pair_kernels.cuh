@@ -452,6 +452,28 @@ __device__ __forceinline__ void finish_particle(const PairArgs &a, int i, const 
 }
 
 
+// Items t0 .. t0+31 of consecutive ranges [off_p, off_p + c_p), range p held
+// by lane p: the range of item t0 + lane, for all lanes at once.  Each range
+// with items in the round marks the lane of its first one there (who: 32
+// ints of the warp's shared memory); a lane's range is the last mark at or
+// below it.  Warp-collective; lanes past the last item get an arbitrary range.
+__device__ __forceinline__ int round_owner(int off_me, int c_me, int t0, int lane, int *who) {
+    const int s = off_me - t0, e = s + c_me;
+    unsigned bit = 0u;
+    if (c_me > 0 && e > 0 && s < 32) {
+        const int b = s > 0 ? s : 0;
+        who[b] = lane;
+        bit = 1u << b;
+    }
+    const unsigned starts = __reduce_or_sync(FULL, bit);
+    __syncwarp();
+    const unsigned upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;
+    const unsigned m = starts & upto;
+    const int own = m ? who[31 - __clz(m)] : 0;
+    __syncwarp();
+    return own;
+}
+
 __device__ __forceinline__ int owner_of(const int *off, int n, int t) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {

@@ -81,11 +81,13 @@ template <class T, int PR> struct BatchSmem {   // PR: pair ring entries (a powe
     } fq;
     TermRec<T> tq[RING];
     int boffs[32];                     // item offsets of the batch's pairs
+    int who[32];                       // pair whose items start at lane k of a round
     unsigned gmask[32];                // per owner: lanes holding its terms
 };
 template <class T> struct ScanSmem {
     SInfo<T> info[32];
     int offs[32];                      // list offsets of the 32 particles
+    int who[32];                       // particle whose entries start at lane k of a round
 };
 template <class T> struct StagedSmem {
     BatchSmem<T, RING> b;
@@ -140,7 +142,8 @@ template <class T> __device__ __forceinline__ V3<T> pair_dl(const SPair<T> &P) {
 // Every stage has one call site (code size: the stages of 16 warps per SM
 // must share the instruction cache).  batch() is a loop whose body does one
 // action per turn: consumers first, so that no ring reaches 64 entries,
-// then one step of the current producer.
+// then steps of the current producer until its ring holds 32 entries or
+// its items are done.
 template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged {
     using R4 = typename R4T<T>::type;
     const PairArgs &a;
@@ -160,6 +163,7 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
     // va, vb, vc = its start, direction and centre in i's frame
     unsigned cm = 0u;                  // features of the other shape left to test
     int cp = 0, cside = 0, cidx = 0, coff = 0;
+    int citems = 0;                    // items of this lane's pair in the current phase
     V3<T> va, vb, vc;
     T crb = T(0), crc = T(0);          // j's edge radius; r_cut
 
@@ -361,15 +365,23 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         }
         int total;
         ws.boffs[lane] = warp_excl_scan(c, lane, &total);
+        citems = c;
         __syncwarp();
         return total;
     }
 
-    // take vertex item t (t < total): map the vertex, reach test
-    __device__ __forceinline__ void load_vertex_item(int t, int total, int nb) {
+    // the pair of item t0 + lane of the current phase (warp-collective)
+    __device__ __forceinline__ int item_pair(int t0) {
+        return round_owner(ws.boffs[lane], citems, t0, lane, ws.who);
+    }
+
+    // take vertex item t0 + lane (if below total): map the vertex, reach test
+    __device__ __forceinline__ void load_vertex_item(int t0, int total) {
         cm = 0u;
+        const int own = item_pair(t0);
+        const int t = t0 + lane;
         if (t >= total) return;
-        cp = owner_of(ws.boffs, nb, t);
+        cp = own;
         const int k = t - ws.boffs[cp];
         const SPair<T> &P = pair(cp);
         const Geom &gi = geom_i(P), &gj = geo[P.gj];
@@ -451,11 +463,13 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         }
     }
 
-    // take edge item t: j's edge into i's frame, reach test
-    __device__ __forceinline__ void load_edge_item(int t, int total, int nb) {
+    // take edge item t0 + lane (if below total): j's edge into i's frame, reach test
+    __device__ __forceinline__ void load_edge_item(int t0, int total) {
         cm = 0u;
+        const int own = item_pair(t0);
+        const int t = t0 + lane;
         if (t >= total) return;
-        cp = owner_of(ws.boffs, nb, t);
+        cp = own;
         const SPair<T> &P = pair(cp);
         const Geom &gi = geom_i(P), &gj = geo[P.gj];
         cidx = nth_set_bit(P.ejm, t - ws.boffs[cp]);
@@ -530,13 +544,23 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
                 continue;
             }
             if (!__any_sync(FULL, cm)) {
-                if (phase == 1) load_vertex_item(t0 + lane, total, nb);
-                else load_edge_item(t0 + lane, total, nb);
+                if (phase == 1) load_vertex_item(t0, total);
+                else load_edge_item(t0, total);
                 t0 += 32;
                 continue;
             }
-            if (DIM == 3 && phase == 2) edge_step();
-            else vertex_step();
+            // producer steps while the ring they feed has room for 32 more
+            // (3D steps feed the feature ring, 2D vertex steps the term ring)
+            if (DIM == 3 && phase == 2) {
+                do edge_step();
+                while (ft - fh < 32 && __any_sync(FULL, cm));
+            } else if constexpr (DIM == 3) {
+                do vertex_step();
+                while (ft - fh < 32 && __any_sync(FULL, cm));
+            } else {
+                do vertex_step();
+                while (tt - th < 32 && __any_sync(FULL, cm));
+            }
         }
         ph = (ph + nb) & (PR - 1);
         np -= nb;
@@ -568,18 +592,17 @@ __device__ __forceinline__ int scan_particle(const PairArgs &a, ScanSmem<T> &ss,
     return a.nn[i];
 }
 
-// List entry t of the warp's particles base..base+31: the range test and the
-// pair setup (separating-axis test, feature masks).  Returns whether the pair
-// is active; *pl is the owner's lane, *gi its geometry.
+// List entry t of the warp's particles base..base+31 (of the particle in lane
+// pl): the range test and the pair setup (separating-axis test, feature
+// masks).  Returns whether the pair is active; *gi is the owner's geometry.
 template <class T, int DIM, bool COUNT>
 __device__ __forceinline__ bool scan_entry(const PairArgs &a, const typename R4T<T>::type *tab,
                                            const int *itab, const Geom *geo, const ScanSmem<T> &ss,
-                                           int base, int t, T sig_all, PairWork<T> *wk, int *pl,
+                                           int base, int t, int pl, T sig_all, PairWork<T> *wk,
                                            int *gi_out, PathCount *pc) {
-    *pl = owner_of(ss.offs, 32, t);
-    const int k = t - ss.offs[*pl];
-    const int i = base + *pl;
-    const SInfo<T> &pi = ss.info[*pl];
+    const int k = t - ss.offs[pl];
+    const int i = base + pl;
+    const SInfo<T> &pi = ss.info[pl];
     const Geom &gi = geo[pi.geom];
     *gi_out = pi.geom;
     M33<T> Ri;
@@ -680,13 +703,14 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             }
             if (t0 >= total) break;
             const int t = t0 + lane;
+            const int pl = round_owner(ws.s.offs[lane], nn_me, t0, lane, ws.s.who);
             t0 += 32;
             bool active = false;
             PairWork<T> wk;
-            int pl = 0, gi = 0;
+            int gi = 0;
             if (t < total)
-                active = scan_entry<T, DIM, COUNT>(a, tab, itab, geo, ws.s, base, t, sig_all, &wk,
-                                                   &pl, &gi, &st.pc);
+                active = scan_entry<T, DIM, COUNT>(a, tab, itab, geo, ws.s, base, t, pl, sig_all,
+                                                   &wk, &gi, &st.pc);
             const unsigned m = __ballot_sync(FULL, active);
             if (active) store_record(ws.b.pr[ring_slot(m, lane, st.ph + st.np)], wk, pl, gi);
             st.np += __popc(m);
@@ -744,12 +768,13 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
         int cnt = 0;
         for (int t0 = 0; t0 < total; t0 += 32) {
             const int t = t0 + lane;
+            const int pl = round_owner(ws.s.offs[lane], nn_me, t0, lane, ws.s.who);
             bool active = false;
             PairWork<T> wk;
-            int pl = 0, gi = 0;
+            int gi = 0;
             if (t < total)
-                active = scan_entry<T, DIM, COUNT>(a, tab, itab, geo, ws.s, base, t, sig_all, &wk,
-                                                   &pl, &gi, &pc);
+                active = scan_entry<T, DIM, COUNT>(a, tab, itab, geo, ws.s, base, t, pl, sig_all,
+                                                   &wk, &gi, &pc);
             const unsigned m = __ballot_sync(FULL, active);
             if (active) store_record(ws.stage[__popc(m & ((1u << lane) - 1u))], wk, pl, gi);
             __syncwarp();
