@@ -518,11 +518,13 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         int phase = 0, t0 = 0, total = 0;
         cm = 0u;
         for (;;) {
+            // cm changes only in producer turns: one vote serves this turn
+            const bool any_cm = __any_sync(FULL, cm);
             if (tt - th >= 32 || (phase == 3 && tt > th)) {
                 run_terms(tt - th < 32 ? tt - th : 32);
                 continue;
             }
-            const bool produced = t0 >= total && !__any_sync(FULL, cm);
+            const bool produced = t0 >= total && !any_cm;
             if (ft - fh >= 32 || (produced && ft > fh)) {
                 const int n = ft - fh < 32 ? ft - fh : 32;
                 if (DIM == 3 && phase == 2) run_segments(n);
@@ -543,7 +545,7 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
                 t0 = 0;
                 continue;
             }
-            if (!__any_sync(FULL, cm)) {
+            if (!any_cm) {
                 if (phase == 1) load_vertex_item(t0, total);
                 else load_edge_item(t0, total);
                 t0 += 32;
@@ -820,6 +822,16 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
         const int cnt = a.rec_count[g];
         const uint4 *in = reinterpret_cast<const uint4 *>(reinterpret_cast<const SPair<T> *>(a.recs) +
                                                           (size_t)g * 32 * a.cap);
+        // the records of this warp's next group into L2 while this one runs
+        // (its first 32 records: one 128-byte line per lane at most)
+        const int gn = g + nwarps;
+        if (gn * 32 < a.n) {
+            const int cn = min(a.rec_count[gn], 32);
+            const char *nx = reinterpret_cast<const char *>(reinterpret_cast<const SPair<T> *>(a.recs) +
+                                                            (size_t)gn * 32 * a.cap);
+            const int lines = (cn * (int)sizeof(SPair<T>) + 127) / 128;
+            if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
+        }
         st.S.zero();
         for (int b0 = 0; b0 < cnt; b0 += 32) {
             const int nb = cnt - b0 < 32 ? cnt - b0 : 32;
