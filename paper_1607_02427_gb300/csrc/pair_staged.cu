@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
         int cnt = 0;
         for (int t0 = 0; t0 < total; t0 += 32) {
             const int t = t0 + lane;
-            const int pl = round_owner(ws.s.offs[lane], nn_me, t0, lane, ws.s.who);
+            const int pl = t < total ? owner_of(ws.s.offs, 32, t) : 0;
             bool active = false;
             PairWork<T> wk;
             int gi = 0;
