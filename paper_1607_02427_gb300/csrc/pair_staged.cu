@@ -835,12 +835,19 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
         st.S.zero();
         for (int b0 = 0; b0 < cnt; b0 += 32) {
             const int nb = cnt - b0 < 32 ? cnt - b0 : 32;
-            // records b0.. into the ring from slot ph (the ring is empty here)
+            // records b0.. into the ring from slot ph (the ring is empty here):
+            // asynchronous 16-byte global-to-shared copies, all in flight at
+            // once, then one wait
             uint4 *dst = reinterpret_cast<uint4 *>(ws.pr);
             for (int q = lane; q < nb * QW; q += 32) {
                 const int r = q / QW, c = q - r * QW;
-                dst[(size_t)((st.ph + r) & (APPLY_PR - 1)) * QW + c] = in[(size_t)(b0 + r) * QW + c];
+                const unsigned s = (unsigned)__cvta_generic_to_shared(
+                    dst + (size_t)((st.ph + r) & (APPLY_PR - 1)) * QW + c);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s),
+                             "l"(in + (size_t)(b0 + r) * QW + c)
+                             : "memory");
             }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
             __syncwarp();
             st.np = nb;
             st.batch(nb);
