@@ -58,28 +58,27 @@ template <class T> struct SInfo {      // one particle of the warp
     int geom, rep;
     float sc;                          // FP32 list separation scale of the replica
 };
-template <class T> struct VFItem {     // (vertex, face) after the plane test
-    typename R4T<T>::type p;           // the vertex in the face owner's frame; w: its
-                                       // signed plane distance
-    int code;                          // pair | side << 5 | vertex << 6 | face << 11
-};
-template <class T> struct EEItem {     // edge pair after the sphere and line tests
-    typename R4T<T>::type a2;          // j's edge start in i's frame; w: code =
-                                       // pair | edge of i << 5 | edge of j << 10
-    typename R4T<T>::type d2;          // j's edge direction in i's frame
-};
-template <class T> struct TermRec {    // a term with r < r_cut
-    typename R4T<T>::type q;           // the point on i's feature (i's frame); w: r^2
-    typename R4T<T>::type rv;          // i's point minus j's point (i's frame); w: pair
-};
 // Per-warp shared memory of the batch stages and of the list scan.
 template <class T, int PR> struct BatchSmem {   // PR: pair ring entries (a power of 2)
     SPair<T> pr[PR];
+    // The rings hold their records' fields in separate arrays, so that the
+    // lanes' 16-byte accesses to consecutive slots are contiguous.
     union {
-        VFItem<T> vf[RING];
-        EEItem<T> ee[RING];
+        struct {                          // (vertex, face) after the plane test
+            typename R4T<T>::type p[RING];   // the vertex in the face owner's frame;
+                                             // w: its signed plane distance
+            int code[RING];                  // pair | side << 5 | vertex << 6 | face << 11
+        } vf;
+        struct {                          // edge pair after the sphere and line tests
+            typename R4T<T>::type a2[RING];  // j's edge start in i's frame; w: code =
+                                             // pair | edge of i << 5 | edge of j << 10
+            typename R4T<T>::type d2[RING];  // j's edge direction in i's frame
+        } ee;
     } fq;
-    TermRec<T> tq[RING];
+    struct {                              // terms with r < r_cut
+        typename R4T<T>::type q[RING];       // the point on i's feature (i's frame); w: r^2
+        typename R4T<T>::type rv[RING];      // i's point minus j's point (i's frame); w: pair
+    } tq;
     int boffs[32];                     // item offsets of the batch's pairs
     int who[32];                       // pair whose items start at lane k of a round
     unsigned gmask[32];                // per owner: lanes holding its terms
@@ -185,9 +184,9 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
     __device__ __forceinline__ void push_term(bool ok, V3<T> q, V3<T> rv, T r2, int p) {
         const unsigned m = __ballot_sync(FULL, ok);
         if (ok) {
-            TermRec<T> &t = ws.tq[ring_slot(m, lane, tt)];
-            t.q = {q.x, q.y, q.z, r2};
-            t.rv = {rv.x, rv.y, rv.z, (T)p};
+            const int s = ring_slot(m, lane, tt);
+            ws.tq.q[s] = {q.x, q.y, q.z, r2};
+            ws.tq.rv[s] = {rv.x, rv.y, rv.z, (T)p};
         }
         tt += __popc(m);
         __syncwarp();
@@ -195,9 +194,9 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
     __device__ __forceinline__ void push_face(bool ok, V3<T> pv, T h, int code) {
         const unsigned m = __ballot_sync(FULL, ok);
         if (ok) {
-            VFItem<T> &it = ws.fq.vf[ring_slot(m, lane, ft)];
-            it.p = {pv.x, pv.y, pv.z, h};
-            it.code = code;
+            const int s = ring_slot(m, lane, ft);
+            ws.fq.vf.p[s] = {pv.x, pv.y, pv.z, h};
+            ws.fq.vf.code[s] = code;
         }
         ft += __popc(m);
         __syncwarp();
@@ -205,9 +204,9 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
     __device__ __forceinline__ void push_edge(bool ok, V3<T> A2, V3<T> D2, int code) {
         const unsigned m = __ballot_sync(FULL, ok);
         if (ok) {
-            EEItem<T> &it = ws.fq.ee[ring_slot(m, lane, ft)];
-            it.a2 = {A2.x, A2.y, A2.z, (T)code};
-            it.d2 = {D2.x, D2.y, D2.z, T(0)};
+            const int s = ring_slot(m, lane, ft);
+            ws.fq.ee.a2[s] = {A2.x, A2.y, A2.z, (T)code};
+            ws.fq.ee.d2[s] = {D2.x, D2.y, D2.z, T(0)};
         }
         ft += __popc(m);
         __syncwarp();
@@ -221,8 +220,8 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         const bool has = lane < n;
         int owner = 32 + lane;                    // lanes without a term: distinct keys
         if (has) {
-            const TermRec<T> &t = ws.tq[(th + lane) & (RING - 1)];
-            const auto tq = t.q, trv = t.rv;
+            const int s = (th + lane) & (RING - 1);
+            const auto tq = ws.tq.q[s], trv = ws.tq.rv[s];
             const SPair<T> &P = pair((int)trv.w);
             owner = P.owner;
             T U;
@@ -258,9 +257,9 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         T r2 = T(0);
         int p = 0;
         if (lane < n) {
-            const VFItem<T> &it = ws.fq.vf[(fh + lane) & (RING - 1)];
-            const auto ip = it.p;
-            const int code = it.code;
+            const int s = (fh + lane) & (RING - 1);
+            const auto ip = ws.fq.vf.p[s];
+            const int code = ws.fq.vf.code[s];
             p = code & 31;
             const int side = (code >> 5) & 1, vtx = (code >> 6) & 31, f = (code >> 11) & 31;
             const SPair<T> &P = pair(p);
@@ -297,8 +296,8 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         T r2 = T(0);
         int p = 0;
         if (lane < n) {
-            const EEItem<T> &it = ws.fq.ee[(fh + lane) & (RING - 1)];
-            const auto a2 = it.a2, d2 = it.d2;
+            const int s = (fh + lane) & (RING - 1);
+            const auto a2 = ws.fq.ee.a2[s], d2 = ws.fq.ee.d2[s];
             const int code = (int)a2.w;
             p = code & 31;
             const int ea = (code >> 5) & 31, eb = (code >> 10) & 31;
