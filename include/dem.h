@@ -247,7 +247,7 @@ int dem_get_virial(dem_ctx *ctx, double *per_replica_W6);
 int dem_set_box(dem_ctx *ctx, const double *box);
 
 /* Named numeric parameters:
- *   "skin"        neighbour-list skin (default: the largest sigma_ij)
+ *   "skin"        neighbour-list skin (default: the largest sigma_ij, at most 0.4)
  *   "par_eps"     squared-sine threshold of the parallel-edge rule (1e-6)
  *   "decomp"      DEM_DECOMP_* of the pair kernel
  *   "block"       threads per block of the pair kernel (0 = default)

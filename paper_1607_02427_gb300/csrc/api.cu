@@ -573,10 +573,17 @@ double max_sigma(const dem_ctx *ctx) {
     return m;
 }
 
+// Default neighbour-list skin: the largest sigma_ij, at most 0.4 (lengths in
+// the units of the shapes).  A skin of a whole sigma for unit spheres lists
+// seven times the interaction volume; 0.4 keeps rebuilds tens of steps apart
+// at kT = 1, dt = 1e-3.
+constexpr double SKIN_CAP = 0.4;
+double default_skin(const dem_ctx *ctx) { return std::min(max_sigma(ctx), SKIN_CAP); }
+
 // Cell grids, list cutoffs and degrees of freedom of every replica (needs the
 // shape of each particle).  Reallocates cell arrays and the list.
 int setup_replicas(dem_ctx *ctx) {
-    if (ctx->skin < 0) ctx->skin = max_sigma(ctx);
+    if (ctx->skin < 0) ctx->skin = default_skin(ctx);
     std::vector<Rep> reps(ctx->R);
     int cell_off = 0;
     double worst_ratio = 0;   // expected neighbours estimate
@@ -1153,7 +1160,7 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
 int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
     if (!valid(ctx) || !name || !value) return DEM_ERR_ARG;
     std::string n(name);
-    if (n == "skin") *value = ctx->skin < 0 ? max_sigma(ctx) : ctx->skin;
+    if (n == "skin") *value = ctx->skin < 0 ? default_skin(ctx) : ctx->skin;
     else if (n == "par_eps") *value = ctx->par_eps;
     else if (n == "npt_chunk") *value = ctx->npt_chunk;
     else if (n == "decomp") *value = ctx->decomp;
