@@ -86,7 +86,6 @@ def nest_guests(s, hosts, guest, local_points, seed, gap_min=0.8):
     gid = len(shapes) - 1
     pos, orient = [s.pos.copy()], [s.orient.copy()]
     ids = [s.shape_id.copy()]
-    rnd = np.array([shapes[k]["rounding"] for k in s.shape_id])
     added = []
     for h in hosts:
         lp = np.asarray(local_points[int(rng.integers(len(local_points)))], float)
@@ -111,8 +110,11 @@ def nest_guests(s, hosts, guest, local_points, seed, gap_min=0.8):
             e = d / dist
             sh_k = shapes[int(cand_ids[k])]
             sig = sh_k["rounding"] + guest["rounding"] if s.sigma <= 0 else s.sigma
-            o_k = s.orient[k] if k < s.n else (np.array([1.0, 0, 0, 0]) if dim == 3 else np.array([0.0]))
-            g = dist - W._support(sh_k, o_k, e)
+            if k < s.n:
+                g = dist - W._support(sh_k, s.orient[k], e)
+            else:
+                g = dist                     # an earlier guest: a point
+
             if g < gap_min * sig:
                 ok = False
                 break
