@@ -703,8 +703,9 @@ PairArgs pair_args(dem_ctx *ctx) {
 // first).
 int ensure_recs(dem_ctx *ctx, int decomp) {
     if (decomp != DEM_DECOMP_SPLIT) return DEM_OK;
-    const size_t groups = ((size_t)ctx->N + 31) / 32;
-    const size_t need = groups * 32 * (size_t)ctx->cap * pair_record_bytes(ctx->precision);
+    const size_t G = (size_t)split_group(ctx->N);
+    const size_t groups = ((size_t)ctx->N + G - 1) / G;
+    const size_t need = groups * G * (size_t)ctx->cap * pair_record_bytes(ctx->precision);
     if (need > ctx->rec_bytes || !ctx->recs) {
         if (ctx->recs) cudaFree(ctx->recs);
         ctx->recs = nullptr;

@@ -137,14 +137,18 @@ struct PairArgs {
     double eps, sigma, par_eps;
     Status *status;
     unsigned long long *counters;  // counting launches only
-    // SPLIT decomposition: active-pair records of each group of 32 particles
-    // (group g at recs + g * 32 * cap records) and their counts
+    // SPLIT decomposition: active-pair records of each group of `group`
+    // particles (32, 16, 8 or 4; group g at recs + g * group * cap records)
+    // and their counts
     void *recs;
     int *rec_count;
+    int group;
 };
 
 // Bytes of one active-pair record of the SPLIT decomposition.
 size_t pair_record_bytes(int precision);
+// Particles per warp group of the SPLIT kernels for n particles.
+int split_group(int n);
 
 struct NlistArgs {
     int n, dim, cap, cell_cap;

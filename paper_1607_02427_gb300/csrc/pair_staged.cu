@@ -758,14 +758,15 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
         for (int k = 0; k < NCOUNT; ++k) pc.v[k] = 0;
     constexpr int QW = sizeof(SPair<T>) / sizeof(uint4);
     const int nwarps = gridDim.x * wpb;
-    for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
-        const int g = base / 32;
-        const int nn_me = scan_particle<T>(a, ws.s, lane, base + lane);
+    const int G = a.group;   // particles per warp (lanes G..31 hold none)
+    for (int base = (blockIdx.x * wpb + w) * G; base < a.n; base += nwarps * G) {
+        const int g = base / G;
+        const int nn_me = scan_particle<T>(a, ws.s, lane, lane < G ? base + lane : a.n);
         int total;
         ws.s.offs[lane] = warp_excl_scan(nn_me, lane, &total);
         __syncwarp();
         uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<SPair<T> *>(a.recs) +
-                                               (size_t)g * 32 * a.cap);
+                                               (size_t)g * G * a.cap);
         int cnt = 0;
         for (int t0 = 0; t0 < total; t0 += 32) {
             const int t = t0 + lane;
@@ -816,18 +817,19 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
     Staged<T, COMP, DIM, COUNT, APPLY_PR> st(a, tab, geo, itab, ws, lane);
     constexpr int QW = sizeof(SPair<T>) / sizeof(uint4);
     const int nwarps = gridDim.x * wpb;
-    for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
-        const int g = base / 32;
+    const int G = a.group;   // particles per warp (lanes G..31 own none)
+    for (int base = (blockIdx.x * wpb + w) * G; base < a.n; base += nwarps * G) {
+        const int g = base / G;
         const int cnt = a.rec_count[g];
         const uint4 *in = reinterpret_cast<const uint4 *>(reinterpret_cast<const SPair<T> *>(a.recs) +
-                                                          (size_t)g * 32 * a.cap);
+                                                          (size_t)g * G * a.cap);
         // the records of this warp's next group into L2 while this one runs
         // (its first 32 records: one 128-byte line per lane at most)
         const int gn = g + nwarps;
-        if (gn * 32 < a.n) {
+        if ((long long)gn * G < a.n) {
             const int cn = min(a.rec_count[gn], 32);
             const char *nx = reinterpret_cast<const char *>(reinterpret_cast<const SPair<T> *>(a.recs) +
-                                                            (size_t)gn * 32 * a.cap);
+                                                            (size_t)gn * G * a.cap);
             const int lines = (cn * (int)sizeof(SPair<T>) + 127) / 128;
             if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
         }
@@ -852,7 +854,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
             st.batch(nb);
         }
         const int i_me = base + lane;
-        if (i_me < a.n) finish_particle(a, i_me, st.S, orientation<T>(a, i_me));
+        if (lane < G && i_me < a.n) finish_particle(a, i_me, st.S, orientation<T>(a, i_me));
         __syncwarp();
     }
     if constexpr (COUNT)
@@ -888,7 +890,8 @@ cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, 
     const size_t t = (smem_tables + 127) & ~(size_t)127;
     const size_t smem1 = t + (SBLOCK / 32) * sizeof(ScanBlockSmem<T>);
     const size_t smem2 = t + (SBLOCK / 32) * sizeof(BatchSmem<T, APPLY_PR>);
-    const long long need = (a.n + SBLOCK - 1) / SBLOCK;   // 32 particles per warp
+    const int warps = (a.n + a.group - 1) / a.group;      // a.group particles per warp
+    const long long need = (warps + SBLOCK / 32 - 1) / (SBLOCK / 32);
     auto launch = [&](auto kernel, size_t smem) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -928,8 +931,20 @@ size_t pair_record_bytes(int precision) {
     return precision == DEM_FP64 ? sizeof(SPair<double>) : sizeof(SPair<float>);
 }
 
-cudaError_t launch_pair_split(const PairArgs &a, int precision, bool count, size_t smem_tables,
+// Particles per warp of the SPLIT kernels: 32, or fewer (16, 8, 4) while
+// that leaves less than one wave of the feature kernel (five blocks of four
+// warps on every SM), so that a small system spreads over the whole GPU.
+int split_group(int n) {
+    const int wave = 5 * (SBLOCK / 32) * sm_count();
+    int G = 32;
+    while (G > 4 && (n + G - 1) / G < wave) G >>= 1;
+    return G;
+}
+
+cudaError_t launch_pair_split(const PairArgs &a0, int precision, bool count, size_t smem_tables,
                               cudaStream_t s) {
+    PairArgs a = a0;
+    a.group = split_group(a.n);
     switch (precision) {
         case DEM_FP64: return launch_split_prec<double, false>(a, count, smem_tables, s);
         case DEM_FP32: return launch_split_prec<float, false>(a, count, smem_tables, s);
