@@ -436,6 +436,7 @@ struct dem_ctx {
     std::vector<HostGeom> geoms;
     std::vector<HostShape> shapes;
     std::vector<int> sizes, offs;
+    int max_rep = 0;                  // largest replica
     std::vector<double> box;   // R * 3
     std::vector<Rep> reps;
     std::vector<int> shape_host;
@@ -750,6 +751,9 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     a.rotor32 = ctx->precision != DEM_FP64;
     a.ket = ctx->ket; a.virial = ctx->virial; a.reps_rw = ctx->d_reps;
     a.n_chunks = ctx->n_chunks; a.chunk_rep = ctx->chunk_rep; a.partial = ctx->partial;
+    // every replica within one reduction chunk: the thermostat kernel sums the
+    // kinetic energies itself (the NPT kernels take the chunk partials)
+    a.direct_sums = !a.npt && ctx->max_rep <= SUM_CHUNK;
     return a;
 }
 
@@ -763,7 +767,7 @@ int launch_forces(dem_ctx *ctx, bool count, cudaEvent_t e0 = nullptr, cudaEvent_
     if (e0) CK(cudaEventRecordWithFlags(e0, ctx->stream, cudaEventRecordExternal));
     CK(launch_pair(pair_args(ctx), ctx->precision, ctx->decomp, ctx->block, count, ctx->stream));
     if (e1) CK(cudaEventRecordWithFlags(e1, ctx->stream, cudaEventRecordExternal));
-    ctx->launches += 3;
+    ctx->launches += 2 + (ctx->decomp == DEM_DECOMP_SPLIT ? 2 : 1);
     return DEM_OK;
 }
 
@@ -777,13 +781,16 @@ int launch_step(dem_ctx *ctx, double dt, int ens, double kT, double tau,
     CK(launch_first_half(sa, ctx->stream));
     int rc = launch_forces(ctx, false, e0, e1);
     if (rc) return rc;
-    ctx->launches += ens != DEM_NVE ? 4 : 2;
     CK(launch_second_half(sa, ctx->stream));
+    ctx->launches += 2;
     if (ens != DEM_NVE) {
-        CK(launch_chunk_sums(sa, ctx->stream));
+        if (!sa.direct_sums) {
+            CK(launch_chunk_sums(sa, ctx->stream));
+            ctx->launches += 1;
+        }
         CK(launch_thermo_end(sa, ctx->stream));
         CK(launch_scale(sa, ctx->stream));
-        ctx->launches += 1;
+        ctx->launches += 2;
     }
     return DEM_OK;
 }
@@ -1045,6 +1052,7 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
         }
         ctx->offs.push_back(N);
         ctx->sizes.push_back(replica_sizes[r]);
+        ctx->max_rep = std::max(ctx->max_rep, replica_sizes[r]);
         N += replica_sizes[r];
         for (int a = 0; a < 3; ++a) {
             double L = a < ctx->dim ? box[ctx->dim * r + a] : 1.0;
@@ -1255,7 +1263,7 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
     if (rc) return rc;
     StepArgs sa = step_args(ctx, 0.0, DEM_NVE, 1.0, 1.0);
     CK(launch_kinetic(sa, ctx->stream));
-    CK(launch_chunk_sums(sa, ctx->stream));
+    if (!sa.direct_sums) CK(launch_chunk_sums(sa, ctx->stream));
     CK(launch_thermo_end(sa, ctx->stream));   // NVE branch: stores K per replica
     CK(cudaStreamSynchronize(ctx->stream));
     return DEM_OK;

@@ -328,7 +328,9 @@ __global__ void k_chunk_sums(const StepArgs a) {
 __global__ void k_thermo_end(const StepArgs a) {
     const int r = blockIdx.x;
     const Rep &rp = a.reps[r];
-    double K = block_sum(a.partial, rp.chunk_off, rp.n_chunk, 3, 0);
+    // one chunk per replica: its sum directly (the same value as its partial)
+    double K = a.direct_sums ? block_sum(a.ke, rp.off, rp.n, 1, 0)
+                             : block_sum(a.partial, rp.chunk_off, rp.n_chunk, 3, 0);
     if (threadIdx.x == 0) {
         Thermo &t = a.thermo[r];
         const double g = (double)rp.g_dof, d = 0.5 * a.dt;
@@ -636,22 +638,43 @@ inline int grid_for(int n, int block) {
     return g > 0 ? g : 1;
 }
 
+// Threads per block of the per-particle step kernels: 256, or fewer (down to
+// one warp) while blocks of 256 would leave SMs idle.  FP64 runs at a few
+// flops per clock per SM on this part, so a small system's integrator work
+// is spread over as many SMs as it can fill.
+int particle_block(int n) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    int b = 256;
+    while (b > 32 && (n + b - 1) / b < sms) b >>= 1;
+    return b;
+}
+
 }  // namespace
 
 cudaError_t launch_first_half(const StepArgs &a, cudaStream_t s) {
-    k_first_half<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    const int b = particle_block(a.n);
+    k_first_half<<<grid_for(a.n, b), b, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_displacement(const StepArgs &a, cudaStream_t s) {
-    k_displacement<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    const int b = particle_block(a.n);
+    k_displacement<<<grid_for(a.n, b), b, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_second_half(const StepArgs &a, cudaStream_t s) {
-    k_second_half<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    const int b = particle_block(a.n);
+    k_second_half<<<grid_for(a.n, b), b, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_kinetic(const StepArgs &a, cudaStream_t s) {
-    k_kinetic<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    const int b = particle_block(a.n);
+    k_kinetic<<<grid_for(a.n, b), b, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_thermo_end(const StepArgs &a, cudaStream_t s) {
@@ -675,7 +698,8 @@ cudaError_t launch_thermo_begin(const StepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_scale(const StepArgs &a, cudaStream_t s) {
-    k_scale<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    const int b = particle_block(a.n);
+    k_scale<<<grid_for(a.n, b), b, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_replica_sums(int n_reps, const Rep *reps, const double *per_particle,
