@@ -41,6 +41,7 @@ UNIT = "particle-steps/s"
 # GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock.
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 rate (far below the FP32 rate)
 
 # FP32 flops of each counted code path of the pair kernel (FMA = 2, add /
 # mul / reciprocal = 1, compare = 0), hand-counted from csrc/pair.cu and
@@ -473,6 +474,20 @@ def measure_extras(a, dem, d, system, run, ens, prec, torch):
             out[name] = {"value": n * k / (time.perf_counter() - t0), "unit": UNIT, "steps": k,
                          "decomposition": {1: "thread", 2: "warp", 3: "staged", 4: "split"}[
                              int(d2.get_param("decomp"))]}
+            if p == dem.DEM_FP64:
+                # the FP64 pair kernels against the FP64 rate (a few profiled steps)
+                d2.set_param("profile", 1)
+                d2.step(1, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+                d2.set_param("profile", 1)
+                d2.step(5, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
+                pms = d2.get_param("pair_ms_total") / max(1.0, d2.get_param("pair_launches"))
+                d2.set_param("profile", 0)
+                fl = algorithmic_flops(d2.counters(), False)
+                ach = fl / (pms / 1e3) / 1e12
+                out[name]["roofline"] = {
+                    "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "kernel_ms": pms,
+                    "peak_note": "nominal FP64 rate of GB300 (no measured FP64 peak)"}
     # plain FP64 single-system path: one context per replica, launch by launch
     if system.n_replicas > 1:
         sample = list(range(0, system.n_replicas, max(1, system.n_replicas // 24)))[:24]
