@@ -248,6 +248,9 @@ int dem_set_box(dem_ctx *ctx, const double *box);
 
 /* Named numeric parameters:
  *   "skin"        neighbour-list skin (default: the largest sigma_ij, at most 0.4)
+ *   "split_group" SPLIT decomposition: particles per warp, 4, 8, 16 or 32; 0
+ *                 (default) takes 32, or fewer while N leaves the GPU
+ *                 underfilled; get_param returns the size in use
  *   "par_eps"     squared-sine threshold of the parallel-edge rule (1e-6)
  *   "decomp"      DEM_DECOMP_* of the pair kernel
  *   "block"       threads per block of the pair kernel (0 = default)

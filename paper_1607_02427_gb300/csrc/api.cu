@@ -458,6 +458,7 @@ struct dem_ctx {
     // barostat (dem_set_barostat) and the steps per NPT chunk
     double P = 0.0, tau_P = 0.0;
     int npt_chunk = 100;
+    int split_G = 0;                  // SPLIT particles per warp (0: from N)
     // device memory
     double4_32a *pos = nullptr, *vel = nullptr, *quat = nullptr, *angmom = nullptr;
     double4_32a *force = nullptr, *torque = nullptr, *x_last = nullptr;
@@ -681,6 +682,11 @@ int setup_replicas(dem_ctx *ctx) {
     return DEM_OK;
 }
 
+// Particles per warp group of the SPLIT kernels: the one set, else from N.
+int ctx_split_group(const dem_ctx *ctx) {
+    return ctx->split_G > 0 ? ctx->split_G : split_group(ctx->N);
+}
+
 PairArgs pair_args(dem_ctx *ctx) {
     PairArgs a = {};
     a.n = ctx->N; a.dim = ctx->dim; a.cap = ctx->cap;
@@ -696,6 +702,7 @@ PairArgs pair_args(dem_ctx *ctx) {
     a.counters = ctx->d_counters;
     a.recs = ctx->recs;
     a.rec_count = ctx->rec_count;
+    a.group = ctx_split_group(ctx);
     return a;
 }
 
@@ -704,7 +711,7 @@ PairArgs pair_args(dem_ctx *ctx) {
 // first).
 int ensure_recs(dem_ctx *ctx, int decomp) {
     if (decomp != DEM_DECOMP_SPLIT) return DEM_OK;
-    const size_t G = (size_t)split_group(ctx->N);
+    const size_t G = (size_t)ctx_split_group(ctx);
     const size_t groups = ((size_t)ctx->N + G - 1) / G;
     const size_t need = groups * G * (size_t)ctx->cap * pair_record_bytes(ctx->precision);
     if (need > ctx->rec_bytes || !ctx->recs) {
@@ -718,7 +725,8 @@ int ensure_recs(dem_ctx *ctx, int decomp) {
         ctx->rec_bytes = need;
         free_graph(ctx);
     }
-    if (!ctx->rec_count) CK(dalloc(&ctx->rec_count, groups));
+    // counts for the smallest group size, so that any group size fits
+    if (!ctx->rec_count) CK(dalloc(&ctx->rec_count, ((size_t)ctx->N + 3) / 4));
     return DEM_OK;
 }
 
@@ -1130,6 +1138,11 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
     } else if (n == "npt_chunk") {
         if (!(value >= 1) || value > 1e9) return set_err(ctx, DEM_ERR_ARG, "npt_chunk must be >= 1");
         ctx->npt_chunk = (int)value;
+    } else if (n == "split_group") {
+        const int G = (int)value;
+        if (value != (double)G || (G != 0 && G != 4 && G != 8 && G != 16 && G != 32))
+            return set_err(ctx, DEM_ERR_ARG, "split_group must be 0, 4, 8, 16 or 32");
+        ctx->split_G = G;
     } else if (n == "par_eps") {
         if (!(value >= 0)) return set_err(ctx, DEM_ERR_ARG, "par_eps must be >= 0");
         ctx->par_eps = value;
@@ -1172,6 +1185,7 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
     if (n == "skin") *value = ctx->skin < 0 ? default_skin(ctx) : ctx->skin;
     else if (n == "par_eps") *value = ctx->par_eps;
     else if (n == "npt_chunk") *value = ctx->npt_chunk;
+    else if (n == "split_group") *value = ctx_split_group(ctx);
     else if (n == "decomp") *value = ctx->decomp;
     else if (n == "block") *value = ctx->block;
     else if (n == "graph") *value = ctx->use_graph;

@@ -944,7 +944,7 @@ int split_group(int n) {
 cudaError_t launch_pair_split(const PairArgs &a0, int precision, bool count, size_t smem_tables,
                               cudaStream_t s) {
     PairArgs a = a0;
-    a.group = split_group(a.n);
+    if (a.group != 4 && a.group != 8 && a.group != 16 && a.group != 32) a.group = split_group(a.n);
     switch (precision) {
         case DEM_FP64: return launch_split_prec<double, false>(a, count, smem_tables, s);
         case DEM_FP32: return launch_split_prec<float, false>(a, count, smem_tables, s);

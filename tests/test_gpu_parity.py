@@ -253,3 +253,24 @@ def test_set_state_keeps_valid_list(dem, precision):
                      s2.replica_sizes, s2.epsilon, s2.sigma)
         dem.dem_set_state(d.ctx, t.shape_id, t.pos, t.orient, t.vel, t.angmom)
         assert_parity(_ctx_errors(d, t), precision, "set_state new shapes")
+
+
+@pytest.mark.parametrize("group", [4, 8, 16, 32])
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp32c"])
+@pytest.mark.parametrize("name", ["mixed3d", "polys2d", "dented"])
+def test_split_group_sizes(dem, name, precision, group):
+    """SPLIT with each number of particles per warp: parity with the oracle
+    and the same work as the THREAD decomposition."""
+    s = system(name)
+    errs, ref, out = compare_forces(dem, s, precision, decomp=4, split_group=group)
+    assert_parity(errs, precision, f"{name}/split group {group}")
+    with dem.DEM(s, dem.DEM_FP64, decomp=4, split_group=group) as d:
+        assert d.get_param("split_group") == group
+        c_split = d.counters()
+        for bad in (1, 2, 12, 64, 8.5, -4):
+            with pytest.raises(dem.DemError):
+                d.set_param("split_group", bad)
+    with dem.DEM(s, dem.DEM_FP64, decomp=1) as d:
+        c_thread = d.counters()
+    keep = [k for k in range(18) if k not in (3, 13, 14)]
+    np.testing.assert_array_equal(c_split[keep], c_thread[keep])
