@@ -345,8 +345,11 @@ def main():
     decomp_name = {1: "thread", 2: "warp", 3: "staged", 4: "split"}[int(d.get_param("decomp"))]
     tune = {}
     if a.decomp == "auto":
-        for k, nm in enumerate(["thread64", "thread128", "warp128", "staged128", "split128"]):
+        for k, nm in enumerate(["thread64", "thread128", "warp128", "staged128", "split_g32",
+                                "split_g16", "split_g8", "split_g4"]):
             tune[nm] = d.get_param(f"autotune_ms_{k}")
+    if decomp_name == "split":
+        decomp_name = f"split, {int(d.get_param('split_group'))} particles per warp"
 
     # warm-up
     d.step(a.warmup, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])

@@ -272,10 +272,12 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value);
 /* Run every pair-kernel decomposition and block size on the current state
  * and keep the fastest (timed with CUDA events on the context's stream).
  * Candidates, in order: THREAD with 64 and 128 threads per block, WARP,
- * STAGED, SPLIT (-1 when its records do not fit in device memory);
- * their mean times are readable as parameters "autotune_ms_0", ... .
- * Results are identical for every choice up to floating-point summation
- * order; the chosen one is the "decomp" and "block" parameters. */
+ * STAGED, and SPLIT with 32, 16, 8 and 4 particles per warp (-1 when its
+ * records do not fit in device memory, or for the group sizes other than
+ * one fixed with "split_group"); their mean times are readable as
+ * parameters "autotune_ms_0" ... "autotune_ms_7".  Results are identical for
+ * every choice up to floating-point summation order; the chosen one is the
+ * "decomp", "block" and "split_group" parameters. */
 int dem_autotune(dem_ctx *ctx);
 
 /* Work counters of one force evaluation at the current state (host array of

@@ -459,6 +459,7 @@ struct dem_ctx {
     double P = 0.0, tau_P = 0.0;
     int npt_chunk = 100;
     int split_G = 0;                  // SPLIT particles per warp (0: from N)
+    bool split_user = false;          // split_G set by the caller (the autotuner keeps it)
     // device memory
     double4_32a *pos = nullptr, *vel = nullptr, *quat = nullptr, *angmom = nullptr;
     double4_32a *force = nullptr, *torque = nullptr, *x_last = nullptr;
@@ -1143,6 +1144,7 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
         if (value != (double)G || (G != 0 && G != 4 && G != 8 && G != 16 && G != 32))
             return set_err(ctx, DEM_ERR_ARG, "split_group must be 0, 4, 8, 16 or 32");
         ctx->split_G = G;
+        ctx->split_user = G != 0;
     } else if (n == "par_eps") {
         if (!(value >= 0)) return set_err(ctx, DEM_ERR_ARG, "par_eps must be >= 0");
         ctx->par_eps = value;
@@ -1608,21 +1610,33 @@ int dem_autotune(dem_ctx *ctx) {
     if (!ctx->have_state) return set_err(ctx, DEM_ERR_STATE, "no state set");
     int rc = compute_forces(ctx);   // the list is current before timing
     if (rc) return rc;
-    struct Cand { int decomp, block; };
-    const Cand cands[] = {{DEM_DECOMP_THREAD, 64}, {DEM_DECOMP_THREAD, 128},
-                          {DEM_DECOMP_WARP, 128}, {DEM_DECOMP_STAGED, 128},
-                          {DEM_DECOMP_SPLIT, 128}};
+    // SPLIT at each number of particles per warp, unless the caller fixed it
+    struct Cand { int decomp, block, group; };
+    const Cand cands[] = {{DEM_DECOMP_THREAD, 64, 0}, {DEM_DECOMP_THREAD, 128, 0},
+                          {DEM_DECOMP_WARP, 128, 0},  {DEM_DECOMP_STAGED, 128, 0},
+                          {DEM_DECOMP_SPLIT, 128, 32}, {DEM_DECOMP_SPLIT, 128, 16},
+                          {DEM_DECOMP_SPLIT, 128, 8},  {DEM_DECOMP_SPLIT, 128, 4}};
+    const int G_keep = ctx->split_G;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 3.0e38f;
     Cand pick = cands[0];
+    int n_timed = 0;
     ctx->tune_ms.clear();
     for (const Cand &c : cands) {
+        if (c.group) {
+            if (ctx->split_user && c.group != G_keep) {   // the caller's group only
+                ctx->tune_ms.push_back(-1.f);
+                continue;
+            }
+            ctx->split_G = c.group;
+        }
         if (ensure_recs(ctx, c.decomp) != DEM_OK) {   // no room for SPLIT's records
             ctx->tune_ms.push_back(-1.f);
             continue;
         }
+        ++n_timed;
         PairArgs pa = pair_args(ctx);
         CK(launch_pair(pa, ctx->precision, c.decomp, c.block, false, ctx->stream));   // warm-up
         CK(cudaEventRecord(e0, ctx->stream));
@@ -1639,9 +1653,10 @@ int dem_autotune(dem_ctx *ctx) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->launches += 4 * (long long)(sizeof(cands) / sizeof(cands[0]));
+    ctx->launches += 4 * (long long)n_timed;   // launch calls (SPLIT: two kernels each)
     ctx->decomp = pick.decomp;
     ctx->block = pick.block;
+    ctx->split_G = pick.group ? pick.group : G_keep;
     free_graph(ctx);
     // the last timed launch left the forces of the current state in place
     return compute_forces(ctx);
