@@ -1622,7 +1622,7 @@ int dem_autotune(dem_ctx *ctx) {
     CK(cudaEventCreate(&e1));
     float best = 3.0e38f;
     Cand pick = cands[0];
-    int n_timed = 0;
+    long long kernels = 0;
     ctx->tune_ms.clear();
     for (const Cand &c : cands) {
         if (c.group) {
@@ -1636,7 +1636,7 @@ int dem_autotune(dem_ctx *ctx) {
             ctx->tune_ms.push_back(-1.f);
             continue;
         }
-        ++n_timed;
+        kernels += 4 * (c.decomp == DEM_DECOMP_SPLIT ? 2 : 1);   // warm-up + 3 timed
         PairArgs pa = pair_args(ctx);
         CK(launch_pair(pa, ctx->precision, c.decomp, c.block, false, ctx->stream));   // warm-up
         CK(cudaEventRecord(e0, ctx->stream));
@@ -1653,7 +1653,7 @@ int dem_autotune(dem_ctx *ctx) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->launches += 4 * (long long)n_timed;   // launch calls (SPLIT: two kernels each)
+    ctx->launches += kernels;
     ctx->decomp = pick.decomp;
     ctx->block = pick.block;
     ctx->split_G = pick.group ? pick.group : G_keep;
