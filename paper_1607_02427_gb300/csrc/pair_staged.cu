@@ -2,11 +2,12 @@
 // Eq. DEM_2D; Section "Algorithm" of arXiv:1607.02427 re-designed for
 // sm_103a).
 //
-// One warp owns 32 particles at a time and streams their feature-pair work
-// through per-warp shared-memory rings, so that every stage runs with full
-// warps on uniform work instead of one lane walking all features of a pair:
+// One warp owns a group of particles at a time (32 in the fused kernel; 32,
+// 16, 8 or 4 in SPLIT) and streams their feature-pair work through per-warp
+// shared-memory rings, so that every stage runs with full warps on uniform
+// work instead of one lane walking all features of a pair:
 //
-//   scan     lanes take the 32 particles' list entries: range test, pair
+//   scan     lanes take the group's list entries: range test, pair
 //            setup (M, dl, separating-axis test, feature masks); the pairs
 //            that pass are appended to the pair ring in ballot order.
 //   batch    32 queued pairs at a time:
@@ -85,7 +86,7 @@ template <class T, int PR> struct BatchSmem {   // PR: pair ring entries (a powe
 };
 template <class T> struct ScanSmem {
     SInfo<T> info[32];
-    int offs[32];                      // list offsets of the 32 particles
+    int offs[32];                      // list offsets of the group's particles
     int who[32];                       // particle whose entries start at lane k of a round
 };
 template <class T> struct StagedSmem {
@@ -593,8 +594,8 @@ __device__ __forceinline__ int scan_particle(const PairArgs &a, ScanSmem<T> &ss,
     return a.nn[i];
 }
 
-// List entry t of the warp's particles base..base+31 (of the particle in lane
-// pl): the range test and the pair setup (separating-axis test, feature
+// List entry t of the warp's particles base, base+1, ... (of the particle in
+// lane pl): the range test and the pair setup (separating-axis test, feature
 // masks).  Returns whether the pair is active; *gi is the owner's geometry.
 template <class T, int DIM, bool COUNT>
 __device__ __forceinline__ bool scan_entry(const PairArgs &a, const typename R4T<T>::type *tab,
@@ -730,8 +731,8 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             if (st.pc.v[k]) atomicAdd(a.counters + k, (unsigned long long)st.pc.v[k]);
 }
 
-// ---- SPLIT: a scan kernel writes the active pairs of each group of 32
-// particles to HBM (group g at recs + g 32 cap, in the order STAGED queues
+// ---- SPLIT: a scan kernel writes the active pairs of each group of G
+// particles to HBM (group g at recs + g G cap, in the order STAGED queues
 // them), a feature kernel evaluates them.  The scan is bound by the latency
 // of the neighbour gathers and runs with a small footprint at a higher
 // occupancy; the feature kernel keeps the batch stages. ----
