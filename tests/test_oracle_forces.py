@@ -155,6 +155,34 @@ def test_face_to_face_cubes_count(oracle_mod, gap):
                                                  rel=1e-12)
 
 
+def test_overcount_isosurface_shift(oracle_mod):
+    """Section "Model", worked example: the 1 kT isosurface of the face-to-
+    face cube interaction lies farther out than a single term's by about 10%
+    of sigma (tests/golden/overcount.txt).  The oracle's energy of two
+    aligned cubes is bisected for the gap where it equals kT = epsilon; the
+    single term's 1 kT gap is sigma (U(sigma) = epsilon)."""
+    g = _golden("overcount.txt")
+    sig = 0.3
+    rc = 2 ** (1 / 6) * sig
+
+    def U(gap):
+        s = two_body(W.cube(1.0, 0.15), W.cube(1.0, 0.15), [0, 0, 1.0 + gap], sigma=sig)
+        return oracle_mod.forces(s)["U"][0]
+
+    lo, hi = sig, rc                    # U(lo) = 56 kT > kT > U(hi) = 0
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if U(mid) > 1.0:
+            lo = mid
+        else:
+            hi = mid
+    shift = (0.5 * (lo + hi) - sig) / sig
+    assert shift == pytest.approx(g["isosurface_shift_over_sigma"], abs=0.005)
+    # the 56 terms at the gap: 56 U(gap) = kT there
+    u1, _ = oracle_mod.wca(0.5 * (lo + hi), 1.0, sig)
+    assert 56 * u1 == pytest.approx(1.0, rel=1e-9)
+
+
 def test_squares_corner_and_edge_counts(oracle_mod):
     g = _golden("overcount.txt")
     sq = W.square(1.0, 0.15)
