@@ -581,6 +581,8 @@ double max_sigma(const dem_ctx *ctx) {
 // seven times the interaction volume; 0.4 keeps rebuilds tens of steps apart
 // at kT = 1, dt = 1e-3.
 constexpr double SKIN_CAP = 0.4;
+// Largest replica whose thermostat block sums and scales it directly.
+constexpr int DIRECT_MAX = 2048;
 double default_skin(const dem_ctx *ctx) { return std::min(max_sigma(ctx), SKIN_CAP); }
 
 // Cell grids, list cutoffs and degrees of freedom of every replica (needs the
@@ -760,9 +762,11 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     a.rotor32 = ctx->precision != DEM_FP64;
     a.ket = ctx->ket; a.virial = ctx->virial; a.reps_rw = ctx->d_reps;
     a.n_chunks = ctx->n_chunks; a.chunk_rep = ctx->chunk_rep; a.partial = ctx->partial;
-    // every replica within one reduction chunk: the thermostat kernel sums the
-    // kinetic energies itself (the NPT kernels take the chunk partials)
-    a.direct_sums = !a.npt && ctx->max_rep <= SUM_CHUNK;
+    // replicas of at most DIRECT_MAX particles: the thermostat kernel (one
+    // block per replica) sums the kinetic energies itself and, under NVT,
+    // applies the step's second scaling (the NPT kernels take the chunk
+    // partials)
+    a.direct_sums = !a.npt && ctx->max_rep <= DIRECT_MAX;
     return a;
 }
 
@@ -798,8 +802,11 @@ int launch_step(dem_ctx *ctx, double dt, int ens, double kT, double tau,
             ctx->launches += 1;
         }
         CK(launch_thermo_end(sa, ctx->stream));
-        CK(launch_scale(sa, ctx->stream));
-        ctx->launches += 2;
+        ctx->launches += 1;
+        if (!sa.direct_sums) {   // else k_thermo_end scaled the small replicas
+            CK(launch_scale(sa, ctx->stream));
+            ctx->launches += 1;
+        }
     }
     return DEM_OK;
 }

@@ -191,8 +191,8 @@ struct StepArgs {
     int n_chunks;            // reduction chunks over all replicas
     const int *chunk_rep;    // replica of each chunk
     double *partial;         // n_chunks * 3 chunk sums: K, K_trans (NPT), Tr W (NPT)
-    int direct_sums;         // NVE/NVT with every replica in one chunk: k_thermo_end sums
-                             // the kinetic energies itself (no chunk partials)
+    int direct_sums;         // NVE/NVT, every replica small: k_thermo_end sums the kinetic
+                             // energies itself and, under NVT, applies the second scaling
 };
 
 // ---- launch wrappers (pair.cu, nlist.cu, integrate.cu) ----

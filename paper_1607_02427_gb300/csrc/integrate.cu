@@ -328,7 +328,8 @@ __global__ void k_chunk_sums(const StepArgs a) {
 __global__ void k_thermo_end(const StepArgs a) {
     const int r = blockIdx.x;
     const Rep &rp = a.reps[r];
-    // one chunk per replica: its sum directly (the same value as its partial)
+    __shared__ double s_end;
+    // small replicas: the sum over the particles directly (no chunk partials)
     double K = a.direct_sums ? block_sum(a.ke, rp.off, rp.n, 1, 0)
                              : block_sum(a.partial, rp.chunk_off, rp.n_chunk, 3, 0);
     if (threadIdx.x == 0) {
@@ -347,8 +348,23 @@ __global__ void k_thermo_end(const StepArgs a) {
             t.eta_h = eta + xh * d;
             t.xi_h = xh + 0.5 * d * nh_rate(K * s1 * s1, g, a.kT, a.tau);
             t.s1 = s1;
+            s_end = s2;
         } else {
             t.K = K;
+        }
+    }
+    // NVT, small replicas: this step's second thermostat scaling of the
+    // replica's velocities and angular momenta here (else k_scale does it)
+    if (a.nvt && a.direct_sums) {
+        __syncthreads();
+        const double s = s_end;
+        for (int k = threadIdx.x; k < rp.n; k += blockDim.x) {
+            const int i = rp.off + k;
+            double4_32a v = a.vel[i], L = a.angmom[i];
+            v.x *= s; v.y *= s; v.z *= s;
+            L.x *= s; L.y *= s; L.z *= s;
+            a.vel[i] = v;
+            a.angmom[i] = L;
         }
     }
 }
