@@ -113,3 +113,25 @@ def test_nvt_thermalises(oracle_mod):
     assert K[1500:].mean() == pytest.approx(0.5 * g * 1.0, rel=0.35)
     H = tr[0, :, 3]
     assert np.ptp(H[100:]) < 0.02 * K[1500:].mean()
+
+
+@pytest.mark.parametrize("name", ["dented", "lshapes"])
+def test_energy_error_scales_dt2_concave(oracle_mod, name):
+    """Concave shapes with disks / spheres nested in their notches and dents
+    (Section "Model"): the spread of the conserved energy over a fixed time
+    falls as dt^2 (Section "Energy Conservation": a second-order integrator)."""
+    from tests.helpers import dent_points, nest_guests, notch_points
+    if name == "dented":
+        D = W.dented_cube(1.0, 0.6, 0.12)
+        s = nest_guests(open_cluster([D], np.zeros(8, np.int32), 41), range(0, 8, 2),
+                        W.sphere(0.15, 0.009), dent_points(D, 0.27), 41)
+    else:
+        L = W.l_shape2d(0.6, 0.12)
+        s = nest_guests(open_cluster([L], np.zeros(10, np.int32), 42), range(0, 10, 2),
+                        W.disk(0.15, 0.01), notch_points(L, 0.27), 42)
+    spread = []
+    for dt in (0.001, 0.0005):
+        _, tr = oracle_mod.run(s, int(round(0.2 / dt)), dt, ensemble="nve")
+        assert tr[0, :, 2].max() > 0.5, "the run must have interactions"
+        spread.append(np.ptp(tr[0, :, 3]))
+    assert 2.8 < spread[0] / spread[1] < 5.5, spread
