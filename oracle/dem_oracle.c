@@ -342,7 +342,11 @@ static void pair_terms(acc_t *A, int i, int j, const shape_t *si, const shape_t 
             }
         return;
     }
-    for (int ea = 0; ea < si->ne; ++ea)            /* E_i x E_j */
+    /* E_i x E_j.  Segment 1 of every edge pair is i's edge: the lower-
+     * indexed particle's edge is the parallel-edge rule's reference (inside
+     * the band, and not exactly parallel, the midpoint of the overlap of the
+     * other edge's projection on the reference depends on that choice). */
+    for (int ea = 0; ea < si->ne; ++ea)
         for (int eb = 0; eb < sj->ne; ++eb) {
             v3 p1, p2;
             int par;

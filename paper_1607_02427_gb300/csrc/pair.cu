@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
             w.rc = (T)WCA_CUT * pg.sig;
             w.sig2 = pg.sig * pg.sig;
             w.gj = pg.gj;
+            w.jref = j < i;
             if (!pair_setup<T, COUNT>(tab, itab, gi, gj, &w, &pc)) continue;
             bump<COUNT>(&pc, C_ACTIVE);
             eval_pair<T, DIM, COUNT>(tab, itab, gi, gj, w, eps, par_eps, S, &pc);
@@ -125,6 +126,7 @@ template <class T> struct alignas(16) QPair {
     T rc, sig2;
     int gj, owner;       // owner: the particle's lane in the warp
     unsigned vim, vjm, eim, ejm, fim, fjm;
+    int jref;            // j < i: j's edge is the parallel-edge rule's reference
 };
 template <class T> struct alignas(16) PInfo {   // one particle of the warp
     T r[9];              // R_i
@@ -158,6 +160,7 @@ __device__ __forceinline__ void run_batch(WarpSmem<T> &ws, int qh, int nb, int l
         w.gj = qp.gj;
         w.vim = qp.vim; w.vjm = qp.vjm; w.eim = qp.eim; w.ejm = qp.ejm;
         w.fim = qp.fim; w.fjm = qp.fjm;
+        w.jref = qp.jref;
         PartSink<T> part;
         part.zero();
         eval_pair<T, DIM, COUNT>(tab, itab, geo[ws.p[qp.owner].geom], geo[qp.gj], w, eps, par_eps,
@@ -283,6 +286,7 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
                     wk.rc = (T)WCA_CUT * pg.sig;
                     wk.sig2 = pg.sig * pg.sig;
                     wk.gj = pg.gj;
+                    wk.jref = j < i;
                     active = pair_setup<T, COUNT>(tab, itab, gi, gj, &wk, &pc);
                     if (active) bump<COUNT>(&pc, C_ACTIVE);
                 }
@@ -302,6 +306,7 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
                 qp.owner = pl;
                 qp.vim = wk.vim; qp.vjm = wk.vjm; qp.eim = wk.eim; qp.ejm = wk.ejm;
                 qp.fim = wk.fim; qp.fjm = wk.fjm;
+                qp.jref = wk.jref;
             }
             qt += __popc(m);
             __syncwarp();

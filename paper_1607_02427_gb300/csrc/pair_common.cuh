@@ -223,13 +223,18 @@ __device__ __forceinline__ void face_rest(const R4 *tab, const int *itab, int fa
 // for that s, and if that t leaves [0,1], t clamped and the optimal s for it
 // (each step solves one linear condition of the quadratic).  Nearly
 // parallel (|D1 x D2|^2 <= par_eps |D1|^2 |D2|^2): the parallel-edge rule
-// of Section "Model": the midpoint of the overlap of D2's projection on
-// segment 1, and its nearest point on segment 2; with no overlap, the
-// nearest of the four endpoint-to-segment pairs.
+// of Section "Model": the midpoint of the overlap of the other segment's
+// projection on the reference segment, and its nearest point on the other
+// segment; with no overlap, the nearest of the four endpoint-to-segment
+// pairs.  Unless the edges are exactly parallel the rule's result depends on
+// which segment is the reference, so both orders of a particle pair must
+// name the same one (else F_ij != -F_ji): the edge of the particle with the
+// lower index.  ref2 = false: segment 1 is the reference; ref2 = true:
+// segment 2 is.
 template <class T>
 __device__ __forceinline__ void segment_nearest(V3<T> A1, V3<T> D1, T inv_a, V3<T> A2,
-                                                V3<T> D2, T inv_c, T par_eps, V3<T> *P1,
-                                                V3<T> *P2) {
+                                                V3<T> D2, T inv_c, T par_eps, bool ref2,
+                                                V3<T> *P1, V3<T> *P2) {
     V3<T> W = A1 - A2;
     T a = dot(D1, D1), b = dot(D1, D2), c = dot(D2, D2);
     T d = dot(D1, W), e = dot(D2, W);
@@ -247,11 +252,19 @@ __device__ __forceinline__ void segment_nearest(V3<T> A1, V3<T> D1, T inv_a, V3<
             s = clamp01((b - d) * inv_a);
         }
     } else {
-        T t0 = -d * inv_a, t1 = (b - d) * inv_a;
+        // the other segment's endpoints projected on the reference's line
+        T t0, t1;
+        if (ref2) { t0 = e * inv_c; t1 = (e + b) * inv_c; }
+        else { t0 = -d * inv_a; t1 = (b - d) * inv_a; }
         T lo = fmax(T(0), fmin(t0, t1)), hi = fmin(T(1), fmax(t0, t1));
         if (lo <= hi) {
-            s = T(0.5) * (lo + hi);
-            t = clamp01((e + s * b) * inv_c);
+            if (ref2) {
+                t = T(0.5) * (lo + hi);
+                s = clamp01((t * b - d) * inv_a);
+            } else {
+                s = T(0.5) * (lo + hi);
+                t = clamp01((e + s * b) * inv_c);
+            }
         } else {
             // four endpoint-to-segment candidates in a fixed order
             T best = T(3.0e38);

@@ -139,6 +139,7 @@ template <class T> struct PairWork {
     V3<T> dl;            // x_j - x_i in i's frame
     T rc, sig2;
     int gj;
+    int jref;            // 1 when j < i: j's edge is the parallel-edge rule's reference
     unsigned vim, vjm;   // vertices of i / of j that can reach the other
     unsigned eim, ejm;   // edges
     unsigned fim, fjm;   // faces
@@ -380,7 +381,7 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                 if (sep * sep >= rc2 * n2 && n2 > par_eps * dot(D1, D1) * dot(D2, D2)) continue;
                 bump<COUNT>(pc, C_SEGSEG);
                 V3<T> P1, P2;
-                segment_nearest<T>(A1, D1, ad.w, A2, D2, bd.w, par_eps, &P1, &P2);
+                segment_nearest<T>(A1, D1, ad.w, A2, D2, bd.w, par_eps, w.jref != 0, &P1, &P2);
                 const V3<T> rv = P1 - P2;
                 const T r2 = dot(rv, rv);
                 if (r2 < rc2) {

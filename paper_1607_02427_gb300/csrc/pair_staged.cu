@@ -51,7 +51,8 @@ template <class T> struct SPair {      // a queued active pair
     T rc, sig2;
     int gj, owner;                     // j's geometry; the owner's lane
     unsigned vim, vjm, eim, ejm, fim, fjm;
-    int gi, pad;                       // i's geometry
+    int gi;                            // i's geometry
+    int jref;                          // j < i: j's edge is the parallel-edge rule's reference
 };
 template <class T> struct SInfo {      // one particle of the warp
     typename R4T<T>::type row[3];      // (R_i[r][0..2], x[r]); x: FP32 delta_i, FP64 position
@@ -309,7 +310,7 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
             V3<T> P1, P2;
             bump<COUNT>(&pc, C_SEGSEG);
             segment_nearest<T>(xyz<T>(aa), xyz<T>(ad), ad.w, v3<T>(a2.x, a2.y, a2.z),
-                               v3<T>(d2.x, d2.y, d2.z), inv_c, par_eps, &P1, &P2);
+                               v3<T>(d2.x, d2.y, d2.z), inv_c, par_eps, P.jref != 0, &P1, &P2);
             const V3<T> d = P1 - P2;
             const T rr = dot(d, d);
             if (rr < P.rc * P.rc) {
@@ -634,6 +635,7 @@ __device__ __forceinline__ bool scan_entry(const PairArgs &a, const typename R4T
     wk->rc = (T)WCA_CUT * pg.sig;
     wk->sig2 = pg.sig * pg.sig;
     wk->gj = pg.gj;
+    wk->jref = j < i;
     const bool active = pair_setup<T, COUNT>(tab, itab, gi, gj, wk, pc);
     if (active) bump<COUNT>(pc, C_ACTIVE);
     return active;
@@ -649,7 +651,7 @@ __device__ __forceinline__ void store_record(SPair<T> &P, const PairWork<T> &wk,
     P.vim = wk.vim; P.vjm = wk.vjm; P.eim = wk.eim; P.ejm = wk.ejm;
     P.fim = wk.fim; P.fjm = wk.fjm;
     P.gi = gi;
-    P.pad = 0;
+    P.jref = wk.jref;
 }
 
 // Shared-memory tables of a pair block: geometry records, geometries, int

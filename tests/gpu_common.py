@@ -19,13 +19,34 @@ FP32 geometry with coordinates of order one carries errors of a few 1e-7,
 i.e. a few 1e-7 / sigma relative to S_i; 1e-5 leaves a margin of ten or more.
 Particles the oracle flags as having an edge pair within a decade of the
 parallel-edge threshold are excluded (there the rule switches branch, and a
-lower-precision evaluation may take the other one) and counted.
+lower-precision evaluation may take the other one) and counted; every
+parity test bounds their number to 1% of the particles.
+
+A second, stricter measure relates each particle's error to its own net
+force instead of its terms' scales:
+    rel_F(i) = |F_i - F_i^oracle| / max(|F_i^oracle|, 1e-2 F_rms),
+F_rms the root mean square net force over the particles with terms, and
+the same for torques.  Where a particle's terms cancel this amplifies the
+rounding of its terms: by the ratio of S_i to max(|F_i|, 1e-2 F_rms),
+which reaches 1e3 or more for particles with many steep, nearly cancelling
+terms.  FP64 rounds positions of size L (the box) and contact geometry of
+order one to about 1e-16 of them; with that amplification the net-force
+error of FP64 reaches a few 1e-12, so its bar is 1e-10 (measured worst:
+2.2e-12 on the full-size batch).  It is reported for every case ("relF",
+"relT") and bounded by RELTOL; it is skipped for states with overlapping
+inner shapes (where a particle's terms are far above every net force and
+no relative measure is meaningful).  Its denominators have a floor of
+1e-12 of the particle's term scale, so that analytically zero quantities
+(the torques of spheres) do not divide rounding by zero.
 """
 from __future__ import annotations
 
 import numpy as np
 
 TOL = {0: 1e-12, 1: 1e-5, 2: 1e-5}
+# bars of the net-force measure rel_F / rel_T (see above)
+RELTOL = {0: 1e-10, 1: 1e-2, 2: 1e-2}
+FLAGGED_MAX = 0.01        # largest fraction of particles excluded near the parallel band
 
 
 def load_dem():
@@ -68,12 +89,24 @@ def force_errors(system, ref, out):
     zero_bad = (np.abs(f[zero]).max() if zero.any() else 0.0,
                 np.abs(t[zero]).max() if zero.any() else 0.0)
     Rmax = max(float(np.max(np.linalg.norm(sh["verts"], axis=1))) for sh in system.shapes)
+    sel = ok & ~zero
+    Fn = np.linalg.norm(ref["force"], axis=1)
+    Tn = np.linalg.norm(ref["torque"], axis=1)
+    Frms = np.sqrt(np.mean(Fn[~zero] ** 2)) if (~zero).any() else 0.0
+    Trms = np.sqrt(np.mean(Tn[~zero] ** 2)) if (~zero).any() else 0.0
+    dF = np.maximum(np.maximum(Fn, 1e-2 * Frms), 1e-12 * S)
+    dT = np.maximum(np.maximum(Tn, 1e-2 * Trms), 1e-12 * T)
+    relF = np.linalg.norm(f - ref["force"], axis=1) / np.maximum(dF, 1e-300)
+    relT = np.linalg.norm(t - ref["torque"], axis=1) / np.maximum(dT, 1e-300)
     errs = {
+        "relF": float(relF[sel].max()) if sel.any() else 0.0,
+        "relT": float(relT[sel].max()) if sel.any() else 0.0,
         "F": float(errF[ok & ~zero].max()) if (ok & ~zero).any() else 0.0,
         "T": float(errT[ok & ~zero].max()) if (ok & ~zero).any() else 0.0,
         "U": float(errU[ok & ~zero].max()) if (ok & ~zero).any() else 0.0,
         "zero": max(zero_bad),
         "flagged": int((~ok).sum()),
+        "n": int(len(ok)),
         "normF": float(np.linalg.norm(f - ref["force"]) / max(np.linalg.norm(ref["force"]), 1e-300)),
     }
     # per-replica totals
@@ -104,11 +137,16 @@ def report(what, errs):
             fh.write(json.dumps({"case": what, **row}) + "\n")
 
 
-def assert_parity(errs, precision, what=""):
+def assert_parity(errs, precision, what="", flagged_max=FLAGGED_MAX, rel=True):
     report(what, errs)
     tol = TOL[precision]
     for k in ("F", "T", "U", "W", "Utot"):
         assert errs[k] <= tol, f"{what}: {k} error {errs[k]:.3e} > {tol:.0e} ({errs})"
+    for k in (("relF", "relT") if rel else ()):
+        assert errs[k] <= RELTOL[precision], \
+            f"{what}: {k} error {errs[k]:.3e} > {RELTOL[precision]:.0e} ({errs})"
+    assert errs["flagged"] <= flagged_max * errs["n"], \
+        f"{what}: {errs['flagged']} of {errs['n']} particles flagged near the parallel band"
     assert errs["zero"] == 0.0, f"{what}: non-zero force on a particle without terms"
     if errs["counts"] is None:
         return

@@ -152,3 +152,97 @@ def dent_points(D, sigma, fracs=(0.82, 0.9, 0.97)):
     depth = D["verts"][4, 2] - apex[2]
     k = np.hypot(depth, t) / t           # axial height per unit face distance
     return [apex + np.array([0.0, 0.0, f * rc * k]) for f in fracs]
+
+
+# ---------------------------------------------------------------------------
+# Aligned and tied geometries (Section "Model": the parallel-edge rule and the
+# face-to-face overcounting example)
+# ---------------------------------------------------------------------------
+
+SIG_EDGE = 0.3            # sigma of the edge-case systems (rounding 0.15)
+
+
+def ridge_pair(sin2, dx, gap, sigma=SIG_EDGE):
+    """Two unit cubes, each turned 45 degrees about x so that an edge along x
+    forms a ridge; i's ridge points up, j's down, at a height gap above it.
+    j is turned further by theta about z (sin^2 theta = sin2: the squared
+    sine of the angle between the two ridges) and shifted by dx along x.
+    dx = 0.3: the ridges' projections overlap on [-0.2, 0.5], so the
+    parallel-edge rule puts the contact at the overlap's midpoint x = 0.15,
+    while the ordinary nearest points lie where the ridges cross, x = 0.3;
+    dx = 1.2: no overlap (the rule falls back to the endpoint pairs)."""
+    r45 = axis_angle_quat([1, 0, 0], np.pi / 4)
+    th = np.arcsin(np.sqrt(sin2))
+    qj = quat_mul(axis_angle_quat([0, 0, 1], th), r45)
+    return two_body(W.cube(1.0, sigma / 2), W.cube(1.0, sigma / 2),
+                    [dx, 0.0, np.sqrt(2.0) + gap], qa=r45, qb=qj, sigma=sigma)
+
+
+def face_to_face(gap, lateral=(0.0, 0.0), sigma=SIG_EDGE):
+    """Two aligned unit cubes, j above i's top face at the face gap, shifted
+    sideways by lateral (partial face overlap when non-zero)."""
+    return two_body(W.cube(1.0, sigma / 2), W.cube(1.0, sigma / 2),
+                    [lateral[0], lateral[1], 1.0 + gap], sigma=sigma)
+
+
+def collinear_ridges(gap, sigma=SIG_EDGE):
+    """Two cubes turned 45 degrees about x, side by side along x: their
+    ridges are collinear with a gap (parallel, no overlap) and their x faces
+    face each other at the same gap."""
+    r45 = axis_angle_quat([1, 0, 0], np.pi / 4)
+    return two_body(W.cube(1.0, sigma / 2), W.cube(1.0, sigma / 2), [1.0 + gap, 0.0, 0.0],
+                    qa=r45, qb=r45, sigma=sigma)
+
+
+def vertex_over_face_edge(gap, corner=False, sigma=SIG_EDGE):
+    """A cube j standing on a vertex whose lowest vertex lies a gap above
+    i's top face, exactly over the edge y = 0.5 of that face (corner: over
+    the corner x = y = 0.5): the vertex projects onto the face's boundary,
+    where the inside test of the vertex-face term is tied."""
+    a = np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0)
+    axis = np.cross(a, [0.0, 0.0, -1.0])
+    ang = np.arccos(np.dot(a, [0.0, 0.0, -1.0]))
+    qj = axis_angle_quat(axis, ang)
+    low = rotmat(qj) @ np.array([0.5, 0.5, 0.5])          # the vertex that points down
+    target = np.array([0.5 if corner else 0.0, 0.5, 0.5 + gap])
+    return two_body(W.cube(1.0, sigma / 2), W.cube(1.0, sigma / 2), target - low, qb=qj,
+                    sigma=sigma)
+
+
+def aligned_lattice(dim, n_side, gap, jitter, seed, sigma=SIG_EDGE):
+    """Unrotated unit squares or cubes on a square or simple-cubic lattice of
+    spacing 1 + gap in a periodic box, each displaced by up to jitter per
+    axis: every edge pair is exactly parallel or exactly perpendicular, and
+    neighbours meet face to face (edge to edge in 2D) at gaps near gap with
+    partial overlaps."""
+    rng = np.random.default_rng(seed)
+    a = 1.0 + gap
+    sites = W.sc_sites([n_side] * dim, [a] * dim)
+    pos = sites + rng.uniform(-jitter, jitter, size=sites.shape)
+    n = len(pos)
+    shape = W.cube(1.0, sigma / 2) if dim == 3 else W.square(1.0, sigma / 2)
+    orient = np.tile([1.0, 0, 0, 0], (n, 1)) if dim == 3 else np.zeros((n, 1))
+    s = W.System(dim, [shape], np.zeros(n, np.int32), np.mod(pos, n_side * a), orient,
+                 np.zeros((n, dim)), np.zeros((n, 3 if dim == 3 else 1)),
+                 np.full((1, dim), n_side * a), np.array([n], np.int32), 1.0, sigma)
+    return s
+
+
+def square_pairs_2d(gap, sigma=SIG_EDGE):
+    """2D ties: squares corner to corner (each corner vertex at the two
+    edges of the other corner) and edge to edge (facing edges parallel),
+    as two replicas."""
+    sq = W.square(1.0, sigma / 2)
+    cc = two_body(sq, sq, [1 + gap / np.sqrt(2), 1 + gap / np.sqrt(2)], sigma=sigma)
+    ee = two_body(sq, sq, [0.3, 1 + gap], sigma=sigma)
+    return W.merge([cc, ee], "square_pairs")
+
+
+def swap_pair(s):
+    """The same two-particle system with the particles' order swapped (the
+    parallel-edge rule's reference edge is the lower-indexed particle's)."""
+    t = copy_system(s)
+    for k in ("pos", "orient", "vel", "angmom"):
+        setattr(t, k, getattr(t, k)[::-1].copy())
+    t.shape_id = t.shape_id[::-1].copy()
+    return t

@@ -252,7 +252,9 @@ def test_set_state_keeps_valid_list(dem, precision):
         t = W.System(s2.dim, s2.shapes, ids, s2.pos, s2.orient, s2.vel, s2.angmom, s2.box,
                      s2.replica_sizes, s2.epsilon, s2.sigma)
         dem.dem_set_state(d.ctx, t.shape_id, t.pos, t.orient, t.vel, t.angmom)
-        assert_parity(_ctx_errors(d, t), precision, "set_state new shapes")
+        # the spheres nested in the dents now lie inside plain cubes: an
+        # overlapping state, compared on the term scales only
+        assert_parity(_ctx_errors(d, t), precision, "set_state new shapes", rel=False)
 
 
 @pytest.mark.parametrize("group", [4, 8, 16, 32])
