@@ -68,8 +68,11 @@ extern "C" {
 #define DEM_FP32_COMP 2   /* geometry and force in FP32, compensated (two-sum)
                              FP32 sums of force and torque                      */
 /* In every mode positions, velocities, orientations, angular momenta,
- * per-particle energies and virials are held in FP64, and the pair
- * separation x_j - x_i is formed in FP64 before it is rounded. */
+ * per-particle energies and virials are held in FP64.  In the FP32 modes the
+ * neighbour list keeps each pair's separation d0 = x_j - x_i of the last
+ * list build (taken in FP64, rounded to FP32) and each particle keeps its
+ * displacement delta since that build (FP64, rounded to FP32); the pair
+ * kernels form x_j - x_i = d0 + delta_j - delta_i in FP32. */
 
 /* ---- ensembles ---- */
 #define DEM_NVE 0
@@ -161,9 +164,15 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
  * neighbour list is rebuilt when any shape id differs from the previous
  * call's, or when a particle lies more than skin/2 from its position at the
  * last build (the test a step makes); otherwise the list is kept, which is
- * exact: it holds every pair within the interaction range.  Errors: DEM_ERR_ARG, DEM_ERR_BOX (a box edge below
- * twice the neighbour-list cutoff R_i + R_j + r_cut + skin of the replica's
- * largest shapes), DEM_ERR_CUDA, DEM_ERR_NONFINITE. */
+ * exact: it holds every pair within the interaction range.
+ * Errors: DEM_ERR_ARG (a shape id out of range; a non-finite position,
+ * orientation, velocity or angular momentum, or a quaternion of zero norm:
+ * checked on the device as the arrays are imported, host or device alike),
+ * DEM_ERR_BOX (a box edge below twice the neighbour-list cutoff
+ * R_i + R_j + r_cut + skin of the replica's largest shapes), DEM_ERR_CUDA,
+ * DEM_ERR_NONFINITE (the forces of the state are not finite, e.g. two
+ * particles that coincide).  After an error the context has no state
+ * (dem_step returns DEM_ERR_STATE) until a dem_set_state succeeds. */
 int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const double *orient,
                   const double *vel, const double *angmom, int device_ptrs);
 
@@ -337,10 +346,13 @@ int dem_shape_info(const dem_shape *shape, double *out);
  *   stream     cudaStream_t to run on; NULL is the default stream
  * Neighbours are searched over all pairs (cost ~ n^2: meant for small
  * systems); a particle with more than DEM_NOALLOC_MAX_NEIGHBOURS partners in
- * range gives DEM_ERR_NLIST_OVERFLOW, since no memory can be added.  The call
- * returns after its stream has finished the work.  The first call on each
- * device looks up the static array's address with that device current; make
- * that first call before any stream capture.  Every call on a device shares
+ * range gives DEM_ERR_NLIST_OVERFLOW, since no memory can be added.  A
+ * non-finite position or orientation, or a zero quaternion, gives
+ * DEM_ERR_ARG.  The call returns after its stream has finished the work.
+ * The first call in each CUDA context (on a device: its primary context, and
+ * the new one after a cudaDeviceReset) looks up the static array's address
+ * in that context, which is then current; make that first call before any
+ * stream capture.  Every call on a device shares
  * the one array, which keeps the last call's contents (each call clears what
  * must start at zero); calls that overlap on the GPU (from other threads or
  * streams) race, so the caller must serialise them.  Errors are reported by
@@ -352,8 +364,19 @@ int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double epsilon, do
                        const double *orient, int precision, double *force, double *torque,
                        double *energy, void *stream);
 
+/* Measured fused multiply-add throughput of the current device: every
+ * thread of a full-occupancy grid runs 8 independent chains a <- a b + c of
+ * iters turns (iters >= 4) in FP32 (precision DEM_FP32) or FP64 (DEM_FP64);
+ * *tflops = 2 flops per FMA over the best of three timed launches (CUDA
+ * events, after one warm-up launch), *ms that launch's duration.  The paper
+ * has no counterpart: the pair kernels do plain ALU arithmetic, and this is
+ * the peak their roofline fraction is taken against.  Allocates a small
+ * device buffer and a stream for the measurement.  Errors: DEM_ERR_ARG,
+ * DEM_ERR_CUDA (dem_last_error(NULL) gives the reason). */
+int dem_fma_peak(int precision, int iters, double *tflops, double *ms);
+
 /* One-line description of the last error of ctx (or of the last failed
- * dem_create or dem_forces_noalloc when ctx is NULL). */
+ * dem_create, dem_forces_noalloc or dem_fma_peak when ctx is NULL). */
 const char *dem_last_error(const dem_ctx *ctx);
 
 void dem_destroy(dem_ctx *ctx);

@@ -607,7 +607,7 @@ int setup_replicas(dem_ctx *ctx) {
         }
         rp.g_dof = (int)g;
         double sig = ctx->sigma > 0 ? ctx->sigma : 2 * rnd_max;
-        double rlist = 2 * Rmax * (1 + 1e-6) + WCA_CUT * sig + ctx->skin;
+        double rlist = pair_range(Rmax, sig, ctx->skin);
         double vol = 1.0;
         rp.allpairs = 0;
         for (int a = 0; a < 3; ++a) {
@@ -875,6 +875,9 @@ int compute_forces(dem_ctx *ctx) {
             if (rc) return rc;
             continue;
         }
+        if (st.bad_input)
+            return set_err(ctx, DEM_ERR_ARG, "particle %d: non-finite position, orientation, "
+                           "velocity or angular momentum, or a zero quaternion", st.bad_input - 1);
         if (st.nonfinite) return set_err(ctx, DEM_ERR_NONFINITE, "non-finite force or energy");
         return DEM_OK;
     }
@@ -1251,13 +1254,16 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
         if (rc) return rc;
     }
     const int odim = dim == 3 ? 4 : 1, adim = dim == 3 ? 3 : 1;
+    // the import kernels record a non-finite value or a zero quaternion here
+    CK(cudaMemsetAsync(&ctx->status->bad_input, 0, sizeof(int), ctx->stream));
+    ctx->have_state = false;
     const double *src[4] = {pos, orient, vel, angmom};
     const int widths[4] = {dim, odim, dim, adim};
     const double *dsrc[4];
     if (device_ptrs) {
         for (int k = 0; k < 4; ++k) dsrc[k] = src[k];
         CK(launch_import_state((int)n, dim, dsrc[0], dsrc[1], dsrc[2], dsrc[3], ctx->pos, ctx->quat,
-                               ctx->vel, ctx->angmom, ctx->stream));
+                               ctx->vel, ctx->angmom, ctx->status, ctx->stream));
     } else {
         // the four arrays go through the staging buffer one at a time
         double *stage = ctx->staging;
@@ -1268,7 +1274,7 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
             // import only the array just staged: the others keep their values
             CK(launch_import_state((int)n, dim, k == 0 ? stage : nullptr, k == 1 ? stage : nullptr,
                                    k == 2 ? stage : nullptr, k == 3 ? stage : nullptr, ctx->pos,
-                                   ctx->quat, ctx->vel, ctx->angmom, ctx->stream));
+                                   ctx->quat, ctx->vel, ctx->angmom, ctx->status, ctx->stream));
         }
     }
     CK(launch_prepare_state((int)n, dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom, ctx->rep,
@@ -1283,7 +1289,12 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
     }
     ctx->have_state = true;
     rc = compute_forces(ctx);
-    if (rc) return rc;
+    if (rc) {
+        // a rejected input or non-finite forces leave no usable state: steps
+        // return DEM_ERR_STATE until a valid dem_set_state, which rebuilds
+        ctx->have_state = false;
+        return rc;
+    }
     StepArgs sa = step_args(ctx, 0.0, DEM_NVE, 1.0, 1.0);
     CK(launch_kinetic(sa, ctx->stream));
     if (!sa.direct_sums) CK(launch_chunk_sums(sa, ctx->stream));

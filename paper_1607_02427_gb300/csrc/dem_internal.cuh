@@ -99,6 +99,8 @@ struct Status {
     int built;               // set by the list build when it ran this step
     int box_limit;           // NPT: a box fell below what its cell grid or minimum
                              // image allows within the call
+    int bad_input;           // 1 + index of a particle whose imported state was not
+                             // finite or whose quaternion had zero norm (else 0)
 };
 
 // Per-replica thermostat state (FP64): canonical end-of-step values and the
@@ -229,7 +231,8 @@ cudaError_t launch_export_state(int n, int dim, const double4_32a *pos, const do
                                 cudaStream_t s);
 cudaError_t launch_import_state(int n, int dim, const double *pos_in, const double *orient_in,
                                 const double *vel_in, const double *angmom_in, double4_32a *pos,
-                                double4_32a *quat, double4_32a *vel, double4_32a *angmom, cudaStream_t s);
+                                double4_32a *quat, double4_32a *vel, double4_32a *angmom,
+                                Status *status, cudaStream_t s);
 cudaError_t launch_export_forces(int n, int dim, const double4_32a *force, const double4_32a *torque_b,
                                  const double4_32a *quat, double *force_out, double *torque_out,
                                  cudaStream_t s);
@@ -248,6 +251,14 @@ struct HostTables {
     double Rmax = 0, rnd_max = 0;
 };
 int make_host_tables(const dem_shape *shapes, int n_shapes, HostTables *t, std::string *err);
+
+// Centre distance within which two particles of bounding radii up to Rmax
+// (the padded FP32 radii of the geometry records) can interact, plus the
+// list skin: 2 Rmax + r_cut(sigma_max) + skin, the radii enlarged by 1e-6
+// relative so that no rounding can bring an interacting pair beyond it.
+inline double pair_range(double Rmax, double sig_max, double skin) {
+    return 2.0 * Rmax * (1.0 + 1e-6) + 1.122462048309373 * sig_max + skin;
+}
 void set_global_error(const std::string &msg);
 
 }  // namespace dem

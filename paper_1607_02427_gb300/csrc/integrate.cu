@@ -569,27 +569,63 @@ __global__ void k_prepare(int n, int dim, double4_32a *pos, double4_32a *quat, f
     }
 }
 
+// Input state into the packed arrays.  A particle whose imported values
+// are not all finite, or whose quaternion has zero norm, is recorded in
+// status->bad_input (1 + its index) and given a harmless state (centre at
+// the origin, identity orientation, at rest), so that the kernels that
+// follow in the same call run on finite data; the call then fails.
 __global__ void k_import(int n, int dim, const double *pos_in, const double *orient_in,
                          const double *vel_in, const double *angmom_in, double4_32a *pos,
-                         double4_32a *quat, double4_32a *vel, double4_32a *angmom) {
+                         double4_32a *quat, double4_32a *vel, double4_32a *angmom,
+                         Status *status) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        bool bad = false;
         if (dim == 3) {
-            if (pos_in) pos[i] = make_double4_32a(pos_in[3 * i], pos_in[3 * i + 1], pos_in[3 * i + 2], 0.0);
-            if (vel_in) vel[i] = make_double4_32a(vel_in[3 * i], vel_in[3 * i + 1], vel_in[3 * i + 2], 0.0);
-            if (orient_in)
-                quat[i] = make_double4_32a(orient_in[4 * i], orient_in[4 * i + 1], orient_in[4 * i + 2],
-                                       orient_in[4 * i + 3]);
-            if (angmom_in)
-                angmom[i] = make_double4_32a(angmom_in[3 * i], angmom_in[3 * i + 1], angmom_in[3 * i + 2], 0.0);
+            if (pos_in) {
+                double4_32a x = make_double4_32a(pos_in[3 * i], pos_in[3 * i + 1], pos_in[3 * i + 2], 0.0);
+                if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z))) { bad = true; x = make_double4_32a(0, 0, 0, 0); }
+                pos[i] = x;
+            }
+            if (vel_in) {
+                double4_32a v = make_double4_32a(vel_in[3 * i], vel_in[3 * i + 1], vel_in[3 * i + 2], 0.0);
+                if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) { bad = true; v = make_double4_32a(0, 0, 0, 0); }
+                vel[i] = v;
+            }
+            if (orient_in) {
+                double4_32a q = make_double4_32a(orient_in[4 * i], orient_in[4 * i + 1], orient_in[4 * i + 2],
+                                                 orient_in[4 * i + 3]);
+                const double q2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+                if (!(isfinite(q2) && q2 > 0.0)) { bad = true; q = make_double4_32a(1, 0, 0, 0); }
+                quat[i] = q;
+            }
+            if (angmom_in) {
+                double4_32a L = make_double4_32a(angmom_in[3 * i], angmom_in[3 * i + 1], angmom_in[3 * i + 2], 0.0);
+                if (!(isfinite(L.x) && isfinite(L.y) && isfinite(L.z))) { bad = true; L = make_double4_32a(0, 0, 0, 0); }
+                angmom[i] = L;
+            }
         } else {
-            if (pos_in) pos[i] = make_double4_32a(pos_in[2 * i], pos_in[2 * i + 1], 0.0, 0.0);
-            if (vel_in) vel[i] = make_double4_32a(vel_in[2 * i], vel_in[2 * i + 1], 0.0, 0.0);
+            if (pos_in) {
+                double4_32a x = make_double4_32a(pos_in[2 * i], pos_in[2 * i + 1], 0.0, 0.0);
+                if (!(isfinite(x.x) && isfinite(x.y))) { bad = true; x = make_double4_32a(0, 0, 0, 0); }
+                pos[i] = x;
+            }
+            if (vel_in) {
+                double4_32a v = make_double4_32a(vel_in[2 * i], vel_in[2 * i + 1], 0.0, 0.0);
+                if (!(isfinite(v.x) && isfinite(v.y))) { bad = true; v = make_double4_32a(0, 0, 0, 0); }
+                vel[i] = v;
+            }
             if (orient_in) {
                 double th = orient_in[i];
+                if (!isfinite(th)) { bad = true; th = 0.0; }
                 quat[i] = make_double4_32a(cos(0.5 * th), 0.0, 0.0, sin(0.5 * th));
             }
-            if (angmom_in) angmom[i] = make_double4_32a(0.0, 0.0, angmom_in[i], 0.0);
+            if (angmom_in) {
+                double L = angmom_in[i];
+                if (!isfinite(L)) { bad = true; L = 0.0; }
+                angmom[i] = make_double4_32a(0.0, 0.0, L, 0.0);
+            }
         }
+        if (bad && status) atomicMax(&status->bad_input, i + 1);
     }
 }
 
@@ -732,9 +768,10 @@ cudaError_t launch_prepare_state(int n, int dim, double4_32a *pos, double4_32a *
 }
 cudaError_t launch_import_state(int n, int dim, const double *pos_in, const double *orient_in,
                                 const double *vel_in, const double *angmom_in, double4_32a *pos,
-                                double4_32a *quat, double4_32a *vel, double4_32a *angmom, cudaStream_t s) {
+                                double4_32a *quat, double4_32a *vel, double4_32a *angmom,
+                                Status *status, cudaStream_t s) {
     k_import<<<grid_for(n, 256), 256, 0, s>>>(n, dim, pos_in, orient_in, vel_in, angmom_in, pos,
-                                              quat, vel, angmom);
+                                              quat, vel, angmom, status);
     return cudaGetLastError();
 }
 cudaError_t launch_export_state(int n, int dim, const double4_32a *pos, const double4_32a *quat,
