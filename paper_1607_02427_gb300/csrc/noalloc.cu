@@ -14,6 +14,8 @@
 // it keeps the last call's contents, so each call clears what must start at
 // zero (the status word, the replica index of every particle), and calls
 // that overlap on the GPU race: the caller must serialise them.
+#include <cuda.h>   // CUcontext / CUresult types only; the entry points are looked up
+
 #include <mutex>
 
 #include "dem_internal.cuh"
@@ -22,7 +24,6 @@ using namespace dem;
 
 namespace {
 
-constexpr double WCA_CUT = 1.122462048309373;   // 2^(1/6)
 constexpr int MAX_N = DEM_NOALLOC_MAX_N;
 constexpr int CAP = DEM_NOALLOC_MAX_NEIGHBOURS;
 constexpr size_t TABLE_BYTES = 128 * 1024;      // geometry records
@@ -56,26 +57,76 @@ constexpr size_t SCRATCH_BYTES = OFF_STATUS + align256(sizeof(Status));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
-// Device address of the static array, looked up once per device.
-std::mutex g_mu;
-void *g_base[128] = {};
+// Device address of the static array in the CUDA context current on the
+// calling thread.  The address belongs to a context, not to a device
+// ordinal: after cudaDeviceReset the module is loaded again into a new
+// primary context, and a caller may make a context of its own current.  So
+// the address is looked up (cudaGetSymbolAddress, with that context current)
+// once per context, keyed by the driver's unique context id, and cached.
+// The context queries come from the driver through the runtime's
+// entry-point lookup, so the library does not link libcuda.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
 
-int scratch_base(void **out, std::string *err) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) { *err = cudaGetErrorString(e); return DEM_ERR_CUDA; }
-    if (dev < 0 || dev >= 128) { *err = "device index out of range"; return DEM_ERR_CUDA; }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_base[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+std::mutex g_mu;
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    void *base;
+};
+ScratchEntry g_cache[64];
+int g_cached = 0;
+PfnCtxGetCurrent g_ctx_current = nullptr;
+PfnCtxGetId g_ctx_id = nullptr;
+
+int current_context_id(unsigned long long *id, std::string *err) {
+    if (!g_ctx_current || !g_ctx_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            *err = "driver context queries unavailable";
             return DEM_ERR_CUDA;
         }
-        g_base[dev] = p;
+        g_ctx_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+        g_ctx_id = reinterpret_cast<PfnCtxGetId>(f2);
     }
-    *out = g_base[dev];
+    CUcontext c = nullptr;
+    if (g_ctx_current(&c) != CUDA_SUCCESS) { *err = "cuCtxGetCurrent failed"; return DEM_ERR_CUDA; }
+    if (!c) {
+        // no context yet on this thread: make the current device's primary
+        // context current (cudaSetDevice initialises it)
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(dev);
+        if (e != cudaSuccess) { *err = cudaGetErrorString(e); return DEM_ERR_CUDA; }
+        if (g_ctx_current(&c) != CUDA_SUCCESS || !c) { *err = "no CUDA context"; return DEM_ERR_CUDA; }
+    }
+    if (g_ctx_id(c, id) != CUDA_SUCCESS) { *err = "cuCtxGetId failed"; return DEM_ERR_CUDA; }
+    return DEM_OK;
+}
+
+int scratch_base(void **out, std::string *err) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    unsigned long long id = 0;
+    int rc = current_context_id(&id, err);
+    if (rc) return rc;
+    for (int k = 0; k < g_cached; ++k)
+        if (g_cache[k].ctx_id == id) { *out = g_cache[k].base; return DEM_OK; }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return DEM_ERR_CUDA;
+    }
+    // a full cache drops its oldest entry (contexts of a finished reset)
+    if (g_cached == 64) {
+        for (int k = 1; k < 64; ++k) g_cache[k - 1] = g_cache[k];
+        --g_cached;
+    }
+    g_cache[g_cached++] = {id, p};
+    *out = p;
     return DEM_OK;
 }
 
@@ -117,7 +168,7 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
         return fail(DEM_ERR_ARG, "dem_forces_noalloc: shape tables exceed the static limit");
     // minimum image is exact when every box edge is at least twice the range
     const double sig_max = sigma > 0 ? sigma : 2.0 * t.rnd_max;
-    const double range = 2.0 * t.Rmax + WCA_CUT * sig_max;
+    const double range = pair_range(t.Rmax, sig_max, 0.0);
     Rep rp = {};
     for (int a = 0; a < 3; ++a) {
         rp.L[a] = a < dim ? box[a] : 1.0;
@@ -187,7 +238,8 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     NA_CK(cudaMemcpyAsync(shp, shape_id, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
 
     // pack the state, all-pairs list, pair kernel, world-frame outputs
-    NA_CK(launch_import_state(n, dim, pos, orient, nullptr, nullptr, pos4, quat4, nullptr, nullptr, st));
+    NA_CK(launch_import_state(n, dim, pos, orient, nullptr, nullptr, pos4, quat4, nullptr, nullptr,
+                              status, st));
     NA_CK(launch_prepare_state(n, dim, pos4, quat4, quatf, nullptr, rep, reprec, 0, st));
     NlistArgs na = {};
     na.n = n; na.dim = dim; na.cap = CAP; na.cell_cap = 0;
@@ -216,6 +268,9 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     Status hs;
     NA_CK(cudaMemcpyAsync(&hs, status, sizeof(Status), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
+    if (hs.bad_input)
+        return fail(DEM_ERR_ARG, "dem_forces_noalloc: particle " + std::to_string(hs.bad_input - 1) +
+                                     ": non-finite position or orientation, or a zero quaternion");
     if (hs.nlist_overflow)
         return fail(DEM_ERR_NLIST_OVERFLOW, "dem_forces_noalloc: a particle has more than " +
                                                 std::to_string(CAP) + " neighbours in range");

@@ -37,7 +37,8 @@ EXPORTS = ["dem_create", "dem_set_state", "dem_get_state", "dem_set_thermostat",
            "dem_compute", "dem_get_forces", "dem_get_energy", "dem_get_particle_energy",
            "dem_get_virial", "dem_set_box", "dem_set_param", "dem_get_param", "dem_autotune",
            "dem_get_counters", "dem_set_stream", "dem_shape_info", "dem_last_error",
-           "dem_destroy", "dem_forces_noalloc", "dem_set_barostat", "dem_get_box"]
+           "dem_destroy", "dem_forces_noalloc", "dem_set_barostat", "dem_get_box",
+           "dem_fma_peak"]
 DEM_NOALLOC_MAX_N = 16384
 DEM_NOALLOC_MAX_NEIGHBOURS = 64
 
@@ -92,6 +93,7 @@ def load():
         "dem_destroy": [vp],
         "dem_forces_noalloc": [C.POINTER(dem_shape), C.c_int, C.c_double, C.c_double, dp,
                                C.c_int, vp, vp, vp, C.c_int, vp, vp, vp, vp],
+        "dem_fma_peak": [C.c_int, C.c_int, dp, dp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -277,12 +279,45 @@ def dem_destroy(ctx):
         load().dem_destroy(ctx)
 
 
+def dem_fma_peak(precision: int, iters: int):
+    """Measured FMA throughput (TFLOP/s, ms of the timed launch) of the
+    current device in FP32 (DEM_FP32) or FP64 (DEM_FP64)."""
+    t, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(load().dem_fma_peak(int(precision), int(iters), C.byref(t), C.byref(ms)))
+    return t.value, ms.value
+
+
 def dem_forces_noalloc(shapes: Sequence[dict], epsilon: float, sigma: float, box, shape_id,
                        pos, orient, precision: int, force, torque, energy=None,
                        stream_handle: Optional[int] = None):
     """Forces of one system with no device allocation (see dem.h).  shape_id,
-    pos, orient, force, torque and energy are CUDA tensors."""
+    pos, orient, force, torque and energy are CUDA tensors: contiguous,
+    int32 (shape_id) or float64 (the rest), with the sizes dem.h states;
+    anything else raises ValueError before the library is called (the
+    library cannot check device arrays it is handed)."""
+    import torch
     lib = load()
+    if not isinstance(shape_id, torch.Tensor) or shape_id.dim() != 1:
+        raise ValueError("shape_id must be a 1-D CUDA tensor")
+    n = int(shape_id.shape[0])
+    dim = int(shapes[0]["dim"])
+    widths = {"pos": dim, "orient": 4 if dim == 3 else 1, "force": dim,
+              "torque": 3 if dim == 3 else 1, "energy": 1}
+    named = {"shape_id": (shape_id, torch.int32, 1), "pos": (pos, torch.float64, widths["pos"]),
+             "orient": (orient, torch.float64, widths["orient"]),
+             "force": (force, torch.float64, widths["force"]),
+             "torque": (torque, torch.float64, widths["torque"])}
+    if energy is not None:
+        named["energy"] = (energy, torch.float64, 1)
+    for nm, (t, dt, w) in named.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{nm} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{nm} must have dtype {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{nm} must be contiguous")
+        if t.numel() != n * w:
+            raise ValueError(f"{nm} must hold {n} x {w} values, got {t.numel()}")
     arr = (dem_shape * len(shapes))()
     keep = []
     for k, sh in enumerate(shapes):
@@ -290,7 +325,6 @@ def dem_forces_noalloc(shapes: Sequence[dict], epsilon: float, sigma: float, box
         arr[k] = s
         keep += kk
     b = _host(np.asarray(box, np.float64).ravel(), np.float64)
-    n = int(shape_id.shape[0])
     return _check(lib.dem_forces_noalloc(arr, len(shapes), float(epsilon), float(sigma),
                                          b.ctypes.data_as(C.POINTER(C.c_double)), n,
                                          _ptr(shape_id), _ptr(pos), _ptr(orient), int(precision),
