@@ -39,6 +39,8 @@ METRIC = "particle-steps/s and FP32-peak fraction, FP32+comp batched vs plain FP
 UNIT = "particle-steps/s"
 
 # GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock.
+# The roofline uses the measured FMA rates (dem_fma_peak); these nominal
+# figures are reported beside them for context.
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 rate (far below the FP32 rate)
@@ -214,6 +216,19 @@ class ClockSampler:
 # Roofline
 # ---------------------------------------------------------------------------
 
+def measured_peaks(dem):
+    """FP32 and FP64 FMA throughput of this GPU (dem_fma_peak: independent
+    FMA chains on every lane of a full-occupancy grid), each launch scaled to
+    about 20 ms; best of three launches after a warm-up."""
+    out = {}
+    for name, p, it0 in (("fp32", dem.DEM_FP32, 16384), ("fp64", dem.DEM_FP64, 256)):
+        t, ms = dem.dem_fma_peak(p, it0)
+        it = max(4, int(it0 * 20.0 / max(ms, 1e-3)) // 4 * 4)
+        t, ms = dem.dem_fma_peak(p, it)
+        out[name] = {"tflops": t, "launch_ms": ms, "iters": it}
+    return out
+
+
 def algorithmic_flops(counts, comp):
     f = sum(FLOPS_PER_PATH[k] * int(counts[k]) for k in FLOPS_PER_PATH)
     if comp:
@@ -385,10 +400,12 @@ def main():
     flops = algorithmic_flops(counts, prec == dem.DEM_FP32_COMP)
     achieved = flops / (pair_ms / 1e3) / 1e12
     clocks = clk.summary()
+    peaks = measured_peaks(dem)
+    peak = peaks["fp64" if prec == dem.DEM_FP64 else "fp32"]["tflops"]
 
     extras = {}
     if not a.no_extras:
-        extras = measure_extras(a, dem, d, system, run, ens, prec, torch)
+        extras = measure_extras(a, dem, d, system, run, ens, prec, torch, peaks)
     cpu = None
     if rank == 0 and world == 1 and not a.no_extras:
         cpu = time_oracle(system, run, a.cpu_seconds)
@@ -412,15 +429,19 @@ def main():
             "parallelism": f"replicas x{world}",
         },
         "roofline": {
-            "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ncu_traffic(a.workload, a.precision),
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(a.workload, a.precision),
             "kernel": f"pair-feature kernel (decomposition {decomp_name})",
             "autotune_ms": tune,
             "kernel_ms": pair_ms, "kernel_share_of_step": pair_ms / (t_max / a.steps),
             "flops_per_launch": flops, "feature_pairs_per_launch": pair_fpe,
             "work_counters": {name: int(counts[k]) for k, name in WORK_COUNTERS.items()},
             "feature_pairs_per_s": pair_fpe / (pair_ms / 1e3),
-            "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max clock",
+            "peak_note": ("measured on this GPU: FMA-chain microbenchmark (dem_fma_peak), "
+                          "burst of about 20 ms; frac is of measured"),
+            "measured_peaks_tflops": {k: v["tflops"] for k, v in peaks.items()},
+            "nominal_peaks_tflops": {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS,
+                                     "fp32_note": "152 SMs x 128 lanes x 2 x 2.07 GHz"},
         },
         "gpu_launches": launches,
         "list_rebuilds": rebuilds,
@@ -436,7 +457,7 @@ def main():
     d.close()
 
 
-def measure_extras(a, dem, d, system, run, ens, prec, torch):
+def measure_extras(a, dem, d, system, run, ens, prec, torch, peaks):
     """End-to-end through the C ABI with host buffers, and the FP64 paths."""
     out = {}
     st = d.state()
@@ -487,10 +508,11 @@ def measure_extras(a, dem, d, system, run, ens, prec, torch):
                 d2.set_param("profile", 0)
                 fl = algorithmic_flops(d2.counters(), False)
                 ach = fl / (pms / 1e3) / 1e12
+                p64 = peaks["fp64"]["tflops"]
                 out[name]["roofline"] = {
-                    "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "kernel_ms": pms,
-                    "peak_note": "nominal FP64 rate of GB300 (no measured FP64 peak)"}
+                    "bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s",
+                    "frac": ach / p64, "kernel_ms": pms,
+                    "peak_note": "measured FP64 FMA rate of this GPU (dem_fma_peak)"}
     # plain FP64 single-system path: one context per replica, launch by launch
     if system.n_replicas > 1:
         sample = list(range(0, system.n_replicas, max(1, system.n_replicas // 24)))[:24]
