@@ -293,12 +293,10 @@ def oracle_sample(system, target_particles=3000, max_step_s=None, run=None):
     return (W.merge(take) if len(take) > 1 else take[0]), len(take)
 
 
-def time_oracle(system, run, seconds, steps=None):
-    """The FP64 oracle on a bounded sample of the workload: chunks of steps
-    until ``seconds`` have passed (or exactly ``steps``), one thread."""
+def _time_oracle_on(sample, run, seconds, steps=None):
+    """Oracle steps on ``sample`` in chunks until ``seconds`` have passed (or
+    exactly ``steps``); returns (particle-steps/s, steps, seconds)."""
     import oracle
-    oracle.build()
-    sample, nrep = oracle_sample(system)
     ens = run["ensemble"]
     th = None
     done, chunk = 0, 5
@@ -312,10 +310,38 @@ def time_oracle(system, run, seconds, steps=None):
         th = st["thermo"]
         done += k
     dt = time.perf_counter() - t0
-    return {"value": sample.n * done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nrep} replicas ({sample.n} particles, first replicas of the workload, "
-                      f"generator-made start at target density), {done} FP64 steps, "
-                      f"single thread, {dt:.1f} s"}
+    return sample.n * done / dt, done, dt
+
+
+def time_oracle(system, run, seconds, steps=None):
+    """The FP64 oracle on a bounded sample of the workload, on the host cores.
+    value: the oracle as it stands (every pair, one thread).  all_cores: the
+    same oracle with its timing options, a cell-list pair search and OpenMP
+    over particles on every core (nproc), on a larger sample of the same
+    workload (the same pairs and terms; tests/test_oracle_parallel.py)."""
+    import oracle
+    oracle.build()
+    nproc = os.cpu_count() or 1
+    sample, nrep = oracle_sample(system)
+    oracle.set_parallel(1, False)
+    v1, done1, dt1 = _time_oracle_on(sample, run, 0.5 * seconds, steps)
+    out = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{nrep} replicas ({sample.n} particles, first replicas of the workload, "
+                     f"generator-made start at target density), {done1} FP64 steps, every "
+                     f"pair, single thread, {dt1:.1f} s",
+           "nproc": nproc}
+    big, nrep_b = oracle_sample(system, target_particles=4 * sample.n)
+    try:
+        oracle.set_parallel(nproc, True)
+        threads = min(nproc, oracle.max_threads())
+        vm, donem, dtm = _time_oracle_on(big, run, 0.5 * seconds, steps)
+    finally:
+        oracle.set_parallel(1, False)
+    out["all_cores"] = {
+        "value": vm, "unit": UNIT, "cores": threads, "kind": "oracle (cell list, OpenMP)",
+        "sample": f"{nrep_b} replicas ({big.n} particles), {donem} FP64 steps, cell-list pair "
+                  f"search, OpenMP over particles on {threads} threads, {dtm:.1f} s"}
+    return out
 
 
 # ---------------------------------------------------------------------------

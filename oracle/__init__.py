@@ -14,6 +14,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                   reversibility, dt^2 scaling of the NVE energy error,
                   conserved NVT quantity and equipartition.
   primitives      pinned: dense brute-force sampling.
+  set_parallel()  timed CPU baseline only: the same pairs and terms through a
+                  cell list and OpenMP threads; pinned against the plain
+                  evaluation (tests/test_oracle_parallel.py).
 """
 from .oracle import (build, lib_path, pack_shapes, forces, run, point_segment,  # noqa: F401
-                     point_face, segment_segment, wca, DEFAULT_PAR_EPS)
+                     point_face, segment_segment, wca, set_parallel, max_threads,
+                     DEFAULT_PAR_EPS)

@@ -395,7 +395,7 @@ static v3 position(int dim, const double *pos, int i) {
     return mk(pos[dim * i], pos[dim * i + 1], dim == 3 ? pos[dim * i + 2] : 0.0);
 }
 
-static int forces_with_shapes(int dim, const shape_t *shapes, double eps, double sigma,
+static int forces_all_pairs(int dim, const shape_t *shapes, double eps, double sigma,
                               double par_eps, int n, const int *shape_id, const double *pos,
                               const double *orient, const double *box, double *force,
                               double *torque, double *energy, double *virial, double *fscale,
@@ -429,6 +429,167 @@ static int forces_with_shapes(int dim, const shape_t *shapes, double eps, double
         }
     }
     return 0;
+}
+
+
+/* ---------------------------------------------------------------------- */
+/* Timed CPU baseline only: cell-list pair search, OpenMP over particles  */
+/* ---------------------------------------------------------------------- */
+/* The benchmark times the oracle on the host cores in two forms: as it
+ * stands (all pairs, one thread), and with the pair search restricted to a
+ * cell list and the particles shared among OpenMP threads.  The second form
+ * evaluates exactly the same pairs and terms (every pair the cell list
+ * skips is beyond R_i + R_j + r_cut, the exact skip above; every pair is
+ * taken with its lower index first, so the parallel-edge rule keeps its
+ * reference) and differs only in the order of the floating-point sums.
+ * The tests use the first form; oracle_set_parallel selects the second. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 1, g_cells = 0;
+
+void oracle_set_parallel(int threads, int use_cells) {
+    g_threads = threads > 0 ? threads : 1;
+    g_cells = use_cells != 0;
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int forces_parallel(int dim, const shape_t *shapes, double eps, double sigma,
+                           double par_eps, int n, const int *shape_id, const double *pos,
+                           const double *orient, const double *box, double *force,
+                           double *torque, double *energy, double *virial, long long *counts) {
+    int tdim = dim == 3 ? 3 : 1;
+    int nth = g_threads;
+#ifndef _OPENMP
+    nth = 1;
+#endif
+    /* cells of width >= the largest interaction range, >= 3 per axis, else
+     * every pair */
+    double Rmax = 0.0, rnd_max = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const shape_t *sh = &shapes[shape_id[i]];
+        if (sh->R > Rmax) Rmax = sh->R;
+        if (sh->rounding > rnd_max) rnd_max = sh->rounding;
+    }
+    double range = 2.0 * Rmax + pow(2.0, 1.0 / 6.0) * (sigma > 0.0 ? sigma : 2.0 * rnd_max);
+    int nc[3] = {1, 1, 1}, use_cells = g_cells;
+    for (int a = 0; a < dim; ++a) {
+        nc[a] = (int)floor(box[a] / (range * (1.0 + 1e-9)));
+        if (nc[a] < 3) use_cells = 0;
+    }
+    int ncell = nc[0] * nc[1] * nc[2];
+    int *head = NULL, *next = NULL, *cell = NULL;
+    if (use_cells) {
+        head = (int *)malloc(sizeof(int) * ncell);
+        next = (int *)malloc(sizeof(int) * n);
+        cell = (int *)malloc(sizeof(int) * n);
+        if (!head || !next || !cell) { free(head); free(next); free(cell); return -2; }
+        for (int c = 0; c < ncell; ++c) head[c] = -1;
+        for (int i = n - 1; i >= 0; --i) {
+            int cc[3] = {0, 0, 0};
+            for (int a = 0; a < dim; ++a) {
+                double x = pos[dim * i + a];
+                x -= box[a] * floor(x / box[a]);
+                int k = (int)(x / box[a] * nc[a]);
+                cc[a] = k < 0 ? 0 : (k >= nc[a] ? nc[a] - 1 : k);
+            }
+            cell[i] = (cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
+            next[i] = head[cell[i]];
+            head[cell[i]] = i;
+        }
+    }
+    /* per-thread accumulators, summed at the end */
+    size_t per = (size_t)dim * n + (size_t)tdim * n + n + 9;
+    double *buf = (double *)calloc((size_t)nth * per, sizeof(double));
+    long long *cnt = (long long *)calloc((size_t)nth * 3, sizeof(long long));
+    if (!buf || !cnt) { free(buf); free(cnt); free(head); free(next); free(cell); return -2; }
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nth) schedule(dynamic, 8)
+#endif
+    for (int i = 0; i < n; ++i) {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double *b = buf + (size_t)t * per;
+        acc_t A = {eps, sigma, par_eps, dim, b, b + (size_t)dim * n,
+                   b + (size_t)dim * n + (size_t)tdim * n, b + (size_t)dim * n + (size_t)tdim * n + n,
+                   NULL, NULL, NULL, cnt + 3 * t};
+        double Ri[3][3];
+        orientation_matrix(dim, orient, i, Ri);
+        const shape_t *si = &shapes[shape_id[i]];
+        /* candidate j > i: every particle, or those of the 27 (9) cells
+         * around i's cell */
+        int cand_cells[27], ncand = 0;
+        if (use_cells) {
+            int ci = cell[i], cx = ci % nc[0], cy = (ci / nc[0]) % nc[1], cz = ci / (nc[0] * nc[1]);
+            for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int x = (cx + dx + nc[0]) % nc[0], y = (cy + dy + nc[1]) % nc[1];
+                        int z = dim == 3 ? (cz + dz + nc[2]) % nc[2] : 0;
+                        cand_cells[ncand++] = (z * nc[1] + y) * nc[0] + x;
+                    }
+        }
+        int kc = 0, j = use_cells ? -1 : i;
+        for (;;) {
+            if (use_cells) {
+                j = j < 0 ? -1 : next[j];
+                while (j < 0 && kc < ncand) j = head[cand_cells[kc++]];
+                if (j < 0) break;
+                if (j <= i) continue;
+            } else {
+                if (++j >= n) break;
+            }
+            const shape_t *sj = &shapes[shape_id[j]];
+            double sigma_ij = sigma > 0.0 ? sigma : si->rounding + sj->rounding;
+            double rcut = pow(2.0, 1.0 / 6.0) * sigma_ij;
+            v3 d = min_image(dim, sub(position(dim, pos, j), position(dim, pos, i)), box);
+            if (!(len(d) < si->R + sj->R + rcut)) continue;
+            A.counts[0]++;
+            double Rj[3][3];
+            orientation_matrix(dim, orient, j, Rj);
+            pair_terms(&A, i, j, si, sj, Ri, Rj, d, sigma_ij);
+        }
+    }
+    memset(force, 0, sizeof(double) * dim * n);
+    memset(torque, 0, sizeof(double) * tdim * n);
+    memset(energy, 0, sizeof(double) * n);
+    memset(virial, 0, sizeof(double) * 9);
+    if (counts) counts[0] = counts[1] = counts[2] = 0;
+    for (int t = 0; t < nth; ++t) {
+        const double *b = buf + (size_t)t * per;
+        for (size_t k = 0; k < (size_t)dim * n; ++k) force[k] += b[k];
+        for (size_t k = 0; k < (size_t)tdim * n; ++k) torque[k] += b[(size_t)dim * n + k];
+        for (int k = 0; k < n; ++k) energy[k] += b[(size_t)dim * n + (size_t)tdim * n + k];
+        for (int k = 0; k < 9; ++k) virial[k] += b[(size_t)dim * n + (size_t)tdim * n + n + k];
+        if (counts)
+            for (int k = 0; k < 3; ++k) counts[k] += cnt[3 * t + k];
+    }
+    free(buf); free(cnt); free(head); free(next); free(cell);
+    return 0;
+}
+
+/* The plain all-pairs evaluation (tests, scales, flags), or the timed
+ * baseline's cell-list / OpenMP form when oracle_set_parallel chose it. */
+static int forces_with_shapes(int dim, const shape_t *shapes, double eps, double sigma,
+                              double par_eps, int n, const int *shape_id, const double *pos,
+                              const double *orient, const double *box, double *force,
+                              double *torque, double *energy, double *virial, double *fscale,
+                              double *tscale, int *flags, long long *counts) {
+    if ((g_threads > 1 || g_cells) && !fscale && !tscale && !flags)
+        return forces_parallel(dim, shapes, eps, sigma, par_eps, n, shape_id, pos, orient, box,
+                               force, torque, energy, virial, counts);
+    return forces_all_pairs(dim, shapes, eps, sigma, par_eps, n, shape_id, pos, orient, box,
+                            force, torque, energy, virial, fscale, tscale, flags, counts);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -31,8 +31,8 @@ def build(force: bool = False) -> str:
     """Compile dem_oracle.c with gcc into oracle/liboracle.so."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC,
-                               "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-o",
+                               tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -58,6 +58,10 @@ def _load():
         lib.oracle_point_face.argtypes = [dp, C.c_int, dp, dp]
         lib.oracle_segment_segment.restype = C.c_double
         lib.oracle_segment_segment.argtypes = [dp, dp, dp, dp, C.c_double, dp, dp, ip]
+        lib.oracle_set_parallel.restype = None
+        lib.oracle_set_parallel.argtypes = [C.c_int, C.c_int]
+        lib.oracle_max_threads.restype = C.c_int
+        lib.oracle_max_threads.argtypes = []
         lib.oracle_wca.restype = C.c_double
         lib.oracle_wca.argtypes = [C.c_double, C.c_double, C.c_double, dp]
         _lib = lib
@@ -255,3 +259,15 @@ def wca(r, eps: float = 1.0, sigma: float = 1.0):
     f = C.c_double(0.0)
     u = lib.oracle_wca(float(r), float(eps), float(sigma), C.byref(f))
     return u, f.value
+
+
+def set_parallel(threads: int = 1, cells: bool = False):
+    """Timed CPU baseline only: evaluate forces with a cell-list pair search
+    and/or OpenMP over particles (same pairs and terms; sums in another
+    order).  set_parallel(1, False) restores the plain oracle the tests use.
+    Per-particle scales and flags always come from the plain evaluation."""
+    _load().oracle_set_parallel(int(threads), int(bool(cells)))
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
