@@ -50,9 +50,9 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 rate (far below the FP32 ra
 # csrc/pair_common.cuh.  Keys are dem_get_counters indices.
 FLOPS_PER_PATH = {
     10: 15,  # list entry: separation d0 + delta_j - delta_i (6) + range test (9)
-    0: 123,  # in-range pair: j's rotation matrix (30), M = R_i^T R_j (45),
-             # dl = R_i^T d (15), sigma terms (2), centre-line axis in both
-             # frames (26) and the separating-axis bounds (5)
+    0: 106,  # in-range pair: relative quaternion conj(q_i) q_j (28), M from
+             # it (30), dl = R_i^T d (15), sigma terms (2), centre-line axis in
+             # both frames (26) and the separating-axis bounds (5)
     16: 5,   # vertex projection onto the centre line
     3: 23,   # vertex transform into the other frame (18) + reach test (5)
     4: 6,    # face-plane signed distance
@@ -72,6 +72,8 @@ WORK_COUNTERS = {0: "pairs", 1: "feature_pairs", 2: "terms", 3: "vertex_transfor
                  10: "list_entries", 11: "inside", 12: "jframe_terms",
                  15: "active_pairs", 16: "sat_projections", 17: "line_tests"}
 TWO_SUM_EXTRA = 30   # compensated sums: 6 components x (6 - 1) extra flops per term
+SPLIT_EXPAND = 32    # SPLIT feature kernel, per active-pair record: M from the
+                     # relative quaternion (30), r_cut and sigma^2 (2)
 
 
 def parse():
@@ -229,10 +231,12 @@ def measured_peaks(dem):
     return out
 
 
-def algorithmic_flops(counts, comp):
+def algorithmic_flops(counts, comp, split=True):
     f = sum(FLOPS_PER_PATH[k] * int(counts[k]) for k in FLOPS_PER_PATH)
     if comp:
         f += TWO_SUM_EXTRA * int(counts[2])
+    if split:
+        f += SPLIT_EXPAND * int(counts[15])
     return f
 
 
@@ -423,7 +427,8 @@ def main():
     value = n_total * a.steps / (t_max / 1e3)
 
     counts = d.counters()
-    flops = algorithmic_flops(counts, prec == dem.DEM_FP32_COMP)
+    flops = algorithmic_flops(counts, prec == dem.DEM_FP32_COMP,
+                              split=decomp_name.startswith("split"))
     achieved = flops / (pair_ms / 1e3) / 1e12
     clocks = clk.summary()
     peaks = measured_peaks(dem)
@@ -532,7 +537,8 @@ def measure_extras(a, dem, d, system, run, ens, prec, torch, peaks):
                 d2.step(5, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])
                 pms = d2.get_param("pair_ms_total") / max(1.0, d2.get_param("pair_launches"))
                 d2.set_param("profile", 0)
-                fl = algorithmic_flops(d2.counters(), False)
+                fl = algorithmic_flops(d2.counters(), False,
+                                       split=int(d2.get_param("decomp")) == 4)
                 ach = fl / (pms / 1e3) / 1e12
                 p64 = peaks["fp64"]["tflops"]
                 out[name]["roofline"] = {

@@ -108,6 +108,24 @@ __device__ __forceinline__ M33<T> orientation_j(const PairArgs &a, int j, const 
     else return orientation<T>(a, j);
 }
 
+// Orientation quaternion (w, x, y, z) of the neighbour of an in-range list
+// entry, and the relative quaternion conj(qa) qb (R(conj(qa) qb) = R_a^T R_b).
+template <class T>
+__device__ __forceinline__ typename R4T<T>::type quat_j(const PairArgs &a, int j,
+                                                        const PairGeom<T> &pg) {
+    if constexpr (std::is_same<T, float>::value) return pg.qj;
+    else return a.quat[j];
+}
+template <class T, class R4>
+__device__ __forceinline__ void relative_quat(const R4 &qa, const R4 &qb, T *q) {
+    const T aw = qa.x, ax = -qa.y, ay = -qa.z, az = -qa.w;   // conj(qa)
+    const T bw = qb.x, bx = qb.y, by = qb.z, bz = qb.w;
+    q[0] = aw * bw - ax * bx - ay * by - az * bz;
+    q[1] = aw * bx + ax * bw + ay * bz - az * by;
+    q[2] = aw * by - ax * bz + ay * bw + az * bx;
+    q[3] = aw * bz + ax * by - ay * bx + az * bw;
+}
+
 template <class T>
 __device__ __forceinline__ Owner<T> make_owner(const PairArgs &a, int i, const ShapeDev &shi,
                                                const Geom &gi) {
@@ -137,6 +155,8 @@ template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return
 template <class T> struct PairWork {
     M33<T> M;            // R_i^T R_j
     V3<T> dl;            // x_j - x_i in i's frame
+    T q[4];              // STAGED / SPLIT: conj(q_i) q_j, whose rotation matrix is M
+    T sig;               // sigma_ij
     T rc, sig2;
     int gj;
     int jref;            // 1 when j < i: j's edge is the parallel-edge rule's reference

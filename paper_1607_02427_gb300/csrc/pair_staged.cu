@@ -56,6 +56,7 @@ template <class T> struct SPair {      // a queued active pair
 };
 template <class T> struct SInfo {      // one particle of the warp
     typename R4T<T>::type row[3];      // (R_i[r][0..2], x[r]); x: FP32 delta_i, FP64 position
+    typename R4T<T>::type q;           // q_i (w, x, y, z)
     T rnd;
     int geom, rep;
     float sc;                          // FP32 list separation scale of the replica
@@ -85,6 +86,20 @@ template <class T, int PR> struct BatchSmem {   // PR: pair ring entries (a powe
     int who[32];                       // pair whose items start at lane k of a round
     unsigned gmask[32];                // per owner: lanes holding its terms
 };
+// An active pair as SPLIT's scan kernel writes it to device memory: the
+// relative orientation as a quaternion instead of M, sigma instead of r_cut
+// and sigma^2, the geometries, owner lane and rule reference packed in one
+// word, and only the vertex masks (the edge and face masks are the features
+// of those vertices).  The feature kernel expands it into an SPair.
+template <class T> struct alignas(16) GRec {
+    T q[4];                            // q_rel = conj(q_i) q_j: M = R(q_rel) = R_i^T R_j
+    T dl[3];                           // x_j - x_i in i's frame
+    T sig;                             // sigma_ij
+    unsigned ids;                      // gi | gj << 8 | owner << 16 | jref << 21
+    unsigned vim, vjm;
+};
+static_assert(MAX_GEOMS <= 256, "GRec packs geometry indices in 8 bits");
+
 template <class T> struct ScanSmem {
     SInfo<T> info[32];
     int offs[32];                      // list offsets of the group's particles
@@ -584,10 +599,12 @@ __device__ __forceinline__ int scan_particle(const PairArgs &a, ScanSmem<T> &ss,
         const float4 dd = a.delta[i];
         store_rows(pi.row, R, v3<float>(dd.x, dd.y, dd.z));
         pi.rnd = shi.rounding_f;
+        pi.q = a.quatf[i];
     } else {
         const double4_32a xx = a.pos[i];
         store_rows(pi.row, R, v3<double>(xx.x, xx.y, xx.z));
         pi.rnd = shi.rounding;
+        pi.q = a.quat[i];
     }
     pi.geom = shi.geom;
     pi.rep = a.rep[i];
@@ -630,8 +647,12 @@ __device__ __forceinline__ bool scan_entry(const PairArgs &a, const typename R4T
     const Geom &gj = geo[pg.gj];
     bump<COUNT>(pc, C_PAIRS);
     bump<COUNT>(pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
-    wk->M = mul_tn(Ri, orientation_j<T>(a, j, pg));
+    // M = R_i^T R_j = R(conj(q_i) q_j): the relative quaternion is what
+    // SPLIT's records carry, and the scan's culls use the same M
+    relative_quat<T>(pi.q, quat_j<T>(a, j, pg), wk->q);
+    wk->M = quat_mat<T>(wk->q[0], wk->q[1], wk->q[2], wk->q[3]);
     wk->dl = mul_t(Ri, pg.d);
+    wk->sig = pg.sig;
     wk->rc = (T)WCA_CUT * pg.sig;
     wk->sig2 = pg.sig * pg.sig;
     wk->gj = pg.gj;
@@ -639,6 +660,40 @@ __device__ __forceinline__ bool scan_entry(const PairArgs &a, const typename R4T
     const bool active = pair_setup<T, COUNT>(tab, itab, gi, gj, wk, pc);
     if (active) bump<COUNT>(pc, C_ACTIVE);
     return active;
+}
+
+template <class T>
+__device__ __forceinline__ void store_grec(GRec<T> &G, const PairWork<T> &wk, int owner, int gi) {
+    G.q[0] = wk.q[0]; G.q[1] = wk.q[1]; G.q[2] = wk.q[2]; G.q[3] = wk.q[3];
+    G.dl[0] = wk.dl.x; G.dl[1] = wk.dl.y; G.dl[2] = wk.dl.z;
+    G.sig = wk.sig;
+    G.ids = (unsigned)gi | (unsigned)wk.gj << 8 | (unsigned)owner << 16 | (unsigned)wk.jref << 21;
+    G.vim = wk.vim;
+    G.vjm = wk.vjm;
+}
+
+// The SPair of a GRec: M from the relative quaternion, r_cut and sigma^2
+// from sigma (the expressions the scan used), the edge and face masks from
+// the vertex masks (the features with a vertex in them, as pair_setup
+// derives them).
+template <class T>
+__device__ __forceinline__ void expand_grec(SPair<T> &P, const GRec<T> &G, const Geom *geo,
+                                            const int *itab) {
+    const M33<T> M = quat_mat<T>(G.q[0], G.q[1], G.q[2], G.q[3]);
+    store_rows(P.row, M, v3<T>(G.dl[0], G.dl[1], G.dl[2]));
+    P.rc = (T)WCA_CUT * G.sig;
+    P.sig2 = G.sig * G.sig;
+    P.gi = (int)(G.ids & 255u);
+    P.gj = (int)((G.ids >> 8) & 255u);
+    P.owner = (int)((G.ids >> 16) & 31u);
+    P.jref = (int)((G.ids >> 21) & 1u);
+    P.vim = G.vim;
+    P.vjm = G.vjm;
+    const Geom &gi = geo[P.gi], &gj = geo[P.gj];
+    P.eim = feature_mask(itab + gi.vem_off, G.vim);
+    P.ejm = feature_mask(itab + gj.vem_off, G.vjm);
+    P.fim = feature_mask(itab + gi.vfm_off, G.vim);
+    P.fjm = feature_mask(itab + gj.vfm_off, G.vjm);
 }
 
 template <class T>
@@ -740,7 +795,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
 // occupancy; the feature kernel keeps the batch stages. ----
 template <class T> struct ScanBlockSmem {
     ScanSmem<T> s;
-    SPair<T> stage[32];                // this chunk's active pairs, in ballot order
+    GRec<T> stage[32];                 // this chunk's active pairs, in ballot order
 };
 
 template <class T, int DIM, bool COUNT>
@@ -759,7 +814,7 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
     PathCount pc;
     if constexpr (COUNT)
         for (int k = 0; k < NCOUNT; ++k) pc.v[k] = 0;
-    constexpr int QW = sizeof(SPair<T>) / sizeof(uint4);
+    constexpr int QW = sizeof(GRec<T>) / sizeof(uint4);
     const int nwarps = gridDim.x * wpb;
     const int G = a.group;   // particles per warp (lanes G..31 hold none)
     for (int base = (blockIdx.x * wpb + w) * G; base < a.n; base += nwarps * G) {
@@ -768,7 +823,7 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
         int total;
         ws.s.offs[lane] = warp_excl_scan(nn_me, lane, &total);
         __syncwarp();
-        uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<SPair<T> *>(a.recs) +
+        uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<GRec<T> *>(a.recs) +
                                                (size_t)g * G * a.cap);
         int cnt = 0;
         for (int t0 = 0; t0 < total; t0 += 32) {
@@ -781,7 +836,7 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
                 active = scan_entry<T, DIM, COUNT>(a, tab, itab, geo, ws.s, base, t, pl, sig_all,
                                                    &wk, &gi, &pc);
             const unsigned m = __ballot_sync(FULL, active);
-            if (active) store_record(ws.stage[__popc(m & ((1u << lane) - 1u))], wk, pl, gi);
+            if (active) store_grec(ws.stage[__popc(m & ((1u << lane) - 1u))], wk, pl, gi);
             __syncwarp();
             // the chunk's records out, one 16-byte word per lane per round
             const uint4 *src = reinterpret_cast<const uint4 *>(ws.stage);
@@ -818,40 +873,50 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
         a.status->rebuild = 0;
     }
     Staged<T, COMP, DIM, COUNT, APPLY_PR> st(a, tab, geo, itab, ws, lane);
-    constexpr int QW = sizeof(SPair<T>) / sizeof(uint4);
+    constexpr int QW = sizeof(GRec<T>) / sizeof(uint4);
+    // the compact records land at the end of the ring's storage, from where
+    // each lane expands one into its SPair slot (all reads before all writes)
+    static_assert(sizeof(GRec<T>) <= sizeof(SPair<T>), "records must fit in the ring");
+    static_assert(sizeof(SPair<T>) % 16 == 0, "ring slots must keep 16-byte alignment");
+    GRec<T> *gbuf = reinterpret_cast<GRec<T> *>(reinterpret_cast<unsigned char *>(ws.pr) +
+                                                APPLY_PR * sizeof(SPair<T>) - APPLY_PR * sizeof(GRec<T>));
     const int nwarps = gridDim.x * wpb;
     const int G = a.group;   // particles per warp (lanes G..31 own none)
     for (int base = (blockIdx.x * wpb + w) * G; base < a.n; base += nwarps * G) {
         const int g = base / G;
         const int cnt = a.rec_count[g];
-        const uint4 *in = reinterpret_cast<const uint4 *>(reinterpret_cast<const SPair<T> *>(a.recs) +
+        const uint4 *in = reinterpret_cast<const uint4 *>(reinterpret_cast<const GRec<T> *>(a.recs) +
                                                           (size_t)g * G * a.cap);
         // the records of this warp's next group into L2 while this one runs
         // (its first 32 records: one 128-byte line per lane at most)
         const int gn = g + nwarps;
         if ((long long)gn * G < a.n) {
             const int cn = min(a.rec_count[gn], 32);
-            const char *nx = reinterpret_cast<const char *>(reinterpret_cast<const SPair<T> *>(a.recs) +
+            const char *nx = reinterpret_cast<const char *>(reinterpret_cast<const GRec<T> *>(a.recs) +
                                                             (size_t)gn * G * a.cap);
-            const int lines = (cn * (int)sizeof(SPair<T>) + 127) / 128;
+            const int lines = (cn * (int)sizeof(GRec<T>) + 127) / 128;
             if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
         }
         st.S.zero();
         for (int b0 = 0; b0 < cnt; b0 += 32) {
             const int nb = cnt - b0 < 32 ? cnt - b0 : 32;
-            // records b0.. into the ring from slot ph (the ring is empty here):
-            // asynchronous 16-byte global-to-shared copies, all in flight at
-            // once, then one wait
-            uint4 *dst = reinterpret_cast<uint4 *>(ws.pr);
+            // records b0.. into the staging area: asynchronous 16-byte
+            // global-to-shared copies, all in flight at once, then one wait
+            uint4 *dst = reinterpret_cast<uint4 *>(gbuf);
             for (int q = lane; q < nb * QW; q += 32) {
-                const int r = q / QW, c = q - r * QW;
-                const unsigned s = (unsigned)__cvta_generic_to_shared(
-                    dst + (size_t)((st.ph + r) & (APPLY_PR - 1)) * QW + c);
+                const unsigned s = (unsigned)__cvta_generic_to_shared(dst + q);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s),
-                             "l"(in + (size_t)(b0 + r) * QW + c)
+                             "l"(in + (size_t)b0 * QW + q)
                              : "memory");
             }
             asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+            __syncwarp();
+            // the ring is empty here: the batch's pairs take slots 0 .. nb-1
+            GRec<T> gr;
+            if (lane < nb) gr = gbuf[lane];
+            __syncwarp();
+            st.ph = 0;
+            if (lane < nb) expand_grec(ws.pr[lane], gr, geo, itab);
             __syncwarp();
             st.np = nb;
             st.batch(nb);
@@ -931,7 +996,7 @@ cudaError_t launch_pair_staged(const PairArgs &a, int precision, bool count, siz
 }
 
 size_t pair_record_bytes(int precision) {
-    return precision == DEM_FP64 ? sizeof(SPair<double>) : sizeof(SPair<float>);
+    return precision == DEM_FP64 ? sizeof(GRec<double>) : sizeof(GRec<float>);
 }
 
 // Particles per warp of the SPLIT kernels: 32, or fewer (16, 8, 4) while

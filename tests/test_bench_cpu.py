@@ -43,8 +43,10 @@ def test_algorithmic_flops():
     for k in bench.FLOPS_PER_PATH:
         counts[k] = 10 + k
     want = sum(bench.FLOPS_PER_PATH[k] * (10 + k) for k in bench.FLOPS_PER_PATH)
-    assert bench.algorithmic_flops(counts, False) == want
-    assert bench.algorithmic_flops(counts, True) == want + bench.TWO_SUM_EXTRA * counts[2]
+    counts[15] = 7
+    assert bench.algorithmic_flops(counts, False, split=False) == want
+    assert bench.algorithmic_flops(counts, True, split=False) == want + bench.TWO_SUM_EXTRA * counts[2]
+    assert bench.algorithmic_flops(counts, False) == want + bench.SPLIT_EXPAND * 7
 
 
 def test_traffic_record_follows_the_source():
