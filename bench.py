@@ -72,6 +72,14 @@ WORK_COUNTERS = {0: "pairs", 1: "feature_pairs", 2: "terms", 3: "vertex_transfor
                  10: "list_entries", 11: "inside", 12: "jframe_terms",
                  15: "active_pairs", 16: "sat_projections", 17: "line_tests"}
 TWO_SUM_EXTRA = 30   # compensated sums: 6 components x (6 - 1) extra flops per term
+# FP32 + two-sum: every term re-evaluated in float-float (csrc/ff.cuh,
+# refined_values), hand-counted in FP32 flops (FMA = 2; ff_add 11, ff_mul 10,
+# ff_mul_f 8, a quaternion rotation 288): four rotations (1152), the
+# separation with its image and sigma_ij (99), the nearest points (a foot on
+# a segment 158; the edge-pair solve 590), rv and r^2 (85), the WCA factor
+# (107), force and torque (123), virial and sums (75).  Counted per term with
+# the foot (1799); edge-pair terms take about 430 more.
+REFINE_PER_TERM = 1799
 SPLIT_EXPAND = 32    # SPLIT feature kernel, per active-pair record: M from the
                      # relative quaternion (30), r_cut and sigma^2 (2)
 
@@ -234,7 +242,7 @@ def measured_peaks(dem):
 def algorithmic_flops(counts, comp, split=True):
     f = sum(FLOPS_PER_PATH[k] * int(counts[k]) for k in FLOPS_PER_PATH)
     if comp:
-        f += TWO_SUM_EXTRA * int(counts[2])
+        f += (TWO_SUM_EXTRA + REFINE_PER_TERM) * int(counts[2])
     if split:
         f += SPLIT_EXPAND * int(counts[15])
     return f

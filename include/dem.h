@@ -65,14 +65,21 @@ extern "C" {
 /* ---- precision modes of the pair kernel ---- */
 #define DEM_FP64 0        /* geometry, force and accumulation in FP64            */
 #define DEM_FP32 1        /* geometry and force in FP32, plain FP32 sums        */
-#define DEM_FP32_COMP 2   /* geometry and force in FP32, compensated (two-sum)
-                             FP32 sums of force and torque                      */
+#define DEM_FP32_COMP 2   /* culls and nearest-point searches in FP32; every term
+                             found (r < r_cut) re-evaluated in float-float (pairs
+                             of floats, about 48 bits) from the FP64 state: its
+                             nearest points, WCA force and torque; compensated
+                             (two-sum) sums of force and torque                 */
 /* In every mode positions, velocities, orientations, angular momenta,
  * per-particle energies and virials are held in FP64.  In the FP32 modes the
  * neighbour list keeps each pair's separation d0 = x_j - x_i of the last
  * list build (taken in FP64, rounded to FP32) and each particle keeps its
  * displacement delta since that build (FP64, rounded to FP32); the pair
- * kernels form x_j - x_i = d0 + delta_j - delta_i in FP32. */
+ * kernels' searches form x_j - x_i = d0 + delta_j - delta_i in FP32.
+ * DEM_FP32_COMP re-evaluates each term from the positions, quaternions and
+ * geometry split into hi + lo floats, so its forces and torques follow the
+ * FP64 definition to about 1e-7 of each particle's own force (DEM_FP32:
+ * about 1e-4 where a particle's terms cancel). */
 
 /* ---- ensembles ---- */
 #define DEM_NVE 0

@@ -377,15 +377,20 @@ void build_tables(const std::vector<HostGeom> &geoms, const std::vector<HostShap
     }
     if (t->itab.empty()) { t->itab.push_back(0); t->itab.push_back(0); }
     t->tf.resize(t->td.size());
-    for (size_t k = 0; k < t->td.size(); ++k)
-        t->tf[k] = make_float4((float)t->td[k].x, (float)t->td[k].y, (float)t->td[k].z,
-                               (float)t->td[k].w);
+    t->tf_lo.resize(t->td.size());
+    for (size_t k = 0; k < t->td.size(); ++k) {
+        float4 h, l;
+        split_ff(t->td[k].x, &h.x, &l.x); split_ff(t->td[k].y, &h.y, &l.y);
+        split_ff(t->td[k].z, &h.z, &l.z); split_ff(t->td[k].w, &h.w, &l.w);
+        t->tf[k] = h;
+        t->tf_lo[k] = l;
+    }
     for (auto &h : hs) {
         ShapeDev sd = {};
         sd.geom = h.geom;
         sd.R = t->geoms[h.geom].R;
         sd.rounding = h.rounding;
-        sd.rounding_f = (float)h.rounding;
+        split_ff(h.rounding, &sd.rounding_f, &sd.rounding_lo);
         sd.mass = h.mass;
         sd.inv_mass = 1.0 / h.mass;
         for (int k = 0; k < 3; ++k) {
@@ -464,12 +469,20 @@ struct dem_ctx {
     double4_32a *pos = nullptr, *vel = nullptr, *quat = nullptr, *angmom = nullptr;
     double4_32a *force = nullptr, *torque = nullptr, *x_last = nullptr;
     float4 *quatf = nullptr;
+    float4 *quatf_lo = nullptr, *xff = nullptr;   // FP32 + two-sum: hi + lo state
+    float4 *d_table_lo = nullptr;                 // FP32 + two-sum: table low parts
     int *shape = nullptr, *rep = nullptr, *nn = nullptr;
     float4 *nlist = nullptr, *delta = nullptr, *posf = nullptr;
     int *cell_count = nullptr, *cell_slots = nullptr;
     double *energy = nullptr, *virial = nullptr, *ke = nullptr, *ket = nullptr;
     void *recs = nullptr;             // SPLIT: active-pair records
     int *rec_count = nullptr;
+    // SPLIT, FP32 + two-sum: the term buffer (term_capw records per warp of
+    // the feature kernel) and each group's first record and count
+    float4 *term_a = nullptr, *term_b = nullptr;
+    int *term_info = nullptr, *term_start = nullptr, *term_cnt = nullptr;
+    int term_capw = 0;
+    size_t term_recs = 0;
     size_t rec_bytes = 0;
     int n_chunks = 0;                 // replica-sum chunks (SUM_CHUNK particles)
     int *chunk_rep = nullptr;
@@ -560,6 +573,11 @@ int upload_tables(dem_ctx *ctx) {
     } else {
         CK(dalloc((float4 **)&ctx->d_table, t.tf.size()));
         CK(cudaMemcpy(ctx->d_table, t.tf.data(), sizeof(float4) * t.tf.size(), cudaMemcpyHostToDevice));
+        if (ctx->precision == DEM_FP32_COMP) {
+            CK(dalloc(&ctx->d_table_lo, t.tf_lo.size()));
+            CK(cudaMemcpy(ctx->d_table_lo, t.tf_lo.data(), sizeof(float4) * t.tf_lo.size(),
+                          cudaMemcpyHostToDevice));
+        }
     }
     CK(dalloc(&ctx->d_shapes, t.shapes.size()));
     CK(cudaMemcpy(ctx->d_shapes, t.shapes.data(), sizeof(ShapeDev) * t.shapes.size(), cudaMemcpyHostToDevice));
@@ -628,6 +646,7 @@ int setup_replicas(dem_ctx *ctx) {
             }
         }
         rp.r_list = rlist;
+        rep_box_ff(rp);
         rp.L_build0 = rp.L[0];
         rp.sc_d = 1.0;
         rp.sc = 1.f;
@@ -706,6 +725,15 @@ PairArgs pair_args(dem_ctx *ctx) {
     a.recs = ctx->recs;
     a.rec_count = ctx->rec_count;
     a.group = ctx_split_group(ctx);
+    if (ctx->precision == DEM_FP32_COMP) {
+        a.quatf_lo = ctx->quatf_lo;
+        a.xff = ctx->xff;
+        a.table_lo = ctx->d_table_lo;
+        split_ff(ctx->sigma > 0 ? ctx->sigma : 0.0, &a.sigma_f, &a.sigma_lo);
+        a.term_a = ctx->term_a; a.term_b = ctx->term_b; a.term_info = ctx->term_info;
+        a.term_start = ctx->term_start; a.term_cnt = ctx->term_cnt;
+        a.term_capw = ctx->term_capw;
+    }
     return a;
 }
 
@@ -730,6 +758,35 @@ int ensure_recs(dem_ctx *ctx, int decomp) {
     }
     // counts for the smallest group size, so that any group size fits
     if (!ctx->rec_count) CK(dalloc(&ctx->rec_count, ((size_t)ctx->N + 3) / 4));
+    if (ctx->precision == DEM_FP32_COMP) {
+        // the term buffer: a region of term_capw records per warp of the
+        // feature kernel.  Start: sixteen terms per particle on average, about
+        // five times what dense fluids of the shapes here produce, so that a
+        // warp whose groups lie in the densest replicas fits; an overflow
+        // grows it and redoes the call.
+        const int maxw = split_apply_max_warps();
+        if (ctx->term_capw == 0)
+            ctx->term_capw = (int)std::max<long long>(512, (16LL * ctx->N + maxw - 1) / maxw);
+        const size_t recs = (size_t)ctx->term_capw * maxw;
+        if (recs > ctx->term_recs) {
+            cudaFree(ctx->term_a); cudaFree(ctx->term_b); cudaFree(ctx->term_info);
+            ctx->term_a = ctx->term_b = nullptr;
+            ctx->term_info = nullptr;
+            ctx->term_recs = 0;
+            if (cudaMalloc(&ctx->term_a, sizeof(float4) * recs) != cudaSuccess ||
+                cudaMalloc(&ctx->term_b, sizeof(float4) * recs) != cudaSuccess ||
+                cudaMalloc(&ctx->term_info, sizeof(int) * recs) != cudaSuccess) {
+                cudaGetLastError();
+                return set_err(ctx, DEM_ERR_NOMEM, "SPLIT needs %zu term records", recs);
+            }
+            ctx->term_recs = recs;
+            free_graph(ctx);
+        }
+        if (!ctx->term_start) {
+            CK(dalloc(&ctx->term_start, ((size_t)ctx->N + 3) / 4));
+            CK(dalloc(&ctx->term_cnt, ((size_t)ctx->N + 3) / 4));
+        }
+    }
     return DEM_OK;
 }
 
@@ -767,6 +824,8 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     // applies the step's second scaling (the NPT kernels take the chunk
     // partials)
     a.direct_sums = !a.npt && ctx->max_rep <= DIRECT_MAX;
+    a.quatf_lo = ctx->quatf_lo;
+    a.xff = ctx->xff;
     return a;
 }
 
@@ -780,7 +839,9 @@ int launch_forces(dem_ctx *ctx, bool count, cudaEvent_t e0 = nullptr, cudaEvent_
     if (e0) CK(cudaEventRecordWithFlags(e0, ctx->stream, cudaEventRecordExternal));
     CK(launch_pair(pair_args(ctx), ctx->precision, ctx->decomp, ctx->block, count, ctx->stream));
     if (e1) CK(cudaEventRecordWithFlags(e1, ctx->stream, cudaEventRecordExternal));
-    ctx->launches += 2 + (ctx->decomp == DEM_DECOMP_SPLIT ? 2 : 1);
+    // SPLIT: scan and feature kernels, and in the FP32 + two-sum mode the term kernel
+    ctx->launches += 2 + (ctx->decomp == DEM_DECOMP_SPLIT
+                              ? (ctx->precision == DEM_FP32_COMP ? 3 : 2) : 1);
     return DEM_OK;
 }
 
@@ -819,9 +880,10 @@ int read_status(dem_ctx *ctx, Status *st) {
 }
 
 int clear_flags(dem_ctx *ctx) {
-    // nlist_overflow, cell_overflow, nonfinite; box_limit
+    // nlist_overflow, cell_overflow, nonfinite; box_limit; term_overflow
     CK(cudaMemsetAsync(&ctx->status->nlist_overflow, 0, 3 * sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(&ctx->status->box_limit, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(&ctx->status->term_overflow, 0, sizeof(int), ctx->stream));
     return DEM_OK;
 }
 
@@ -851,6 +913,11 @@ int grow(dem_ctx *ctx, const Status &st, int *grown) {
         CK(dalloc(&ctx->cell_slots, (size_t)std::max(ctx->n_cells, 1) * ctx->cell_cap));
         *grown = 1;
     }
+    if (st.term_overflow > ctx->term_capw) {
+        // the next ensure_recs allocates the larger buffer
+        ctx->term_capw = st.term_overflow * 3 / 2 + 64;
+        *grown = 1;
+    }
     if (*grown) free_graph(ctx);
     return DEM_OK;
 }
@@ -867,7 +934,8 @@ int compute_forces(dem_ctx *ctx) {
         Status st;
         rc = read_status(ctx, &st);
         if (rc) return rc;
-        if (st.nlist_overflow > ctx->cap || st.cell_overflow > ctx->cell_cap) {
+        if (st.nlist_overflow > ctx->cap || st.cell_overflow > ctx->cell_cap ||
+            st.term_overflow > ctx->term_capw) {
             int grown;
             rc = grow(ctx, st, &grown);
             if (rc) return rc;
@@ -907,7 +975,8 @@ int snapshot(dem_ctx *ctx, bool restore) {
     }
     if (restore) {
         // float copy of the orientations
-        CK(launch_prepare_state(ctx->N, ctx->dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom,
+        CK(launch_prepare_state(ctx->N, ctx->dim, ctx->pos, ctx->quat, ctx->quatf, ctx->quatf_lo,
+                                    ctx->xff, ctx->angmom,
                                 ctx->rep, ctx->d_reps, 0, ctx->stream));
     }
     return DEM_OK;
@@ -1010,7 +1079,9 @@ void dem_destroy(dem_ctx *ctx) {
                     ctx->staging, ctx->red, ctx->scale3, ctx->status, ctx->thermo, ctx->d_reps,
                     ctx->d_shapes, ctx->d_geoms, ctx->d_table, ctx->d_itable, ctx->d_counters,
                     ctx->snap, ctx->snap_thermo, ctx->snap_reps, ctx->ket, ctx->chunk_rep,
-                    ctx->partial, ctx->posf, ctx->recs, ctx->rec_count};
+                    ctx->partial, ctx->posf, ctx->recs, ctx->rec_count, ctx->quatf_lo, ctx->xff,
+                    ctx->d_table_lo, ctx->term_a, ctx->term_b, ctx->term_info, ctx->term_start,
+                    ctx->term_cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
@@ -1092,6 +1163,10 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
         CK(dalloc(&ctx->angmom, n)); CK(dalloc(&ctx->force, n)); CK(dalloc(&ctx->torque, n));
         CK(dalloc(&ctx->x_last, n)); CK(dalloc(&ctx->quatf, n)); CK(dalloc(&ctx->delta, n));
         CK(dalloc(&ctx->posf, n));
+        if (ctx->precision == DEM_FP32_COMP) {
+            CK(dalloc(&ctx->quatf_lo, n));
+            CK(dalloc(&ctx->xff, 2 * n));
+        }
         CK(cudaMemset(ctx->delta, 0, sizeof(float4) * n));
         CK(dalloc(&ctx->shape, n)); CK(dalloc(&ctx->rep, n)); CK(dalloc(&ctx->nn, n));
         CK(dalloc(&ctx->energy, n)); CK(dalloc(&ctx->virial, 6 * n)); CK(dalloc(&ctx->ke, n)); CK(dalloc(&ctx->ket, n));
@@ -1277,7 +1352,8 @@ int dem_set_state(dem_ctx *ctx, const int *shape_id, const double *pos, const do
                                    ctx->quat, ctx->vel, ctx->angmom, ctx->status, ctx->stream));
         }
     }
-    CK(launch_prepare_state((int)n, dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom, ctx->rep,
+    CK(launch_prepare_state((int)n, dim, ctx->pos, ctx->quat, ctx->quatf, ctx->quatf_lo,
+                            ctx->xff, ctx->angmom, ctx->rep,
                             ctx->d_reps, 1, ctx->stream));
     CK(cudaMemsetAsync(ctx->thermo, 0, sizeof(Thermo) * ctx->R, ctx->stream));
     if (same_shapes) {
@@ -1415,7 +1491,8 @@ int step_run(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau
             }
             ctx->prof_n += n;
         }
-        if (st.nlist_overflow > ctx->cap || st.cell_overflow > ctx->cell_cap) {
+        if (st.nlist_overflow > ctx->cap || st.cell_overflow > ctx->cell_cap ||
+            st.term_overflow > ctx->term_capw) {
             int grown;
             rc = grow(ctx, st, &grown);
             if (rc) return rc;
@@ -1596,7 +1673,8 @@ int dem_set_box(dem_ctx *ctx, const double *box) {
     if (rc) { ctx->box = old; setup_replicas(ctx); return rc; }
     CK(cudaMemcpyAsync(ctx->scale3, scale.data(), sizeof(double) * 3 * ctx->R, cudaMemcpyHostToDevice, ctx->stream));
     CK(launch_rescale(ctx->N, ctx->dim, ctx->pos, ctx->x_last, ctx->rep, ctx->scale3, ctx->stream));
-    CK(launch_prepare_state(ctx->N, ctx->dim, ctx->pos, ctx->quat, ctx->quatf, ctx->angmom,
+    CK(launch_prepare_state(ctx->N, ctx->dim, ctx->pos, ctx->quat, ctx->quatf, ctx->quatf_lo,
+                                    ctx->xff, ctx->angmom,
                             ctx->rep, ctx->d_reps, 0, ctx->stream));
     free_graph(ctx);
     rc = force_rebuild(ctx);
@@ -1654,7 +1732,8 @@ int dem_autotune(dem_ctx *ctx) {
             ctx->tune_ms.push_back(-1.f);
             continue;
         }
-        kernels += 4 * (c.decomp == DEM_DECOMP_SPLIT ? 2 : 1);   // warm-up + 3 timed
+        kernels += 4 * (c.decomp == DEM_DECOMP_SPLIT                   // warm-up + 3 timed
+                            ? (ctx->precision == DEM_FP32_COMP ? 3 : 2) : 1);
         PairArgs pa = pair_args(ctx);
         CK(launch_pair(pa, ctx->precision, c.decomp, c.block, false, ctx->stream));   // warm-up
         CK(cudaEventRecord(e0, ctx->stream));

@@ -63,8 +63,15 @@ struct ShapeDev {
     double inv_inertia[3];  // 1 / inertia[k], 0 where inertia[k] = 0
     double inv_mass;
     float rounding_f;    // FP32 copy of rounding for the FP32 kernels
-    float pad;
+    float rounding_lo;   // rounding - rounding_f (FP32 + two-sum refinement)
 };
+
+// An FP64 value as the unevaluated sum of two floats hi + lo.
+__host__ __device__ inline void split_ff(double x, float *h, float *l) {
+    const float hi = (float)x;
+    *h = hi;
+    *l = (float)(x - (double)hi);
+}
 
 struct Rep {
     double L[3];
@@ -81,7 +88,13 @@ struct Rep {
     float disp_pad;      // 0.5 max(0, 1 - sc) r_list, added to displacements in the
                          // rebuild test so that a shrinking box cannot hide a pair
     int chunk_off, n_chunk;   // this replica's reduction chunks (see SUM_CHUNK)
+    float Lf[3], Lf_lo[3];    // L as hi + lo floats (FP32 + two-sum refinement)
 };
+
+// Fill the float-float copies of a replica's box lengths.
+__host__ __device__ inline void rep_box_ff(Rep &rp) {
+    for (int k = 0; k < 3; ++k) split_ff(rp.L[k], &rp.Lf[k], &rp.Lf_lo[k]);
+}
 
 // Per-step replica sums run over fixed chunks of SUM_CHUNK particles (one
 // block each), then over each replica's chunk partials: a fixed order, and
@@ -101,6 +114,8 @@ struct Status {
                              // image allows within the call
     int bad_input;           // 1 + index of a particle whose imported state was not
                              // finite or whose quaternion had zero norm (else 0)
+    int term_overflow;       // SPLIT, FP32 + two-sum: terms a warp needed beyond its
+                             // region of the term buffer (the largest count), else 0
 };
 
 // Per-replica thermostat state (FP64): canonical end-of-step values and the
@@ -145,7 +160,24 @@ struct PairArgs {
     void *recs;
     int *rec_count;
     int group;
+    // FP32 + two-sum refinement of the terms (NULL in the other modes): the
+    // FP64 state split into hi + lo floats
+    const float4 *quatf_lo;  // q - quatf
+    const float4 *xff;       // per particle: (x, y, z) hi, then (x, y, z) lo
+    const float4 *table_lo;  // geometry records minus their FP32 copies
+    float sigma_f, sigma_lo; // the one sigma of all pairs (when sigma > 0)
+    // SPLIT in the FP32 + two-sum mode: the feature kernel writes every term
+    // it finds (features, parameters, pair data) to its warp's region of
+    // term_capw records; a term kernel refines them.  Per group of particles:
+    // the first record and the count.
+    float4 *term_a, *term_b;  // (s, t, r_cut^2, spec code), (dl, j)
+    int *term_info;           // owner | gi << 8 | gj << 16 | jref << 24
+    int *term_start, *term_cnt;
+    int term_capw;
 };
+// Upper bound of the warps of SPLIT's feature kernel (regions of the term
+// buffer), and the launch of its term kernel (FP32 + two-sum).
+int split_apply_max_warps();
 
 // Bytes of one active-pair record of the SPLIT decomposition.
 size_t pair_record_bytes(int precision);
@@ -195,6 +227,7 @@ struct StepArgs {
     double *partial;         // n_chunks * 3 chunk sums: K, K_trans (NPT), Tr W (NPT)
     int direct_sums;         // NVE/NVT, every replica small: k_thermo_end sums the kinetic
                              // energies itself and, under NVT, applies the second scaling
+    float4 *quatf_lo, *xff;  // FP32 + two-sum: hi + lo state (NULL otherwise)
 };
 
 // ---- launch wrappers (pair.cu, nlist.cu, integrate.cu) ----
@@ -223,6 +256,7 @@ cudaError_t launch_kinetic(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_replica_sums(int n_reps, const Rep *reps, const double *per_particle,
                                 int stride, int comps, double *out, cudaStream_t s);
 cudaError_t launch_prepare_state(int n, int dim, double4_32a *pos, double4_32a *quat, float4 *quatf,
+                                 float4 *quatf_lo, float4 *xff,
                                  double4_32a *angmom, const int *rep, const Rep *reps,
                                  int world_to_body, cudaStream_t s);
 cudaError_t launch_export_state(int n, int dim, const double4_32a *pos, const double4_32a *quat,
@@ -242,6 +276,7 @@ cudaError_t launch_rescale(int n, int dim, double4_32a *pos, double4_32a *x_last
 // Geometry tables of a shape set built on the host, in the layout the pair
 // kernels read (api.cu).
 struct HostTables {
+    std::vector<float4> tf_lo;    // td - tf per component (FP32 + two-sum refinement)
     int dim = 3;
     std::vector<float4> tf;
     std::vector<double4_32a> td;

@@ -180,6 +180,20 @@ __device__ __forceinline__ void max_to_status(const StepArgs &a, float dmax) {
         atomicMax(&a.status->maxdisp2, __float_as_uint(dmax));
 }
 
+// FP32 + two-sum mode: the position and the quaternion as hi + lo floats
+// (the hi part of the quaternion is quatf).
+__device__ __forceinline__ void store_ff_state(float4 *quatf_lo, float4 *xff, int i,
+                                               const double4_32a &x, const double4_32a &q) {
+    float h, l[4];
+    split_ff(q.x, &h, &l[0]); split_ff(q.y, &h, &l[1]);
+    split_ff(q.z, &h, &l[2]); split_ff(q.w, &h, &l[3]);
+    quatf_lo[i] = make_float4(l[0], l[1], l[2], l[3]);
+    float xh[3], xl[3];
+    split_ff(x.x, &xh[0], &xl[0]); split_ff(x.y, &xh[1], &xl[1]); split_ff(x.z, &xh[2], &xl[2]);
+    xff[2 * i] = make_float4(xh[0], xh[1], xh[2], 0.f);
+    xff[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.f);
+}
+
 __global__ void k_first_half(const StepArgs a) {
     float dmax = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
@@ -231,6 +245,7 @@ __global__ void k_first_half(const StepArgs a) {
         a.angmom[i] = L;
         a.quat[i] = q;
         a.quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+        if (a.quatf_lo) store_ff_state(a.quatf_lo, a.xff, i, x, q);
         dmax = fmaxf(dmax, since_build(a, rp, i, x));
     }
     max_to_status(a, dmax);
@@ -500,6 +515,7 @@ __global__ void k_box(const StepArgs a) {
         if (!(rp.L[k] >= 2.0 * rp.r_list) || (!rp.allpairs && rp.L[k] < rp.nc[k] * rp.r_list))
             a.status->box_limit = 1;
     }
+    rep_box_ff(rp);
     const double sc = rp.L[0] / rp.L_build0;
     rp.sc_d = sc;
     rp.sc = (float)sc;
@@ -541,7 +557,8 @@ __device__ __forceinline__ M3 qmat(const double4_32a &q) {
 }
 
 __global__ void k_prepare(int n, int dim, double4_32a *pos, double4_32a *quat, float4 *quatf,
-                          double4_32a *angmom, const int *rep, const Rep *reps, int world_to_body) {
+                          float4 *quatf_lo, float4 *xff, double4_32a *angmom, const int *rep,
+                          const Rep *reps, int world_to_body) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Rep &rp = reps[rep[i]];
         double4_32a x = pos[i];
@@ -554,6 +571,7 @@ __global__ void k_prepare(int n, int dim, double4_32a *pos, double4_32a *quat, f
         q.x /= nq; q.y /= nq; q.z /= nq; q.w /= nq;
         quat[i] = q;
         quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+        if (quatf_lo) store_ff_state(quatf_lo, xff, i, x, q);
         if (world_to_body) {
             double4_32a L = angmom[i];
             if (dim == 3) {
@@ -760,10 +778,11 @@ cudaError_t launch_replica_sums(int n_reps, const Rep *reps, const double *per_p
     return cudaGetLastError();
 }
 cudaError_t launch_prepare_state(int n, int dim, double4_32a *pos, double4_32a *quat, float4 *quatf,
+                                 float4 *quatf_lo, float4 *xff,
                                  double4_32a *angmom, const int *rep, const Rep *reps,
                                  int world_to_body, cudaStream_t s) {
-    k_prepare<<<grid_for(n, 256), 256, 0, s>>>(n, dim, pos, quat, quatf, angmom, rep, reps,
-                                               world_to_body);
+    k_prepare<<<grid_for(n, 256), 256, 0, s>>>(n, dim, pos, quat, quatf, quatf_lo, xff, angmom, rep,
+                                               reps, world_to_body);
     return cudaGetLastError();
 }
 cudaError_t launch_import_state(int n, int dim, const double *pos_in, const double *orient_in,

@@ -53,7 +53,11 @@ constexpr size_t OFF_ITAB = OFF_GEOMS + align256(sizeof(Geom) * MAX_GEOMS);
 constexpr size_t OFF_SHAPES = OFF_ITAB + align256(sizeof(int) * MAX_ITAB);
 constexpr size_t OFF_REPREC = OFF_SHAPES + align256(sizeof(ShapeDev) * MAX_SHAPES);
 constexpr size_t OFF_STATUS = OFF_REPREC + align256(sizeof(Rep));
-constexpr size_t SCRATCH_BYTES = OFF_STATUS + align256(sizeof(Status));
+// FP32 + two-sum: the state and the geometry records as hi + lo floats
+constexpr size_t OFF_QUATF_LO = OFF_STATUS + align256(sizeof(Status));
+constexpr size_t OFF_XFF = OFF_QUATF_LO + align256(sizeof(float4) * MAX_N);
+constexpr size_t OFF_TABLE_LO = OFF_XFF + align256(2 * sizeof(float4) * MAX_N);
+constexpr size_t SCRATCH_BYTES = OFF_TABLE_LO + align256(TABLE_BYTES);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
@@ -182,6 +186,7 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     rp.allpairs = 1;
     rp.g_dof = 0;
     rp.r_list = range;
+    rep_box_ff(rp);
     rp.L_build0 = rp.L[0];
     rp.sc_d = 1.0;
     rp.sc = 1.f;
@@ -211,6 +216,10 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     ShapeDev *sdev = reinterpret_cast<ShapeDev *>(b + OFF_SHAPES);
     Rep *reprec = reinterpret_cast<Rep *>(b + OFF_REPREC);
     Status *status = reinterpret_cast<Status *>(b + OFF_STATUS);
+    const bool ffm = precision == DEM_FP32_COMP;
+    float4 *quatf_lo = ffm ? reinterpret_cast<float4 *>(b + OFF_QUATF_LO) : nullptr;
+    float4 *xff = ffm ? reinterpret_cast<float4 *>(b + OFF_XFF) : nullptr;
+    float4 *table_lo = ffm ? reinterpret_cast<float4 *>(b + OFF_TABLE_LO) : nullptr;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     // shape indices are checked on the host
@@ -227,6 +236,9 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
         NA_CK(cudaMemcpyAsync(table, t.td.data(), sizeof(double4_32a) * t.td.size(), cudaMemcpyHostToDevice, st));
     else
         NA_CK(cudaMemcpyAsync(table, t.tf.data(), sizeof(float4) * t.tf.size(), cudaMemcpyHostToDevice, st));
+    if (ffm)
+        NA_CK(cudaMemcpyAsync(table_lo, t.tf_lo.data(), sizeof(float4) * t.tf_lo.size(),
+                              cudaMemcpyHostToDevice, st));
     NA_CK(cudaMemcpyAsync(geoms, t.geoms.data(), sizeof(Geom) * t.geoms.size(), cudaMemcpyHostToDevice, st));
     NA_CK(cudaMemcpyAsync(itab, t.itab.data(), sizeof(int) * t.itab.size(), cudaMemcpyHostToDevice, st));
     NA_CK(cudaMemcpyAsync(sdev, t.shapes.data(), sizeof(ShapeDev) * t.shapes.size(), cudaMemcpyHostToDevice, st));
@@ -240,7 +252,7 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     // pack the state, all-pairs list, pair kernel, world-frame outputs
     NA_CK(launch_import_state(n, dim, pos, orient, nullptr, nullptr, pos4, quat4, nullptr, nullptr,
                               status, st));
-    NA_CK(launch_prepare_state(n, dim, pos4, quat4, quatf, nullptr, rep, reprec, 0, st));
+    NA_CK(launch_prepare_state(n, dim, pos4, quat4, quatf, quatf_lo, xff, nullptr, rep, reprec, 0, st));
     NlistArgs na = {};
     na.n = n; na.dim = dim; na.cap = CAP; na.cell_cap = 0;
     na.pos = pos4; na.shape = shp; na.rep = rep; na.reps = reprec; na.shapes = sdev;
@@ -262,6 +274,12 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     pa.force = force4; pa.torque = torque4; pa.energy = en; pa.virial = vir;
     pa.eps = epsilon; pa.sigma = sigma > 0 ? sigma : 0.0; pa.par_eps = 1e-6;
     pa.status = status; pa.counters = nullptr;
+    if (ffm) {
+        pa.quatf_lo = quatf_lo;
+        pa.xff = xff;
+        pa.table_lo = table_lo;
+        split_ff(sigma > 0 ? sigma : 0.0, &pa.sigma_f, &pa.sigma_lo);
+    }
     NA_CK(launch_pair(pa, precision, DEM_DECOMP_THREAD, 0, false, st));
     NA_CK(launch_export_forces(n, dim, force4, torque4, quat4, force, torque, st));
     if (energy) NA_CK(cudaMemcpyAsync(energy, en, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));

@@ -87,9 +87,12 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
             w.sig2 = pg.sig * pg.sig;
             w.gj = pg.gj;
             w.jref = j < i;
+            w.i = i;
+            w.j = j;
             if (!pair_setup<T, COUNT>(tab, itab, gi, gj, &w, &pc)) continue;
             bump<COUNT>(&pc, C_ACTIVE);
-            eval_pair<T, DIM, COUNT>(tab, itab, gi, gj, w, eps, par_eps, S, &pc);
+            eval_pair<T, DIM, COUNT, COMP && std::is_same<T, float>::value>(tab, itab, gi, gj, w, eps,
+                                                                            par_eps, S, &pc, &a);
         }
         finish_particle(a, i, S, Ri);
     }
@@ -127,6 +130,7 @@ template <class T> struct alignas(16) QPair {
     int gj, owner;       // owner: the particle's lane in the warp
     unsigned vim, vjm, eim, ejm, fim, fjm;
     int jref;            // j < i: j's edge is the parallel-edge rule's reference
+    int j;               // the neighbour (FP32 + two-sum refinement)
 };
 template <class T> struct alignas(16) PInfo {   // one particle of the warp
     T r[9];              // R_i
@@ -142,11 +146,16 @@ template <class T> struct WarpSmem {
 };
 
 // lane add its pairs' partials in queue order.
+// In the FP32 + two-sum mode a pair's partials are float-float for force and
+// torque: the 6 leading parts go to m[0..5], their compensations to
+// m[6..11], and the 7 other sums to rc, sig2 and the first five masks.
 template <class T, bool COMP, int DIM, bool COUNT>
 __device__ __forceinline__ void run_batch(WarpSmem<T> &ws, int qh, int nb, int lane,
                                           const typename R4T<T>::type *tab, const int *itab,
                                           const Geom *geo, T eps, T par_eps,
-                                          SumSink<T, COMP> &S, PathCount *pc) {
+                                          SumSink<T, COMP> &S, PathCount *pc, const PairArgs &a,
+                                          int base) {
+    constexpr bool REF = COMP && std::is_same<T, float>::value;
     if (lane < nb) {
         QPair<T> &qp = ws.q[(qh + lane) & (PQ - 1)];
         PairWork<T> w;
@@ -161,23 +170,54 @@ __device__ __forceinline__ void run_batch(WarpSmem<T> &ws, int qh, int nb, int l
         w.vim = qp.vim; w.vjm = qp.vjm; w.eim = qp.eim; w.ejm = qp.ejm;
         w.fim = qp.fim; w.fjm = qp.fjm;
         w.jref = qp.jref;
-        PartSink<T> part;
-        part.zero();
-        eval_pair<T, DIM, COUNT>(tab, itab, geo[ws.p[qp.owner].geom], geo[qp.gj], w, eps, par_eps,
-                                 part, pc);
+        w.i = base + qp.owner;
+        w.j = qp.j;
+        if constexpr (REF) {
+            FFPartSink part;
+            part.zero();
+            eval_pair<T, DIM, COUNT, true>(tab, itab, geo[ws.p[qp.owner].geom], geo[qp.gj], w, eps,
+                                           par_eps, part, pc, &a);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) qp.m[k] = part.v[k];
-        qp.rc = part.v[12];
+            for (int k = 0; k < 6; ++k) {
+                qp.m[k] = part.f[k].s;
+                qp.m[6 + k] = part.f[k].c;
+            }
+            qp.rc = part.v[0];
+            qp.sig2 = part.v[1];
+            qp.vim = __float_as_uint(part.v[2]);
+            qp.vjm = __float_as_uint(part.v[3]);
+            qp.eim = __float_as_uint(part.v[4]);
+            qp.ejm = __float_as_uint(part.v[5]);
+            qp.fim = __float_as_uint(part.v[6]);
+        } else {
+            PartSink<T> part;
+            part.zero();
+            eval_pair<T, DIM, COUNT, false>(tab, itab, geo[ws.p[qp.owner].geom], geo[qp.gj], w, eps,
+                                            par_eps, part, pc);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) qp.m[k] = part.v[k];
+            qp.rc = part.v[12];
+        }
     }
     __syncwarp();
     for (int e = 0; e < nb; ++e) {
         const QPair<T> &qp = ws.q[(qh + e) & (PQ - 1)];
         if (qp.owner == lane) {
-            T v[13];
+            if constexpr (REF) {
 #pragma unroll
-            for (int k = 0; k < 12; ++k) v[k] = qp.m[k];
-            v[12] = qp.rc;
-            S.add(v);
+                for (int k = 0; k < 6; ++k) S.v[k].merge(qp.m[k], qp.m[6 + k]);
+                const float rest[7] = {qp.rc, qp.sig2, __uint_as_float(qp.vim), __uint_as_float(qp.vjm),
+                                       __uint_as_float(qp.eim), __uint_as_float(qp.ejm),
+                                       __uint_as_float(qp.fim)};
+#pragma unroll
+                for (int k = 0; k < 7; ++k) S.v[6 + k].add(rest[k]);
+            } else {
+                T v[13];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) v[k] = qp.m[k];
+                v[12] = qp.rc;
+                S.add(v);
+            }
         }
     }
     __syncwarp();
@@ -287,6 +327,7 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
                     wk.sig2 = pg.sig * pg.sig;
                     wk.gj = pg.gj;
                     wk.jref = j < i;
+                    wk.j = j;
                     active = pair_setup<T, COUNT>(tab, itab, gi, gj, &wk, &pc);
                     if (active) bump<COUNT>(&pc, C_ACTIVE);
                 }
@@ -307,15 +348,19 @@ __global__ void __launch_bounds__(128) k_pair_warp(const PairArgs a) {
                 qp.vim = wk.vim; qp.vjm = wk.vjm; qp.eim = wk.eim; qp.ejm = wk.ejm;
                 qp.fim = wk.fim; qp.fjm = wk.fjm;
                 qp.jref = wk.jref;
+                qp.j = wk.j;
             }
             qt += __popc(m);
             __syncwarp();
             if (qt - qh >= 32) {
-                run_batch<T, COMP, DIM, COUNT>(ws, qh, 32, lane, tab, itab, geo, eps, par_eps, S, &pc);
+                run_batch<T, COMP, DIM, COUNT>(ws, qh, 32, lane, tab, itab, geo, eps, par_eps, S, &pc,
+                                               a, base);
                 qh += 32;
             }
         }
-        if (qt > qh) run_batch<T, COMP, DIM, COUNT>(ws, qh, qt - qh, lane, tab, itab, geo, eps, par_eps, S, &pc);
+        if (qt > qh)
+            run_batch<T, COMP, DIM, COUNT>(ws, qh, qt - qh, lane, tab, itab, geo, eps, par_eps, S, &pc,
+                                           a, base);
         if (mine) finish_particle(a, i_me, S, Rme);
         __syncwarp();
     }

@@ -11,6 +11,7 @@
 #pragma once
 
 #include "dem_internal.cuh"
+#include "ff.cuh"
 
 namespace dem {
 
@@ -114,6 +115,14 @@ template <> struct Acc<float, true> {
     }
     __device__ __forceinline__ float comp() const { return c; }
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+    // a float-float addend h + l: h by two-sum, l into the compensation
+    __device__ __forceinline__ void add_ff(ff x) {
+        float t = __fadd_rn(s, x.h);
+        float bp = __fsub_rn(t, s);
+        float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x.h, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(e, x.l));
+    }
 };
 
 // WCA of one feature pair (Eq. LJ, Eq. WCA) at squared nearest-point distance
@@ -165,31 +174,40 @@ __device__ __forceinline__ void bump(PathCount *pc, int k, unsigned int n = 1) {
 // convex polygon lies on such an edge).
 // The nearest point after a passed plane test (nf the face record, h the
 // signed plane distance of p).
+// Where the nearest point of a vertex-face term lies: inside the face (the
+// projection), or on face edge k at parameter t.
+struct FaceHit {
+    int inside, k;
+    float t;
+};
+
 template <class T, bool COUNT, class R4>
 __device__ __forceinline__ void face_rest(const R4 *tab, const int *itab, int face_int,
                                           const R4 &nf, V3<T> p, T h, V3<T> *q, T *r2,
-                                          PathCount *pc);
+                                          PathCount *pc, FaceHit *hit = nullptr);
 
 template <class T, bool COUNT, class R4>
 __device__ __forceinline__ bool face_nearest(const R4 *tab, const int *itab, int face_rec,
                                              int face_int, V3<T> p, T rc, V3<T> *q, T *r2,
-                                             PathCount *pc) {
+                                             PathCount *pc, FaceHit *hit = nullptr) {
     R4 nf = tab[face_rec];
     T h = nf.x * p.x + nf.y * p.y + nf.z * p.z - nf.w;
     bump<COUNT>(pc, C_PLANE);
     if (!(fabs(h) < rc)) return false;
-    face_rest<T, COUNT>(tab, itab, face_int, nf, p, h, q, r2, pc);
+    face_rest<T, COUNT>(tab, itab, face_int, nf, p, h, q, r2, pc, hit);
     return true;
 }
 
 template <class T, bool COUNT, class R4>
 __device__ __forceinline__ void face_rest(const R4 *tab, const int *itab, int face_int,
                                           const R4 &nf, V3<T> p, T h, V3<T> *q, T *r2,
-                                          PathCount *pc) {
+                                          PathCount *pc, FaceHit *hit) {
     int fe = itab[face_int], cnt = itab[face_int + 1];
     bool inside = true;
     T best = T(3.0e38);
     V3<T> bq = p;
+    int bk = 0;
+    T bt = T(0);
     bump<COUNT>(pc, C_INPLANE, (unsigned)cnt);
     for (int k = 0; k < cnt; ++k) {
         R4 m = tab[fe + 3 * k + 2];
@@ -203,7 +221,7 @@ __device__ __forceinline__ void face_rest(const R4 *tab, const int *itab, int fa
             V3<T> c = A + E * t;
             V3<T> dd = p - c;
             T d2 = dot(dd, dd);
-            if (d2 < best) { best = d2; bq = c; }
+            if (d2 < best) { best = d2; bq = c; bk = k; bt = t; }
         }
     }
     if (inside) {
@@ -214,6 +232,7 @@ __device__ __forceinline__ void face_rest(const R4 *tab, const int *itab, int fa
         *q = bq;
         *r2 = best;
     }
+    if (hit) *hit = {inside ? 1 : 0, bk, (float)bt};
 }
 
 // Nearest points of segments [A1, A1 + D1] and [A2, A2 + D2] (inv_a =
@@ -234,7 +253,8 @@ __device__ __forceinline__ void face_rest(const R4 *tab, const int *itab, int fa
 template <class T>
 __device__ __forceinline__ void segment_nearest(V3<T> A1, V3<T> D1, T inv_a, V3<T> A2,
                                                 V3<T> D2, T inv_c, T par_eps, bool ref2,
-                                                V3<T> *P1, V3<T> *P2) {
+                                                V3<T> *P1, V3<T> *P2, T *s_out = nullptr,
+                                                T *t_out = nullptr, int *par_out = nullptr) {
     V3<T> W = A1 - A2;
     T a = dot(D1, D1), b = dot(D1, D2), c = dot(D2, D2);
     T d = dot(D1, W), e = dot(D2, W);
@@ -298,6 +318,9 @@ __device__ __forceinline__ void segment_nearest(V3<T> A1, V3<T> D1, T inv_a, V3<
     }
     *P1 = A1 + D1 * s;
     *P2 = A2 + D2 * t;
+    if (s_out) *s_out = s;
+    if (t_out) *t_out = t;
+    if (par_out) *par_out = den > par_eps * a * c ? 0 : 1;
 }
 
 }  // namespace dem

@@ -7,6 +7,7 @@
 
 #include <type_traits>
 
+#include "ff.cuh"
 #include "pair_common.cuh"
 
 namespace dem {
@@ -155,6 +156,7 @@ template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return
 template <class T> struct PairWork {
     M33<T> M;            // R_i^T R_j
     V3<T> dl;            // x_j - x_i in i's frame
+    int i, j;            // the particles (FP32 + two-sum refinement)
     T q[4];              // STAGED / SPLIT: conj(q_i) q_j, whose rotation matrix is M
     T sig;               // sigma_ij
     T rc, sig2;
@@ -221,6 +223,312 @@ __device__ __forceinline__ bool pair_setup(const typename R4T<T>::type *tab, con
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 + two-sum mode: each term with r < r_cut re-evaluated in float-float
+// ---------------------------------------------------------------------------
+// The search found the term's features and, in FP32, the parameters of its
+// nearest points.  The refinement rebuilds both nearest points in i's body
+// frame from the FP64 state split into hi + lo floats (ff.cuh): j's points
+// are mapped with the quaternions of both particles and the minimum-image
+// separation, x_i + R_i p_i = x_j + R_j p_j taken in float-float.  The
+// search's parameters decide only the branch: a parameter it clamped to an
+// end of its segment is exact, an interior one is recomputed in float-float
+// as the search defined it (the foot of a perpendicular, the stationary
+// point of an edge pair, the midpoint of the parallel-edge rule's overlap).
+// The distance is stationary in those parameters, but the lever arm of the
+// torque is not: its error would be first order in them.
+enum TermKind {
+    TK_SPH = 0,    // one-vertex shapes: the centres' vertices
+    TK_VF_I = 1,   // vertex b of j against face a of i
+    TK_VF_J = 2,   // vertex a of i against face b of j
+    TK_EE = 3,     // edge a of i at s against edge b of j at t
+    TK_VE_I = 4,   // 2D: vertex b of j against edge a of i at t
+    TK_VE_J = 5    // 2D: vertex a of i against edge b of j at t
+};
+struct TermSpec {
+    int kind, a, b;
+    FaceHit hit;       // vertex-face terms: inside the face, or face edge k at t;
+                       // edge pairs: hit.inside = 1 when the parallel-edge rule applied
+    float s, t;
+    int jref;          // j's edge is the rule's reference (j < i)
+};
+
+struct FFPair {
+    ff qiw, qjw;       // quaternions (w, u) of i and j
+    ff3 qiu, qju;
+    ff3 d;             // x_j - x_i (minimum image), world frame
+    ff sig2;           // sigma_ij^2
+};
+
+__device__ __forceinline__ ff min_image_ff(ff x, float L, float L_lo) {
+    const float n = rintf(__fdiv_rn(x.h, L));
+    return n != 0.f ? ff_sub(x, ff_mul_f(ff{L, L_lo}, n)) : x;
+}
+
+__device__ __forceinline__ FFPair load_ffpair(const PairArgs &a, int i, int j) {
+    FFPair p;
+    const float4 qih = a.quatf[i], qil = a.quatf_lo[i], qjh = a.quatf[j], qjl = a.quatf_lo[j];
+    p.qiw = {qih.x, qil.x};
+    p.qiu = {{qih.y, qil.y}, {qih.z, qil.z}, {qih.w, qil.w}};
+    p.qjw = {qjh.x, qjl.x};
+    p.qju = {{qjh.y, qjl.y}, {qjh.z, qjl.z}, {qjh.w, qjl.w}};
+    ff3 d = ff3_of(a.xff[2 * j], a.xff[2 * j + 1]) - ff3_of(a.xff[2 * i], a.xff[2 * i + 1]);
+    const Rep &rp = a.reps[a.rep[i]];
+    // the image is decided on the hi part: the pair is within its range,
+    // well inside half a box, so the choice is never close
+    p.d.x = min_image_ff(d.x, rp.Lf[0], rp.Lf_lo[0]);
+    p.d.y = min_image_ff(d.y, rp.Lf[1], rp.Lf_lo[1]);
+    p.d.z = a.dim == 3 ? min_image_ff(d.z, rp.Lf[2], rp.Lf_lo[2]) : d.z;
+    ff sig;
+    if (a.sigma > 0.0) {
+        sig = {a.sigma_f, a.sigma_lo};
+    } else {
+        const ShapeDev &si = a.shapes[a.shape[i]], &sj = a.shapes[a.shape[j]];
+        sig = ff_add({si.rounding_f, si.rounding_lo}, {sj.rounding_f, sj.rounding_lo});
+    }
+    p.sig2 = ff_mul(sig, sig);
+    return p;
+}
+
+// Geometry records as hi (shared-memory table) + lo (device table)
+struct FFTab {
+    const float4 *tab, *lo;
+    const int *itab;
+    __device__ __forceinline__ ff3 rec(int k) const { return ff3_of(tab[k], lo[k]); }
+    __device__ __forceinline__ ff recw(int k) const { return {tab[k].w, lo[k].w}; }
+    __device__ __forceinline__ ff3 vertex(const Geom &g, int v) const { return rec(g.v_off + v); }
+    // edge e: start A, direction D, 1/|D|^2
+    __device__ __forceinline__ void edge(const Geom &g, int e, ff3 *A, ff3 *D, ff *inv) const {
+        *A = rec(g.e_off + 2 * e);
+        *D = rec(g.e_off + 2 * e + 1);
+        *inv = recw(g.e_off + 2 * e + 1);
+    }
+    // edge k of face f: start A, direction E, 1/|E|^2
+    __device__ __forceinline__ void face_edge(const Geom &g, int f, int k, ff3 *A, ff3 *E,
+                                              ff *inv) const {
+        const int fe = itab[g.fi_off + 2 * f];
+        *A = rec(fe + 3 * k);
+        *E = rec(fe + 3 * k + 1);
+        *inv = recw(fe + 3 * k + 1);
+    }
+    // signed distance of p from face f's plane
+    __device__ __forceinline__ ff plane(const Geom &g, int f, ff3 p, ff3 *n) const {
+        const int k = g.f_off + f;
+        *n = rec(k);
+        return ff_sub(ff3_dot(*n, p), recw(k));
+    }
+};
+
+// j's body point in i's frame, i's body point in j's frame, and j's body
+// directions in i's frame
+__device__ __forceinline__ ff3 to_i(const FFPair &p, ff3 Pj) {
+    return ff3_rotate(p.qiw, p.qiu, p.d + ff3_rotate(p.qjw, p.qju, Pj, false), true);
+}
+__device__ __forceinline__ ff3 to_j(const FFPair &p, ff3 Pi) {
+    return ff3_rotate(p.qjw, p.qju, ff3_rotate(p.qiw, p.qiu, Pi, false) - p.d, true);
+}
+__device__ __forceinline__ ff3 dir_to_i(const FFPair &p, ff3 v) {
+    return ff3_rotate(p.qiw, p.qiu, ff3_rotate(p.qjw, p.qju, v, false), true);
+}
+
+// Parameter of the foot of P on A + u D (inv = 1/|D|^2) in [0, 1]: the
+// search's u is kept when it clamped (an end of the segment), else recomputed.
+__device__ __forceinline__ ff foot(ff3 P, ff3 A, ff3 D, ff inv, float u) {
+    if (!(u > 0.f && u < 1.f)) return ff_of(u);
+    return ff_clamp01(ff_mul(ff3_dot(P - A, D), inv));
+}
+
+// Nearest points of i's edge A1 + s D1 and j's edge A2 + t D2 (both in i's
+// frame) as segment_nearest defines them, with the search's branch.
+__device__ __forceinline__ void refine_edges(ff3 A1, ff3 D1, ff ia, ff3 A2, ff3 D2, ff ic,
+                                             const TermSpec &sp, ff *s, ff *t) {
+    const ff3 W = A1 - A2;
+    const ff b = ff3_dot(D1, D2), d = ff3_dot(D1, W), e = ff3_dot(D2, W);
+    if (sp.hit.inside) {           // the parallel-edge rule: midpoint of the overlap
+        ff t0, t1;
+        if (sp.jref) {
+            t0 = ff_mul(e, ic);
+            t1 = ff_mul(ff_add(e, b), ic);
+        } else {
+            t0 = ff_mul(ff_neg(d), ia);
+            t1 = ff_mul(ff_sub(b, d), ia);
+        }
+        const ff lo = ff_max(ff_of(0.f), ff_min(t0, t1)), hi = ff_min(ff_of(1.f), ff_max(t0, t1));
+        if (!ff_lt(hi, lo)) {
+            const ff mid = ff_scale2(ff_add(lo, hi), 0.5f);
+            if (sp.jref) {
+                *t = mid;
+                *s = ff_clamp01(ff_mul(ff_sub(ff_mul(mid, b), d), ia));
+            } else {
+                *s = mid;
+                *t = ff_clamp01(ff_mul(ff_add(e, ff_mul(mid, b)), ic));
+            }
+            return;
+        }
+        // no overlap: an endpoint pair, below
+    }
+    const bool s_in = sp.s > 0.f && sp.s < 1.f, t_in = sp.t > 0.f && sp.t < 1.f;
+    if (s_in && t_in) {            // the stationary point of the quadratic
+        const ff a = ff3_dot(D1, D1), c = ff3_dot(D2, D2);
+        const ff den = ff_sub(ff_mul(a, c), ff_mul(b, b));
+        *s = ff_div(ff_sub(ff_mul(b, e), ff_mul(c, d)), den);
+        *t = ff_div(ff_sub(ff_mul(a, e), ff_mul(b, d)), den);
+    } else if (s_in) {             // t at an end: the optimal s for it
+        *t = ff_of(sp.t);
+        *s = ff_clamp01(ff_mul(ff_sub(ff_mul(*t, b), d), ia));
+    } else if (t_in) {             // s at an end: the optimal t for it
+        *s = ff_of(sp.s);
+        *t = ff_clamp01(ff_mul(ff_add(e, ff_mul(*s, b)), ic));
+    } else {
+        *s = ff_of(sp.s);
+        *t = ff_of(sp.t);
+    }
+}
+
+// The term's nearest points in i's frame: rv = p_i - p_j and the lever arm
+// p_i (i's point relative to its centre).  Every kind maps one point and one
+// direction of j's feature into i's frame (the costly part: four float-float
+// rotations, the same instructions for every lane of a warp); the kind
+// decides only which records are read and how the nearest points follow.
+__device__ __forceinline__ void refine_points(const FFTab &T, const Geom &gi, const Geom &gj,
+                                              const FFPair &p, const TermSpec &sp, ff3 *rv,
+                                              ff3 *arm) {
+    const ff3 zero = ff3_of(0.f, 0.f, 0.f);
+    ff3 Ai = zero, Di = zero, Pj = zero, Dj = zero;   // i's feature, j's feature (body frames)
+    ff ci = ff_of(0.f), cj = ff_of(0.f);              // 1/|D|^2, or i's plane offset
+    switch (sp.kind) {
+        case TK_SPH:
+            Ai = T.vertex(gi, 0);
+            Pj = T.vertex(gj, 0);
+            break;
+        case TK_VF_I:
+            Pj = T.vertex(gj, sp.b);
+            if (sp.hit.inside) {                      // Ai: i's face normal, ci: offset
+                Ai = T.rec(gi.f_off + sp.a);
+                ci = T.recw(gi.f_off + sp.a);
+            } else {
+                T.face_edge(gi, sp.a, sp.hit.k, &Ai, &Di, &ci);
+            }
+            break;
+        case TK_VF_J:
+            Ai = T.vertex(gi, sp.a);
+            if (sp.hit.inside) {                      // Pj: a point of j's face, Dj: its normal
+                T.face_edge(gj, sp.b, 0, &Pj, &Dj, &cj);
+                Dj = T.rec(gj.f_off + sp.b);
+            } else {
+                T.face_edge(gj, sp.b, sp.hit.k, &Pj, &Dj, &cj);
+            }
+            break;
+        case TK_EE:
+            T.edge(gi, sp.a, &Ai, &Di, &ci);
+            T.edge(gj, sp.b, &Pj, &Dj, &cj);
+            break;
+        case TK_VE_I:
+            T.edge(gi, sp.a, &Ai, &Di, &ci);
+            Pj = T.vertex(gj, sp.b);
+            break;
+        default:   // TK_VE_J
+            Ai = T.vertex(gi, sp.a);
+            T.edge(gj, sp.b, &Pj, &Dj, &cj);
+            break;
+    }
+    // j's point and direction in i's frame: R_i^T (d + R_j Pj), R_i^T R_j Dj.
+    // One rotation body in a loop (r: Pj and Dj by q_j, then both by the
+    // conjugate of q_i): the instruction cache holds it once.
+    ff3 Q = Pj, E = Dj;
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+        const bool jr = r < 2, second = r & 1;
+        const ff w = jr ? p.qjw : p.qiw;
+        ff3 u = jr ? p.qju : p.qiu;
+        if (!jr) u = {ff_neg(u.x), ff_neg(u.y), ff_neg(u.z)};
+        const ff3 v = second ? E : Q;
+        ff3 out = ff3_rotate(w, u, v, false);
+        if (r == 0) out = out + p.d;
+        if (second) E = out;
+        else Q = out;
+    }
+    ff3 pi = Ai, pj = Q;
+    switch (sp.kind) {
+        case TK_VF_I:
+            if (sp.hit.inside) {                      // projection minus the vertex: -h n
+                const ff h = ff_sub(ff3_dot(Ai, Q), ci);
+                *rv = ff3_mul(Ai, ff_neg(h));
+                *arm = Q + *rv;
+                return;
+            }
+            pi = ff3_point(Ai, Di, foot(Q, Ai, Di, ci, sp.hit.t));
+            break;
+        case TK_VF_J:
+            if (sp.hit.inside) {                      // the vertex minus its projection: h n
+                const ff h = ff3_dot(E, Ai - Q);
+                *rv = ff3_mul(E, h);
+                *arm = Ai;
+                return;
+            }
+            pj = ff3_point(Q, E, foot(Ai, Q, E, cj, sp.hit.t));
+            break;
+        case TK_EE: {
+            ff s, t;
+            refine_edges(Ai, Di, ci, Q, E, cj, sp, &s, &t);
+            pi = ff3_point(Ai, Di, s);
+            pj = ff3_point(Q, E, t);
+            break;
+        }
+        case TK_VE_I:
+            pi = ff3_point(Ai, Di, foot(Q, Ai, Di, ci, sp.t));
+            break;
+        case TK_VE_J:
+            pj = ff3_point(Q, E, foot(Ai, Q, E, cj, sp.t));
+            break;
+        default:
+            break;
+    }
+    *rv = pi - pj;
+    *arm = pi;
+}
+
+// The refined term's values: force and torque (i's frame) as float-float,
+// half the energy and the virial as floats.  Returns false when the refined
+// distance is not below r_cut (the search's FP32 test let it through at the
+// edge; its WCA term is zero there).
+__device__ __forceinline__ bool refined_values(const FFTab &T, const Geom &gi, const Geom &gj,
+                                               const FFPair &p, const TermSpec &sp, float rc2,
+                                               float eps, V3<float> dl, ff *vf, float *v) {
+    ff3 rv, arm;
+    refine_points(T, gi, gj, p, sp, &rv, &arm);
+    const ff r2 = ff3_dot(rv, rv);
+    if (!(r2.h < rc2)) return false;
+    const ff ir2 = ff_recip(r2);
+    const ff s2 = ff_mul(p.sig2, ir2);
+    const ff s6 = ff_mul(ff_mul(s2, s2), s2);
+    const ff s12 = ff_mul(s6, s6);
+    const float U = 4.f * eps * ff_to_f(ff_sub(s12, s6)) + eps;
+    const ff wf = ff_mul_f(ff_mul(ff_sub(ff_scale2(s12, 2.f), s6), ir2), 24.f * eps);
+    const ff3 f = ff3_mul(rv, wf);
+    const ff3 tq = ff3_cross(arm, f);
+    vf[0] = f.x; vf[1] = f.y; vf[2] = f.z;
+    vf[3] = tq.x; vf[4] = tq.y; vf[5] = tq.z;
+    v[0] = 0.5f * U;
+    const float fx = ff_to_f(f.x), fy = ff_to_f(f.y), fz = ff_to_f(f.z);
+    const float x = -dl.x, y = -dl.y, z = -dl.z;
+    v[1] = 0.5f * x * fx;
+    v[2] = 0.25f * (x * fy + y * fx);
+    v[3] = 0.25f * (x * fz + z * fx);
+    v[4] = 0.5f * y * fy;
+    v[5] = 0.25f * (y * fz + z * fy);
+    v[6] = 0.5f * z * fz;
+    return true;
+}
+
+// refined_values behind a call: THREAD and WARP evaluate terms from six
+// places, which then share one copy of the code in the instruction cache.
+__device__ __noinline__ bool refined_values_call(const FFTab &T, const Geom &gi, const Geom &gj,
+                                                 const FFPair &p, const TermSpec &sp, float rc2,
+                                                 float eps, V3<float> dl, ff *vf, float *v) {
+    return refined_values(T, gi, gj, p, sp, rc2, eps, dl, vf, v);
+}
+
 // The 13 values of one term: force f and torque pi x f in i's frame, half
 // the energy, the body-frame virial 1/2 sym((-dl) (x) f).
 template <class T>
@@ -241,6 +549,14 @@ __device__ __forceinline__ void term_values(V3<T> pi, V3<T> f, V3<T> dl, T U, T 
 // Sinks of the terms: the particle's compensated sums, or a pair's partial.
 template <class T, bool COMP> struct SumSink {
     Acc<T, COMP> v[13];
+    // a refined term (FP32 + two-sum): force and torque as float-float, the
+    // energy and virial as floats
+    __device__ __forceinline__ void add_ff(const ff *vf, const float *x) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k].add_ff(vf[k]);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[6 + k].add(x[k]);
+    }
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int k = 0; k < 13; ++k) v[k].zero();
@@ -250,6 +566,24 @@ template <class T, bool COMP> struct SumSink {
         for (int k = 0; k < 13; ++k) v[k].add(x[k]);
     }
     __device__ __forceinline__ T total(int k) const { return v[k].s + v[k].comp(); }
+};
+// A pair's partial sums in the FP32 + two-sum mode (WARP decomposition):
+// float-float for force and torque, floats for the rest.
+struct FFPartSink {
+    Acc<float, true> f[6];
+    float v[7];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[k].zero();
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] = 0.f;
+    }
+    __device__ __forceinline__ void add_ff(const ff *vf, const float *x) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[k].add_ff(vf[k]);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] += x[k];
+    }
 };
 template <class T> struct PartSink {
     T v[13];
@@ -264,23 +598,47 @@ template <class T> struct PartSink {
 };
 
 // All terms of an active pair (Eq. DEM / Eq. DEM_2D restricted to the
-// masked features, which carry every non-zero term), in i's frame.
-template <class T, int DIM, bool COUNT, class Sink>
+// masked features, which carry every non-zero term), in i's frame.  REF (the
+// FP32 + two-sum mode): each term found is re-evaluated in float-float
+// (refined_values) and added to the sink as float-float; pa then gives the
+// state, and w.i, w.j the particles.
+template <class T, int DIM, bool COUNT, bool REF, class Sink>
 __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, const int *itab,
                                           const Geom &gi, const Geom &gj, const PairWork<T> &w,
-                                          T eps, T par_eps, Sink &sink, PathCount *pc) {
+                                          T eps, T par_eps, Sink &sink, PathCount *pc,
+                                          const PairArgs *pa = nullptr) {
     using R4 = typename R4T<T>::type;
     const T rc = w.rc, rc2 = rc * rc;
     const V3<T> dl = w.dl;
     T U, wf, tv[13];
+    FFPair fp;
+    FFTab ft;
+    if constexpr (REF) {
+        fp = load_ffpair(*pa, w.i, w.j);
+        ft = {reinterpret_cast<const float4 *>(tab), pa->table_lo, itab};
+    }
+    auto refined = [&](int kind, int fa, int fb, FaceHit hit, float ps, float pt) {
+        if constexpr (REF) {
+            const TermSpec sp = {kind, fa, fb, hit, ps, pt, w.jref};
+            ff vf[6];
+            float v[7];
+            if (refined_values_call(ft, gi, gj, fp, sp, (float)rc2, (float)eps, dl, vf, v))
+                sink.add_ff(vf, v);
+        }
+    };
+    const FaceHit nohit = {0, 0, 0.f};
     if (gi.nv == 1 && gj.nv == 1) {             // sphere / disk limit: central WCA
         const V3<T> pi = xyz<T>(tab[gi.v_off]);
         const V3<T> rv = pi - (dl + mul(w.M, xyz<T>(tab[gj.v_off])));
         const T r2 = dot(rv, rv);
         if (r2 < rc2) {
-            wf = wca_factor(r2, w.sig2, eps, &U);
-            term_values(pi, rv * wf, dl, U, tv);
-            sink.add(tv);
+            if constexpr (REF) {
+                refined(TK_SPH, 0, 0, nohit, 0.f, 0.f);
+            } else {
+                wf = wca_factor(r2, w.sig2, eps, &U);
+                term_values(pi, rv * wf, dl, U, tv);
+                sink.add(tv);
+            }
             bump<COUNT>(pc, C_TERMS);
         }
         return;
@@ -297,12 +655,18 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                 const int f = __ffs(mf) - 1;
                 V3<T> q;
                 T r2;
-                if (!face_nearest<T, COUNT>(tab, itab, gi.f_off + f, gi.fi_off + 2 * f, p, rc, &q, &r2, pc))
+                FaceHit hit;
+                if (!face_nearest<T, COUNT>(tab, itab, gi.f_off + f, gi.fi_off + 2 * f, p, rc, &q, &r2, pc,
+                                            &hit))
                     continue;
                 if (r2 < rc2) {
-                    wf = wca_factor(r2, w.sig2, eps, &U);
-                    term_values(q, (q - p) * wf, dl, U, tv);
-                    sink.add(tv);
+                    if constexpr (REF) {
+                        refined(TK_VF_I, f, b, hit, 0.f, 0.f);
+                    } else {
+                        wf = wca_factor(r2, w.sig2, eps, &U);
+                        term_values(q, (q - p) * wf, dl, U, tv);
+                        sink.add(tv);
+                    }
                     bump<COUNT>(pc, C_TERMS);
                 }
             }
@@ -316,13 +680,18 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                 bump<COUNT>(pc, C_SPHERE);
                 if (!(dot(c, c) < lim * lim)) continue;
                 bump<COUNT>(pc, C_PTSEG);
-                const V3<T> q = A + D * clamp01(dot(p - A, D) * ed.w);
+                const T t = clamp01(dot(p - A, D) * ed.w);
+                const V3<T> q = A + D * t;
                 const V3<T> rv = q - p;
                 const T r2 = dot(rv, rv);
                 if (r2 < rc2) {
-                    wf = wca_factor(r2, w.sig2, eps, &U);
-                    term_values(q, rv * wf, dl, U, tv);
-                    sink.add(tv);
+                    if constexpr (REF) {
+                        refined(TK_VE_I, e, b, nohit, 0.f, (float)t);
+                    } else {
+                        wf = wca_factor(r2, w.sig2, eps, &U);
+                        term_values(q, rv * wf, dl, U, tv);
+                        sink.add(tv);
+                    }
                     bump<COUNT>(pc, C_TERMS);
                 }
             }
@@ -340,12 +709,18 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                 const int f = __ffs(mf) - 1;
                 V3<T> q;
                 T r2;
-                if (!face_nearest<T, COUNT>(tab, itab, gj.f_off + f, gj.fi_off + 2 * f, p, rc, &q, &r2, pc))
+                FaceHit hit;
+                if (!face_nearest<T, COUNT>(tab, itab, gj.f_off + f, gj.fi_off + 2 * f, p, rc, &q, &r2, pc,
+                                            &hit))
                     continue;
                 if (r2 < rc2) {
-                    wf = wca_factor(r2, w.sig2, eps, &U);
-                    term_values(u, mul(w.M, (p - q) * wf), dl, U, tv);
-                    sink.add(tv);
+                    if constexpr (REF) {
+                        refined(TK_VF_J, ai, f, hit, 0.f, 0.f);
+                    } else {
+                        wf = wca_factor(r2, w.sig2, eps, &U);
+                        term_values(u, mul(w.M, (p - q) * wf), dl, U, tv);
+                        sink.add(tv);
+                    }
                     bump<COUNT>(pc, C_TERMS);
                     bump<COUNT>(pc, C_JTERMS);
                 }
@@ -360,13 +735,18 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                 bump<COUNT>(pc, C_SPHERE);
                 if (!(dot(c, c) < lim * lim)) continue;
                 bump<COUNT>(pc, C_PTSEG);
-                const V3<T> q = A + D * clamp01(dot(p - A, D) * ed.w);
+                const T t = clamp01(dot(p - A, D) * ed.w);
+                const V3<T> q = A + D * t;
                 const V3<T> rv = p - q;
                 const T r2 = dot(rv, rv);
                 if (r2 < rc2) {
-                    wf = wca_factor(r2, w.sig2, eps, &U);
-                    term_values(u, mul(w.M, rv * wf), dl, U, tv);
-                    sink.add(tv);
+                    if constexpr (REF) {
+                        refined(TK_VE_J, ai, e, nohit, 0.f, (float)t);
+                    } else {
+                        wf = wca_factor(r2, w.sig2, eps, &U);
+                        term_values(u, mul(w.M, rv * wf), dl, U, tv);
+                        sink.add(tv);
+                    }
                     bump<COUNT>(pc, C_TERMS);
                     bump<COUNT>(pc, C_JTERMS);
                 }
@@ -401,13 +781,20 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                 if (sep * sep >= rc2 * n2 && n2 > par_eps * dot(D1, D1) * dot(D2, D2)) continue;
                 bump<COUNT>(pc, C_SEGSEG);
                 V3<T> P1, P2;
-                segment_nearest<T>(A1, D1, ad.w, A2, D2, bd.w, par_eps, w.jref != 0, &P1, &P2);
+                T ps, pt;
+                int par;
+                segment_nearest<T>(A1, D1, ad.w, A2, D2, bd.w, par_eps, w.jref != 0, &P1, &P2, &ps,
+                                   &pt, &par);
                 const V3<T> rv = P1 - P2;
                 const T r2 = dot(rv, rv);
                 if (r2 < rc2) {
-                    wf = wca_factor(r2, w.sig2, eps, &U);
-                    term_values(P1, rv * wf, dl, U, tv);
-                    sink.add(tv);
+                    if constexpr (REF) {
+                        refined(TK_EE, ea, eb, FaceHit{par, 0, 0.f}, (float)ps, (float)pt);
+                    } else {
+                        wf = wca_factor(r2, w.sig2, eps, &U);
+                        term_values(P1, rv * wf, dl, U, tv);
+                        sink.add(tv);
+                    }
                     bump<COUNT>(pc, C_TERMS);
                 }
             }

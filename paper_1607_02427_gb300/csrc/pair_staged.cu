@@ -52,7 +52,8 @@ template <class T> struct SPair {      // a queued active pair
     int gj, owner;                     // j's geometry; the owner's lane
     unsigned vim, vjm, eim, ejm, fim, fjm;
     int gi;                            // i's geometry
-    int jref;                          // j < i: j's edge is the parallel-edge rule's reference
+    int jref;                          // bit 0: j < i (j's edge is the parallel-edge rule's
+                                       // reference); bits 1..: j
 };
 template <class T> struct SInfo {      // one particle of the warp
     typename R4T<T>::type row[3];      // (R_i[r][0..2], x[r]); x: FP32 delta_i, FP64 position
@@ -80,7 +81,11 @@ template <class T, int PR> struct BatchSmem {   // PR: pair ring entries (a powe
     } fq;
     struct {                              // terms with r < r_cut
         typename R4T<T>::type q[RING];       // the point on i's feature (i's frame); w: r^2
+                                             // FP32 + two-sum: (s, t, r_cut^2, spec code)
         typename R4T<T>::type rv[RING];      // i's point minus j's point (i's frame); w: pair
+                                             // FP32 + two-sum: (dl, j)
+        int info[RING];                      // FP32 + two-sum: owner | gi << 8 | gj << 16 |
+                                             // jref << 24 (the term outlives its pair's slot)
     } tq;
     int boffs[32];                     // item offsets of the batch's pairs
     int who[32];                       // pair whose items start at lane k of a round
@@ -97,6 +102,7 @@ template <class T> struct alignas(16) GRec {
     T sig;                             // sigma_ij
     unsigned ids;                      // gi | gj << 8 | owner << 16 | jref << 21
     unsigned vim, vjm;
+    int j;                             // the neighbour
 };
 static_assert(MAX_GEOMS <= 256, "GRec packs geometry indices in 8 bits");
 
@@ -160,7 +166,7 @@ template <class T> __device__ __forceinline__ V3<T> pair_dl(const SPair<T> &P) {
 // action per turn: consumers first, so that no ring reaches 64 entries,
 // then steps of the current producer until its ring holds 32 entries or
 // its items are done.
-template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged {
+template <class T, bool COMP, int DIM, bool COUNT, int PR = RING, bool SPILL = false> struct Staged {
     using R4 = typename R4T<T>::type;
     const PairArgs &a;
     const R4 *tab;
@@ -171,6 +177,15 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
     const T eps, par_eps;
     PathCount pc;
     SumSink<T, COMP> S;                // this lane's particle
+    // FP32 + two-sum: the term ring carries each term's features and
+    // parameters (spec_code), and run_terms re-evaluates it in float-float
+    static constexpr bool REF = COMP && std::is_same<T, float>::value;
+    int base = 0;                      // first particle of the warp's group
+    const float4 *tab_lo = nullptr;    // REF: the table's low parts (shared memory)
+    // SPILL (REF in SPLIT's feature kernel): terms go to the warp's region of
+    // the term buffer (tcur records so far) instead of the term ring
+    long long region = 0;
+    int tcur = 0;
     int ph = 0, np = 0;                // pair ring: head, queued pairs
     int fh = 0, ft = 0;                // feature ring (vertex-face or edge items)
     int th = 0, tt = 0;                // term ring
@@ -195,6 +210,42 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
     __device__ __forceinline__ const Geom &geom_i(const SPair<T> &P) { return geo[P.gi]; }
     __device__ __forceinline__ static bool spheres(const Geom &gi, const Geom &gj) {
         return gi.nv == 1 && gj.nv == 1;
+    }
+
+    // term spec (REF): pair | kind << 5 | a << 8 | b << 15 | face edge << 22 | inside << 26
+    __device__ __forceinline__ static int spec_code(int p, int kind, int fa, int fb, FaceHit h) {
+        return p | kind << 5 | fa << 8 | fb << 15 | h.k << 22 | h.inside << 26;
+    }
+    // A refined term's record carries everything run_terms_refined needs from
+    // its pair, so that terms may wait in the ring past their batch (the
+    // refinement then runs on full warps) until the group of particles ends.
+    __device__ __forceinline__ void push_spec(bool ok, int code, float ps, float pt, int p) {
+        const unsigned m = __ballot_sync(FULL, ok);
+        if constexpr (SPILL) {
+            if (ok) {
+                const int k = tcur + __popc(m & ((1u << lane) - 1u));
+                if (k < a.term_capw) {
+                    const SPair<T> &P = pair(p);
+                    const V3<T> dl = pair_dl(P);
+                    const long long r = region + k;
+                    a.term_a[r] = make_float4(ps, pt, (float)(P.rc * P.rc), __int_as_float(code));
+                    a.term_b[r] = make_float4(dl.x, dl.y, dl.z, __int_as_float(P.jref >> 1));
+                    a.term_info[r] = P.owner | P.gi << 8 | P.gj << 16 | (P.jref & 1) << 24;
+                }
+            }
+            tcur += __popc(m);
+            return;
+        }
+        if (ok) {
+            const int s = ring_slot(m, lane, tt);
+            const SPair<T> &P = pair(p);
+            const V3<T> dl = pair_dl(P);
+            ws.tq.q[s] = {ps, pt, (float)(P.rc * P.rc), __int_as_float(code)};
+            ws.tq.rv[s] = {dl.x, dl.y, dl.z, __int_as_float(P.jref >> 1)};
+            ws.tq.info[s] = P.owner | P.gi << 8 | P.gj << 16 | (P.jref & 1) << 24;
+        }
+        tt += __popc(m);
+        __syncwarp();
     }
 
     // ---- ring appends (the caller's loop consumes) ----
@@ -233,6 +284,10 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
     // n queued terms: values in i's frame, added by the owners' lanes in
     // queue order
     __device__ __forceinline__ void run_terms(int n) {
+        if constexpr (REF) {
+            if constexpr (!SPILL) run_terms_refined(n);
+            return;
+        }
         T v[13];
         const bool has = lane < n;
         int owner = 32 + lane;                    // lanes without a term: distinct keys
@@ -267,12 +322,67 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         __syncwarp();
     }
 
+    // REF: n queued term specs, re-evaluated in float-float (refined_values),
+    // added by the owners' lanes in queue order (force and torque as
+    // float-float)
+    __device__ __forceinline__ void run_terms_refined(int n) {
+        ff vf[6];
+        float v[7];
+        const bool has = lane < n;
+        int owner = 32 + lane;                    // lanes without a term: distinct keys
+        bool ok = false;
+        if (has) {
+            const int s = (th + lane) & (RING - 1);
+            const float4 sp = reinterpret_cast<const float4 &>(ws.tq.q[s]);
+            const float4 sr = reinterpret_cast<const float4 &>(ws.tq.rv[s]);
+            const int code = __float_as_int(sp.w), info = ws.tq.info[s];
+            owner = info & 255;
+            const TermSpec ts = {(code >> 5) & 7, (code >> 8) & 127, (code >> 15) & 127,
+                                 {(code >> 26) & 1, (code >> 22) & 15, sp.y}, sp.x, sp.y,
+                                 (info >> 24) & 1};
+            const FFPair fp = load_ffpair(a, base + owner, __float_as_int(sr.w));
+            const FFTab ft = {reinterpret_cast<const float4 *>(tab), tab_lo, itab};
+            ok = refined_values(ft, geo[(info >> 8) & 255], geo[(info >> 16) & 255], fp, ts, sp.z,
+                                (float)eps, v3<float>(sr.x, sr.y, sr.z), vf, v);
+        }
+        if (!ok) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) vf[k] = ff_of(0.f);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) v[k] = 0.f;
+        }
+        th += n;
+        const unsigned grp = __match_any_sync(FULL, owner);
+        if (has && lane == __ffs(grp) - 1) ws.gmask[owner] = grp;
+        __syncwarp();
+        unsigned rest = ws.gmask[lane];
+        const int cnt = __popc(rest);
+        const int rounds = (int)__reduce_max_sync(FULL, (unsigned)cnt);
+        for (int r = 0; r < rounds; ++r) {
+            const int src = rest ? __ffs(rest) - 1 : lane;
+            rest &= rest - 1u;
+            ff xf[6];
+            float x[7];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                xf[k].h = __shfl_sync(FULL, vf[k].h, src);
+                xf[k].l = __shfl_sync(FULL, vf[k].l, src);
+            }
+#pragma unroll
+            for (int k = 0; k < 7; ++k) x[k] = __shfl_sync(FULL, v[k], src);
+            if (r < cnt) S.add_ff(xf, x);
+        }
+        ws.gmask[lane] = 0u;
+        __syncwarp();
+    }
+
     // n queued (vertex, face) candidates: nearest point on the face
     __device__ __forceinline__ void run_faces(int n) {
         bool ok = false;
         V3<T> q = v3<T>(0, 0, 0), rv = q;
         T r2 = T(0);
-        int p = 0;
+        int p = 0, tcode = 0;
+        FaceHit hit = {0, 0, 0.f};
         if (lane < n) {
             const int s = (fh + lane) & (RING - 1);
             const auto ip = ws.fq.vf.p[s];
@@ -286,7 +396,7 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
             V3<T> qq;
             T rr;
             face_rest<T, COUNT>(tab, itab, gf.fi_off + 2 * f, tab[gf.f_off + f], pv, ip.w, &qq, &rr,
-                                &pc);
+                                &pc, &hit);
             if (rr < P.rc * P.rc) {
                 ok = true;
                 r2 = rr;
@@ -294,16 +404,19 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
                 if (side == 0) {
                     q = qq;
                     rv = qq - pv;
+                    tcode = spec_code(p, TK_VF_I, f, vtx, hit);
                 } else {
                     bump<COUNT>(&pc, C_JTERMS);
                     q = xyz<T>(tab[gi.v_off + vtx]);
                     rv = mul(pair_m(P), pv - qq);
+                    tcode = spec_code(p, TK_VF_J, vtx, f, hit);
                 }
             }
         }
         fh += n;
         __syncwarp();
-        push_term(ok, q, rv, r2, p);
+        if constexpr (REF) push_spec(ok, tcode, 0.f, hit.t, p);
+        else push_term(ok, q, rv, r2, p);
     }
 
     // n queued edge pairs: segment-segment nearest points
@@ -311,7 +424,8 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         bool ok = false;
         V3<T> q = v3<T>(0, 0, 0), rv = q;
         T r2 = T(0);
-        int p = 0;
+        int p = 0, tcode = 0, par = 0;
+        T ps = T(0), pt = T(0);
         if (lane < n) {
             const int s = (fh + lane) & (RING - 1);
             const auto a2 = ws.fq.ee.a2[s], d2 = ws.fq.ee.d2[s];
@@ -325,7 +439,8 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
             V3<T> P1, P2;
             bump<COUNT>(&pc, C_SEGSEG);
             segment_nearest<T>(xyz<T>(aa), xyz<T>(ad), ad.w, v3<T>(a2.x, a2.y, a2.z),
-                               v3<T>(d2.x, d2.y, d2.z), inv_c, par_eps, P.jref != 0, &P1, &P2);
+                               v3<T>(d2.x, d2.y, d2.z), inv_c, par_eps, (P.jref & 1) != 0, &P1, &P2,
+                               &ps, &pt, &par);
             const V3<T> d = P1 - P2;
             const T rr = dot(d, d);
             if (rr < P.rc * P.rc) {
@@ -334,11 +449,13 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
                 q = P1;
                 rv = d;
                 r2 = rr;
+                tcode = spec_code(p, TK_EE, ea, eb, FaceHit{par, 0, 0.f});
             }
         }
         fh += n;
         __syncwarp();
-        push_term(ok, q, rv, r2, p);
+        if constexpr (REF) push_spec(ok, tcode, (float)ps, (float)pt, p);
+        else push_term(ok, q, rv, r2, p);
     }
 
     // ---- producers ----
@@ -361,7 +478,8 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
                 if (ok) bump<COUNT>(&pc, C_TERMS);
             }
         }
-        push_term(ok, q, rv, r2, lane);
+        if constexpr (REF) push_spec(ok, spec_code(lane, TK_SPH, 0, 0, FaceHit{0, 0, 0.f}), 0.f, 0.f, lane);
+        else push_term(ok, q, rv, r2, lane);
     }
 
     // item offsets of the batch's pairs for a phase; returns the item count
@@ -447,6 +565,8 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         } else {
             V3<T> q = v3<T>(0, 0, 0), rv = q;
             T r2 = T(0);
+            T tt2 = T(0);
+            int code = 0;
             if (cm) {
                 f = __ffs(cm) - 1;
                 cm &= cm - 1u;
@@ -457,7 +577,8 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
                 bump<COUNT>(&pc, C_SPHERE);
                 if (dot(c, c) < lim * lim) {
                     bump<COUNT>(&pc, C_PTSEG);
-                    const V3<T> qq = A + D * clamp01(dot(va - A, D) * ed.w);
+                    tt2 = clamp01(dot(va - A, D) * ed.w);
+                    const V3<T> qq = A + D * tt2;
                     const V3<T> d = va - qq;
                     r2 = dot(d, d);
                     if (r2 < crc * crc) {
@@ -466,16 +587,19 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
                         if (cside == 0) {
                             q = qq;
                             rv = qq - va;
+                            code = spec_code(cp, TK_VE_I, f, cidx, FaceHit{0, 0, 0.f});
                         } else {
                             bump<COUNT>(&pc, C_JTERMS);
                             const SPair<T> &P = pair(cp);
                             q = xyz<T>(tab[geom_i(P).v_off + cidx]);
                             rv = mul(pair_m(P), d);
+                            code = spec_code(cp, TK_VE_J, cidx, f, FaceHit{0, 0, 0.f});
                         }
                     }
                 }
             }
-            push_term(ok, q, rv, r2, cp);
+            if constexpr (REF) push_spec(ok, code, 0.f, (float)tt2, cp);
+            else push_term(ok, q, rv, r2, cp);
         }
     }
 
@@ -528,6 +652,11 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         push_edge(ok, va, vb, cp | (ea << 5) | (cidx << 10));
     }
 
+    // the terms still queued, at the end of a group of particles
+    __device__ __forceinline__ void flush_terms() {
+        while (tt > th) run_terms(tt - th < 32 ? tt - th : 32);
+    }
+
     // ---- one batch of nb queued pairs ----
     __device__ __forceinline__ void batch(int nb) {
         // phase 0: sphere terms; 1: vertex items; 2: edge items; 3: done
@@ -536,7 +665,9 @@ template <class T, bool COMP, int DIM, bool COUNT, int PR = RING> struct Staged 
         for (;;) {
             // cm changes only in producer turns: one vote serves this turn
             const bool any_cm = __any_sync(FULL, cm);
-            if (tt - th >= 32 || (phase == 3 && tt > th)) {
+            // (refined terms carry their pair's data and may wait for later
+            // batches: flush_terms runs the rest when the group ends)
+            if (tt - th >= 32 || (!REF && phase == 3 && tt > th)) {
                 run_terms(tt - th < 32 ? tt - th : 32);
                 continue;
             }
@@ -657,6 +788,8 @@ __device__ __forceinline__ bool scan_entry(const PairArgs &a, const typename R4T
     wk->sig2 = pg.sig * pg.sig;
     wk->gj = pg.gj;
     wk->jref = j < i;
+    wk->i = i;
+    wk->j = j;
     const bool active = pair_setup<T, COUNT>(tab, itab, gi, gj, wk, pc);
     if (active) bump<COUNT>(pc, C_ACTIVE);
     return active;
@@ -670,6 +803,7 @@ __device__ __forceinline__ void store_grec(GRec<T> &G, const PairWork<T> &wk, in
     G.ids = (unsigned)gi | (unsigned)wk.gj << 8 | (unsigned)owner << 16 | (unsigned)wk.jref << 21;
     G.vim = wk.vim;
     G.vjm = wk.vjm;
+    G.j = wk.j;
 }
 
 // The SPair of a GRec: M from the relative quaternion, r_cut and sigma^2
@@ -686,7 +820,7 @@ __device__ __forceinline__ void expand_grec(SPair<T> &P, const GRec<T> &G, const
     P.gi = (int)(G.ids & 255u);
     P.gj = (int)((G.ids >> 8) & 255u);
     P.owner = (int)((G.ids >> 16) & 31u);
-    P.jref = (int)((G.ids >> 21) & 1u);
+    P.jref = (int)((G.ids >> 21) & 1u) | G.j << 1;
     P.vim = G.vim;
     P.vjm = G.vjm;
     const Geom &gi = geo[P.gi], &gj = geo[P.gj];
@@ -706,7 +840,7 @@ __device__ __forceinline__ void store_record(SPair<T> &P, const PairWork<T> &wk,
     P.vim = wk.vim; P.vjm = wk.vjm; P.eim = wk.eim; P.ejm = wk.ejm;
     P.fim = wk.fim; P.fjm = wk.fjm;
     P.gi = gi;
-    P.jref = wk.jref;
+    P.jref = wk.jref | wk.j << 1;
 }
 
 // Shared-memory tables of a pair block: geometry records, geometries, int
@@ -723,6 +857,19 @@ __device__ __forceinline__ size_t table_layout(const PairArgs &a, unsigned char 
     return (tb + 127) & ~(size_t)127;
 }
 
+// FP32 + two-sum: the table's low parts follow the tables in shared memory
+// (the refinement reads them for every term); returns the bytes they take.
+__device__ __forceinline__ size_t stage_table_lo(const PairArgs &a, unsigned char *at,
+                                                 const float4 **lo) {
+    float4 *dst = reinterpret_cast<float4 *>(at);
+    for (int k = threadIdx.x; k < a.table_len; k += blockDim.x) dst[k] = a.table_lo[k];
+    *lo = dst;
+    return ((size_t)a.table_len * sizeof(float4) + 127) & ~(size_t)127;
+}
+__host__ __device__ size_t table_lo_bytes(const PairArgs &a, bool ref) {
+    return ref ? ((size_t)a.table_len * sizeof(float4) + 127) & ~(size_t)127 : 0;
+}
+
 // ---- STAGED: scan and batches in one kernel ----
 template <class T, bool COMP, int DIM, bool COUNT>
 __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
@@ -732,7 +879,9 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
     R4 *tab;
     Geom *geo;
     int *itab;
-    const size_t tb = table_layout<T>(a, smem, &tab, &geo, &itab);
+    size_t tb = table_layout<T>(a, smem, &tab, &geo, &itab);
+    const float4 *tlo = nullptr;
+    if constexpr (COMP && std::is_same<T, float>::value) tb += stage_table_lo(a, smem + tb, &tlo);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     StagedSmem<T> &ws = reinterpret_cast<StagedSmem<T> *>(smem + tb)[w];
     stage_tables<T>(a, tab, geo, itab);
@@ -744,11 +893,13 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
     }
     const T sig_all = a.sigma > 0.0 ? (T)a.sigma : T(0);
     Staged<T, COMP, DIM, COUNT> st(a, tab, geo, itab, ws.b, lane);
+    st.tab_lo = tlo;
     const int nwarps = gridDim.x * wpb;
     for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
         const int i_me = base + lane;
         const int nn_me = scan_particle<T>(a, ws.s, lane, i_me);
         st.S.zero();
+        st.base = base;
         int total;
         ws.s.offs[lane] = warp_excl_scan(nn_me, lane, &total);
         __syncwarp();
@@ -775,6 +926,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 4 : 2)
             st.np += __popc(m);
             __syncwarp();
         }
+        st.flush_terms();
         if (i_me < a.n) {
             M33<T> R;
             V3<T> x;
@@ -854,8 +1006,101 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
 
 constexpr int APPLY_PR = 32;   // the feature kernel holds one batch of records at a time
 
+// Blocks per SM of the feature kernel: 5 in FP32 (96 registers), 2 in FP64.
+// (In the FP32 + two-sum mode it only records the terms; the term kernel
+// refines them.)
+template <class T, bool COMP> constexpr int apply_blocks() {
+    return std::is_same<T, float>::value ? 5 : 2;
+}
+
+// ---- SPLIT, FP32 + two-sum: the term kernel ----
+// One warp per 32 consecutive particles (32 / G groups of the feature
+// kernel): the groups' terms, 32 at a time, are refined in float-float
+// (refined_values) and added by their owners' lanes in the order the feature
+// kernel found them; then each lane writes its particle's outputs.  The
+// kernel holds only this code, so the refinement runs on full warps out of
+// a small instruction footprint, with its own registers.
+template <int DIM>
+__global__ void __launch_bounds__(SBLOCK, 4) k_pair_terms(const PairArgs a) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    float4 *tab;
+    Geom *geo;
+    int *itab;
+    size_t tb = table_layout<float>(a, smem, &tab, &geo, &itab);
+    const float4 *tlo;
+    stage_table_lo(a, smem + tb, &tlo);
+    stage_tables<float>(a, tab, geo, itab);
+    int *gmask = reinterpret_cast<int *>(smem + tb + table_lo_bytes(a, true)) + 32 * (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    gmask[lane] = 0;
+    __syncthreads();
+    const FFTab ft = {tab, tlo, itab};
+    const float eps = (float)a.eps;
+    const int G = a.group;
+    const int nwarps = gridDim.x * wpb;
+    for (int base = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < a.n; base += nwarps * 32) {
+        SumSink<float, true> S;
+        S.zero();
+        for (int h = 0; h < 32 / G && base + h * G < a.n; ++h) {
+            const int g = base / G + h;
+            const int start = a.term_start[g], cnt = a.term_cnt[g];
+            for (int t0 = 0; t0 < cnt; t0 += 32) {
+                const bool has = t0 + lane < cnt;
+                int owner = 32 + lane;            // lanes without a term: distinct keys
+                bool ok = false;
+                ff vf[6];
+                float v[7];
+                if (has) {
+                    const int r = start + t0 + lane;
+                    const float4 sp = a.term_a[r], sr = a.term_b[r];
+                    const int code = __float_as_int(sp.w), info = a.term_info[r];
+                    owner = h * G + (info & 255);
+                    const TermSpec ts = {(code >> 5) & 7, (code >> 8) & 127, (code >> 15) & 127,
+                                         {(code >> 26) & 1, (code >> 22) & 15, sp.y}, sp.x, sp.y,
+                                         (info >> 24) & 1};
+                    const FFPair fp = load_ffpair(a, base + owner, __float_as_int(sr.w));
+                    ok = refined_values(ft, geo[(info >> 8) & 255], geo[(info >> 16) & 255], fp, ts,
+                                        sp.z, eps, v3<float>(sr.x, sr.y, sr.z), vf, v);
+                }
+                if (!ok) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) vf[k] = ff_of(0.f);
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) v[k] = 0.f;
+                }
+                // each owner's lane adds its terms in order
+                const unsigned grp = __match_any_sync(FULL, owner);
+                if (has && lane == __ffs(grp) - 1) gmask[owner] = (int)grp;
+                __syncwarp();
+                unsigned rest = (unsigned)gmask[lane];
+                const int cntm = __popc(rest);
+                const int rounds = (int)__reduce_max_sync(FULL, (unsigned)cntm);
+                for (int rr = 0; rr < rounds; ++rr) {
+                    const int src = rest ? __ffs(rest) - 1 : lane;
+                    rest &= rest - 1u;
+                    ff xf[6];
+                    float x[7];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        xf[k].h = __shfl_sync(FULL, vf[k].h, src);
+                        xf[k].l = __shfl_sync(FULL, vf[k].l, src);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) x[k] = __shfl_sync(FULL, v[k], src);
+                    if (rr < cntm) S.add_ff(xf, x);
+                }
+                gmask[lane] = 0;
+                __syncwarp();
+            }
+        }
+        const int i = base + lane;
+        if (i < a.n) finish_particle(a, i, S, orientation<float>(a, i));
+        __syncwarp();
+    }
+}
+
 template <class T, bool COMP, int DIM, bool COUNT>
-__global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
+__global__ void __launch_bounds__(SBLOCK, apply_blocks<T, COMP>())
     k_pair_apply(const PairArgs a) {
     using R4 = typename R4T<T>::type;
     extern __shared__ __align__(32) unsigned char smem[];
@@ -863,6 +1108,7 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
     Geom *geo;
     int *itab;
     const size_t tb = table_layout<T>(a, smem, &tab, &geo, &itab);
+    const float4 *tlo = nullptr;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     BatchSmem<T, APPLY_PR> &ws = reinterpret_cast<BatchSmem<T, APPLY_PR> *>(smem + tb)[w];
     stage_tables<T>(a, tab, geo, itab);
@@ -872,7 +1118,10 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
         a.status->maxdisp2 = 0u;
         a.status->rebuild = 0;
     }
-    Staged<T, COMP, DIM, COUNT, APPLY_PR> st(a, tab, geo, itab, ws, lane);
+    constexpr bool REF = COMP && std::is_same<T, float>::value;
+    Staged<T, COMP, DIM, COUNT, APPLY_PR, REF> st(a, tab, geo, itab, ws, lane);
+    st.tab_lo = tlo;
+    if constexpr (REF) st.region = (long long)(blockIdx.x * wpb + w) * a.term_capw;
     constexpr int QW = sizeof(GRec<T>) / sizeof(uint4);
     // the compact records land at the end of the ring's storage, from where
     // each lane expands one into its SPair slot (all reads before all writes)
@@ -898,6 +1147,8 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
             if (lane < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 128 * lane));
         }
         st.S.zero();
+        st.base = base;
+        const int gstart = st.tcur;
         for (int b0 = 0; b0 < cnt; b0 += 32) {
             const int nb = cnt - b0 < 32 ? cnt - b0 : 32;
             // records b0.. into the staging area: asynchronous 16-byte
@@ -921,8 +1172,18 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
             st.np = nb;
             st.batch(nb);
         }
-        const int i_me = base + lane;
-        if (lane < G && i_me < a.n) finish_particle(a, i_me, st.S, orientation<T>(a, i_me));
+        if constexpr (REF) {
+            // the group's terms for the term kernel
+            if (lane == 0) {
+                a.term_start[g] = (int)(st.region + gstart);
+                a.term_cnt[g] = st.tcur - gstart;
+                if (st.tcur > a.term_capw) atomicMax(&a.status->term_overflow, st.tcur);
+            }
+        } else {
+            st.flush_terms();
+            const int i_me = base + lane;
+            if (lane < G && i_me < a.n) finish_particle(a, i_me, st.S, orientation<T>(a, i_me));
+        }
         __syncwarp();
     }
     if constexpr (COUNT)
@@ -932,7 +1193,9 @@ __global__ void __launch_bounds__(SBLOCK, std::is_same<T, float>::value ? 5 : 2)
 
 template <class T, bool COMP, int DIM>
 cudaError_t launch_dim(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
-    const size_t smem = ((smem_tables + 127) & ~(size_t)127) + (SBLOCK / 32) * sizeof(StagedSmem<T>);
+    const size_t smem = ((smem_tables + 127) & ~(size_t)127) +
+                        table_lo_bytes(a, COMP && std::is_same<T, float>::value) +
+                        (SBLOCK / 32) * sizeof(StagedSmem<T>);
     auto launch = [&](auto kernel) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -975,6 +1238,18 @@ cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, 
         launch(k_pair_scan<T, DIM, false>, smem1);
         launch(k_pair_apply<T, COMP, DIM, false>, smem2);
     }
+    if constexpr (COMP && std::is_same<T, float>::value) {
+        // the term kernel: one warp per 32 particles
+        const size_t smem3 = t + table_lo_bytes(a, true) + (SBLOCK / 32) * 32 * sizeof(int);
+        auto kernel = k_pair_terms<DIM>;
+        if (smem3 > 48 * 1024)
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
+        const long long need3 = ((long long)a.n + SBLOCK - 1) / SBLOCK;
+        const long long cap3 = (long long)blocks_per_sm(kernel, SBLOCK, smem3) * sm_count();
+        int grid3 = (int)(need3 < cap3 ? need3 : cap3);
+        if (grid3 < 1) grid3 = 1;
+        kernel<<<grid3, SBLOCK, smem3, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -1002,6 +1277,8 @@ size_t pair_record_bytes(int precision) {
 // Particles per warp of the SPLIT kernels: 32, or fewer (16, 8, 4) while
 // that leaves less than one wave of the feature kernel (five blocks of four
 // warps on every SM), so that a small system spreads over the whole GPU.
+int split_apply_max_warps() { return apply_blocks<float, true>() * sm_count() * (SBLOCK / 32); }
+
 int split_group(int n) {
     const int wave = 5 * (SBLOCK / 32) * sm_count();
     int G = 32;

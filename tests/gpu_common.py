@@ -45,7 +45,7 @@ import numpy as np
 
 TOL = {0: 1e-12, 1: 1e-5, 2: 1e-5}
 # bars of the net-force measure rel_F / rel_T (see above)
-RELTOL = {0: 1e-10, 1: 1e-2, 2: 1e-2}
+RELTOL = {0: 1e-10, 1: 1e-3, 2: 1e-5}
 FLAGGED_MAX = 0.01        # largest fraction of particles excluded near the parallel band
 
 

@@ -45,7 +45,8 @@ def test_algorithmic_flops():
     want = sum(bench.FLOPS_PER_PATH[k] * (10 + k) for k in bench.FLOPS_PER_PATH)
     counts[15] = 7
     assert bench.algorithmic_flops(counts, False, split=False) == want
-    assert bench.algorithmic_flops(counts, True, split=False) == want + bench.TWO_SUM_EXTRA * counts[2]
+    assert bench.algorithmic_flops(counts, True, split=False) == \
+        want + (bench.TWO_SUM_EXTRA + bench.REFINE_PER_TERM) * counts[2]
     assert bench.algorithmic_flops(counts, False) == want + bench.SPLIT_EXPAND * 7
 
 
