@@ -128,7 +128,11 @@ typedef struct dem_ctx dem_ctx;   /* opaque; owned by the library */
  * convex, because the nearest point on a face is found by its edge tests.
  * A self-intersecting 3D surface is not detected and is the caller's
  * responsibility.  3D edges are derived from the faces.  A shape has at
- * most 32 vertices, 32 edges, 32 faces and 12 vertices per face.
+ * most 128 vertices, 128 edges, 128 faces and 12 vertices per face.  Up to
+ * 32 of each, the pair kernels cull features with one 32-bit mask per kind;
+ * a context holding a larger shape uses two-level masks (four words, empty
+ * words skipped) and runs the THREAD decomposition only ("decomp" refuses
+ * the others, dem_autotune times THREAD alone).
  * Rejected with DEM_ERR_ARG: a 2D polygon with clockwise order, meeting
  * non-neighbour edges or a fold; a 3D face that is not planar or convex; an
  * open or inconsistently oriented surface; a non-positive enclosed volume. */

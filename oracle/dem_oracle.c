@@ -55,7 +55,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define MAXV 64          /* max vertices of one shape */
+#define MAXV 128         /* max vertices of one shape */
 #define MAXFV 16         /* max vertices of one face */
 
 typedef struct { double x, y, z; } v3;

@@ -307,6 +307,14 @@ void build_tables(const std::vector<HostGeom> &geoms, const std::vector<HostShap
                   HostTables *t) {
     t->td.clear(); t->itab.clear(); t->geoms.clear(); t->shapes.clear();
     t->Rmax = 0; t->rnd_max = 0;
+    // one-word feature masks unless some shape has more than 32 vertices,
+    // edges or faces
+    t->mask_words = 1;
+    for (auto &g : geoms)
+        if ((int)(g.v.size() / 3) > NARROW_FEATURES || (int)g.edges.size() > NARROW_FEATURES ||
+            (int)g.faces.size() > NARROW_FEATURES)
+            t->mask_words = WIDE_WORDS;
+    const int words = t->mask_words;
     for (auto &g : geoms) {
         Geom G = {};
         G.nv = (int)(g.v.size() / 3);
@@ -358,20 +366,21 @@ void build_tables(const std::vector<HostGeom> &geoms, const std::vector<HostShap
         }
         G.nfe = nfe;
         // incidence masks: per vertex, bit k set when the vertex bounds edge / face k
+        // (rows of `words` words: feature k is bit k % 32 of word k / 32)
         G.vem_off = (int)t->itab.size();
         for (int v = 0; v < G.nv; ++v) {
-            unsigned m = 0;
+            std::vector<unsigned> m(words, 0u);
             for (size_t k = 0; k < g.edges.size(); ++k)
-                if (g.edges[k].first == v || g.edges[k].second == v) m |= 1u << k;
-            t->itab.push_back((int)m);
+                if (g.edges[k].first == v || g.edges[k].second == v) m[k / 32] |= 1u << (k % 32);
+            for (int w = 0; w < words; ++w) t->itab.push_back((int)m[w]);
         }
         G.vfm_off = (int)t->itab.size();
         for (int v = 0; v < G.nv; ++v) {
-            unsigned m = 0;
+            std::vector<unsigned> m(words, 0u);
             for (size_t f = 0; f < g.faces.size(); ++f)
                 for (int u : g.faces[f])
-                    if (u == v) m |= 1u << f;
-            t->itab.push_back((int)m);
+                    if (u == v) m[f / 32] |= 1u << (f % 32);
+            for (int w = 0; w < words; ++w) t->itab.push_back((int)m[w]);
         }
         t->geoms.push_back(G);
     }
@@ -499,6 +508,7 @@ struct dem_ctx {
     int *d_itable = nullptr;
     unsigned long long *d_counters = nullptr;
     int table_len = 0, itable_len = 0, n_geoms = 0;
+    int mask_words = 1;               // WIDE_WORDS: a shape has more than 32 features
     // snapshot for the overflow retry
     double4_32a *snap = nullptr;
     Thermo *snap_thermo = nullptr;
@@ -562,6 +572,8 @@ int upload_tables(dem_ctx *ctx) {
     build_tables(ctx->geoms, ctx->shapes, &t);
     ctx->table_len = (int)t.td.size();
     ctx->itable_len = (int)t.itab.size();
+    ctx->mask_words = t.mask_words;
+    if (ctx->mask_words > 1) ctx->decomp = DEM_DECOMP_THREAD;
     ctx->n_geoms = (int)t.geoms.size();
     CK(dalloc(&ctx->d_geoms, t.geoms.size()));
     CK(cudaMemcpy(ctx->d_geoms, t.geoms.data(), sizeof(Geom) * t.geoms.size(), cudaMemcpyHostToDevice));
@@ -725,6 +737,7 @@ PairArgs pair_args(dem_ctx *ctx) {
     a.recs = ctx->recs;
     a.rec_count = ctx->rec_count;
     a.group = ctx_split_group(ctx);
+    a.mask_words = ctx->mask_words;
     if (ctx->precision == DEM_FP32_COMP) {
         a.quatf_lo = ctx->quatf_lo;
         a.xff = ctx->xff;
@@ -1236,6 +1249,9 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
     } else if (n == "decomp") {
         int d = (int)value;
         if (d < DEM_DECOMP_AUTO || d > DEM_DECOMP_SPLIT) return set_err(ctx, DEM_ERR_ARG, "bad decomp");
+        if (ctx->mask_words > 1 && d != DEM_DECOMP_AUTO && d != DEM_DECOMP_THREAD)
+            return set_err(ctx, DEM_ERR_ARG, "shapes with more than 32 vertices, edges or faces "
+                           "run the THREAD decomposition only");
         ctx->decomp = d == DEM_DECOMP_AUTO ? DEM_DECOMP_THREAD : d;
     } else if (n == "block") {
         int b = (int)value;
@@ -1721,6 +1737,10 @@ int dem_autotune(dem_ctx *ctx) {
     long long kernels = 0;
     ctx->tune_ms.clear();
     for (const Cand &c : cands) {
+        if (ctx->mask_words > 1 && c.decomp != DEM_DECOMP_THREAD) {   // wide shapes: THREAD only
+            ctx->tune_ms.push_back(-1.f);
+            continue;
+        }
         if (c.group) {
             if (ctx->split_user && c.group != G_keep) {   // the caller's group only
                 ctx->tune_ms.push_back(-1.f);

@@ -30,9 +30,12 @@
 
 namespace dem {
 
-constexpr int MAX_VERTS = 32;       // vertices of one shape (bit masks of 32)
-constexpr int MAX_EDGES = 32;       // edges of one shape (bit masks of 32)
-constexpr int MAX_FACES = 32;       // faces of one shape (bit masks of 32)
+constexpr int MAX_VERTS = 128;      // vertices of one shape
+constexpr int MAX_EDGES = 128;      // edges of one shape
+constexpr int MAX_FACES = 128;      // faces of one shape
+constexpr int NARROW_FEATURES = 32; // up to this many of each: one-word feature masks;
+                                    // more: WIDE_WORDS words (THREAD decomposition)
+constexpr int WIDE_WORDS = 4;
 constexpr int MAX_FACE_VERTS = 12;  // vertices of one face
 constexpr int MAX_GEOMS = 64;       // distinct geometries per context
 constexpr int THREADS = 128;
@@ -174,6 +177,8 @@ struct PairArgs {
     int *term_info;           // owner | gi << 8 | gj << 16 | jref << 24
     int *term_start, *term_cnt;
     int term_capw;
+    int mask_words;           // words per feature mask and incidence row: 1, or
+                              // WIDE_WORDS when a shape has more than 32 features
 };
 // Upper bound of the warps of SPLIT's feature kernel (regions of the term
 // buffer), and the launch of its term kernel (FP32 + two-sum).
@@ -277,6 +282,7 @@ cudaError_t launch_rescale(int n, int dim, double4_32a *pos, double4_32a *x_last
 // kernels read (api.cu).
 struct HostTables {
     std::vector<float4> tf_lo;    // td - tf per component (FP32 + two-sum refinement)
+    int mask_words = 1;           // 1, or WIDE_WORDS for shapes beyond 32 features
     int dim = 3;
     std::vector<float4> tf;
     std::vector<double4_32a> td;

@@ -274,6 +274,7 @@ extern "C" int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double 
     pa.force = force4; pa.torque = torque4; pa.energy = en; pa.virial = vir;
     pa.eps = epsilon; pa.sigma = sigma > 0 ? sigma : 0.0; pa.par_eps = 1e-6;
     pa.status = status; pa.counters = nullptr;
+    pa.mask_words = t.mask_words;
     if (ffm) {
         pa.quatf_lo = quatf_lo;
         pa.xff = xff;

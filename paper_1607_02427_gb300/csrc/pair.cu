@@ -44,7 +44,7 @@ namespace {
 // ---------------------------------------------------------------------------
 // THREAD decomposition
 // ---------------------------------------------------------------------------
-template <class T, bool COMP, int DIM, bool COUNT>
+template <class T, bool COMP, int DIM, bool COUNT, class MK = unsigned>
 __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
     using R4 = typename R4T<T>::type;
     extern __shared__ __align__(32) unsigned char smem[];
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(THREADS) k_pair_thread(const PairArgs a) {
             const Geom &gj = geo[pg.gj];
             bump<COUNT>(&pc, C_PAIRS);
             bump<COUNT>(&pc, C_FPE, defined_feature_pairs(DIM, gi, gj));
-            PairWork<T> w;
+            PairWork<T, MK> w;
             w.M = mul_tn(Ri, orientation_j<T>(a, j, pg));
             w.dl = mul_t(Ri, pg.d);
             w.rc = (T)WCA_CUT * pg.sig;
@@ -105,16 +105,18 @@ template <class T, bool COMP, int DIM>
 cudaError_t launch_thread(const PairArgs &a, int block, bool count, size_t smem, cudaStream_t s) {
     int grid = (a.n + block - 1) / block;
     if (grid < 1) grid = 1;
-    if (count) {
-        auto k = k_pair_thread<T, COMP, DIM, true>;
+    auto launch = [&](auto k) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, block, smem, s>>>(a);
+    };
+    // shapes with more than 32 vertices, edges or faces: two-level masks
+    if (a.mask_words > 1) {
+        if (count) launch(k_pair_thread<T, COMP, DIM, true, WideMask<WIDE_WORDS>>);
+        else launch(k_pair_thread<T, COMP, DIM, false, WideMask<WIDE_WORDS>>);
     } else {
-        auto k = k_pair_thread<T, COMP, DIM, false>;
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, block, smem, s>>>(a);
+        if (count) launch(k_pair_thread<T, COMP, DIM, true>);
+        else launch(k_pair_thread<T, COMP, DIM, false>);
     }
     return cudaGetLastError();
 }
@@ -391,7 +393,7 @@ cudaError_t launch_warp(const PairArgs &a, bool count, size_t smem_tables, cudaS
 template <class T, bool COMP>
 cudaError_t dispatch_dim(const PairArgs &a, int decomp, int block, bool count, size_t smem,
                          cudaStream_t s) {
-    if (decomp == DEM_DECOMP_WARP) {
+    if (decomp == DEM_DECOMP_WARP && a.mask_words == 1) {
         if (a.dim == 2) return launch_warp<T, COMP, 2>(a, count, smem, s);
         return launch_warp<T, COMP, 3>(a, count, smem, s);
     }
@@ -409,8 +411,10 @@ size_t pair_smem_bytes(const PairArgs &a, int precision) {
 cudaError_t launch_pair(const PairArgs &a, int precision, int decomp, int block, bool count,
                         cudaStream_t s) {
     size_t smem = pair_smem_bytes(a, precision);
-    if (decomp == DEM_DECOMP_STAGED) return launch_pair_staged(a, precision, count, smem, s);
-    if (decomp == DEM_DECOMP_SPLIT) return launch_pair_split(a, precision, count, smem, s);
+    // the queue-based decompositions carry one-word masks: contexts with
+    // larger shapes run THREAD (the context refuses other choices for them)
+    if (a.mask_words == 1 && decomp == DEM_DECOMP_STAGED) return launch_pair_staged(a, precision, count, smem, s);
+    if (a.mask_words == 1 && decomp == DEM_DECOMP_SPLIT) return launch_pair_split(a, precision, count, smem, s);
     if (block <= 0) block = THREADS;
     if (block > THREADS) block = THREADS;
     switch (precision) {

@@ -153,7 +153,53 @@ template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return
 // ---------------------------------------------------------------------------
 // Pair setup: separating axis along the centre line and the feature masks
 // ---------------------------------------------------------------------------
-template <class T> struct PairWork {
+// ---------------------------------------------------------------------------
+// Feature masks.  Shapes with at most 32 vertices, edges and faces use one
+// 32-bit word per mask (every decomposition).  Larger shapes (up to 128 of
+// each) use a two-level mask of four words: the culls and loops skip the
+// empty words, then walk the set bits of the others (THREAD decomposition).
+// The incidence rows of the geometry table (the edges / faces of each vertex)
+// have one word per mask word.
+// ---------------------------------------------------------------------------
+template <int W> struct WideMask {
+    unsigned w[W];
+};
+template <class MK> struct MaskWords;
+template <> struct MaskWords<unsigned> { static constexpr int value = 1; };
+template <int W> struct MaskWords<WideMask<W>> { static constexpr int value = W; };
+
+__device__ __forceinline__ unsigned low_bits(int n) { return n >= 32 ? FULL : ((1u << n) - 1u); }
+__device__ __forceinline__ void mask_low(unsigned *m, int n) { *m = low_bits(n); }
+template <int W> __device__ __forceinline__ void mask_low(WideMask<W> *m, int n) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) m->w[k] = n >= 32 * (k + 1) ? FULL : (n > 32 * k ? low_bits(n - 32 * k) : 0u);
+}
+__device__ __forceinline__ void mask_zero(unsigned *m) { *m = 0u; }
+template <int W> __device__ __forceinline__ void mask_zero(WideMask<W> *m) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) m->w[k] = 0u;
+}
+__device__ __forceinline__ void mask_set(unsigned *m, int b) { *m |= 1u << b; }
+template <int W> __device__ __forceinline__ void mask_set(WideMask<W> *m, int b) {
+    m->w[b >> 5] |= 1u << (b & 31);
+}
+__device__ __forceinline__ bool mask_any(unsigned m) { return m != 0u; }
+template <int W> __device__ __forceinline__ bool mask_any(const WideMask<W> &m) {
+    unsigned a = 0u;
+#pragma unroll
+    for (int k = 0; k < W; ++k) a |= m.w[k];
+    return a != 0u;
+}
+// f(b) for every set bit b, in increasing order
+template <class F> __device__ __forceinline__ void for_each_bit(unsigned m, F f) {
+    for (; m; m &= m - 1u) f(__ffs(m) - 1);
+}
+template <int W, class F> __device__ __forceinline__ void for_each_bit(const WideMask<W> &m, F f) {
+    for (int k = 0; k < W; ++k)
+        for (unsigned b = m.w[k]; b; b &= b - 1u) f(32 * k + __ffs(b) - 1);
+}
+
+template <class T, class MK = unsigned> struct PairWork {
     M33<T> M;            // R_i^T R_j
     V3<T> dl;            // x_j - x_i in i's frame
     int i, j;            // the particles (FP32 + two-sum refinement)
@@ -162,33 +208,41 @@ template <class T> struct PairWork {
     T rc, sig2;
     int gj;
     int jref;            // 1 when j < i: j's edge is the parallel-edge rule's reference
-    unsigned vim, vjm;   // vertices of i / of j that can reach the other
-    unsigned eim, ejm;   // edges
-    unsigned fim, fjm;   // faces
+    MK vim, vjm;         // vertices of i / of j that can reach the other
+    MK eim, ejm;         // edges
+    MK fim, fjm;         // faces
 };
 
-__device__ __forceinline__ unsigned low_bits(int n) { return n >= 32 ? FULL : ((1u << n) - 1u); }
-
 // Mask of the features (edges or faces) with a vertex in vmask, from the
-// per-vertex incidence masks inc.
+// per-vertex incidence masks inc (one row of mask words per vertex).
 __device__ __forceinline__ unsigned feature_mask(const int *inc, unsigned vmask) {
     unsigned m = 0;
     for (unsigned v = vmask; v; v &= v - 1u) m |= (unsigned)inc[__ffs(v) - 1];
     return m;
 }
+template <int W>
+__device__ __forceinline__ WideMask<W> feature_mask(const int *inc, const WideMask<W> &vmask) {
+    WideMask<W> m;
+    mask_zero(&m);
+    for_each_bit(vmask, [&](int v) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) m.w[k] |= (unsigned)inc[W * v + k];
+    });
+    return m;
+}
 
 // Returns false when the pair is separated along its centre line by at least
 // r_cut (all of its terms are zero).
-template <class T, bool COUNT>
+template <class T, bool COUNT, class MK>
 __device__ __forceinline__ bool pair_setup(const typename R4T<T>::type *tab, const int *itab,
-                                           const Geom &gi, const Geom &gj, PairWork<T> *w,
+                                           const Geom &gi, const Geom &gj, PairWork<T, MK> *w,
                                            PathCount *pc) {
-    w->vim = low_bits(gi.nv);
-    w->vjm = low_bits(gj.nv);
-    w->eim = low_bits(gi.ne);
-    w->ejm = low_bits(gj.ne);
-    w->fim = low_bits(gi.nf);
-    w->fjm = low_bits(gj.nf);
+    mask_low(&w->vim, gi.nv);
+    mask_low(&w->vjm, gj.nv);
+    mask_low(&w->eim, gi.ne);
+    mask_low(&w->ejm, gj.ne);
+    mask_low(&w->fim, gi.nf);
+    mask_low(&w->fjm, gj.nf);
     const T d2 = dot(w->dl, w->dl);
     if (gi.nv == 1 && gj.nv == 1) return true;           // sphere limit: one term
     if (!(d2 > T(0))) return true;                         // coincident centres
@@ -202,18 +256,20 @@ __device__ __forceinline__ bool pair_setup(const typename R4T<T>::type *tab, con
     // support of i towards j, and i's vertices that reach j's slab
     const T lo_i = dn - hj - w->rc;
     T hi = T(-3.0e38);
-    unsigned vim = 0;
+    MK vim;
+    mask_zero(&vim);
     for (int k = 0; k < gi.nv; ++k) {
         const T p = dot(xyz<T>(tab[gi.v_off + k]), u);
         hi = fmax(hi, p);
-        if (p > lo_i) vim |= 1u << k;
+        if (p > lo_i) mask_set(&vim, k);
     }
     bump<COUNT>(pc, C_PROJ, (unsigned)(gi.nv + 2 * gj.nv));
     if (!(dn - hi - hj < w->rc)) return false;
     const T hi_j = hi + w->rc - dn;                        // j's vertices: v . uj < hi_j
-    unsigned vjm = 0;
+    MK vjm;
+    mask_zero(&vjm);
     for (int k = 0; k < gj.nv; ++k)
-        if (dot(xyz<T>(tab[gj.v_off + k]), uj) < hi_j) vjm |= 1u << k;
+        if (dot(xyz<T>(tab[gj.v_off + k]), uj) < hi_j) mask_set(&vjm, k);
     w->vim = vim;
     w->vjm = vjm;
     w->eim = feature_mask(itab + gi.vem_off, vim);
@@ -602,9 +658,9 @@ template <class T> struct PartSink {
 // FP32 + two-sum mode): each term found is re-evaluated in float-float
 // (refined_values) and added to the sink as float-float; pa then gives the
 // state, and w.i, w.j the particles.
-template <class T, int DIM, bool COUNT, bool REF, class Sink>
+template <class T, int DIM, bool COUNT, bool REF, class Sink, class MK>
 __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, const int *itab,
-                                          const Geom &gi, const Geom &gj, const PairWork<T> &w,
+                                          const Geom &gi, const Geom &gj, const PairWork<T, MK> &w,
                                           T eps, T par_eps, Sink &sink, PathCount *pc,
                                           const PairArgs *pa = nullptr) {
     using R4 = typename R4T<T>::type;
@@ -645,20 +701,18 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
     }
     const T reach_i = T(gi.R) + rc, reach_j = T(gj.R) + rc;
     // vertex of j against the faces (2D: edges) of i, in i's frame
-    for (unsigned mb = w.vjm; mb; mb &= mb - 1u) {
-        const int b = __ffs(mb) - 1;
+    for_each_bit(w.vjm, [&](int b) {
         const V3<T> p = dl + mul(w.M, xyz<T>(tab[gj.v_off + b]));
         bump<COUNT>(pc, C_VTX);
-        if (!(dot(p, p) < reach_i * reach_i)) continue;
+        if (!(dot(p, p) < reach_i * reach_i)) return;
         if constexpr (DIM == 3) {
-            for (unsigned mf = w.fim; mf; mf &= mf - 1u) {
-                const int f = __ffs(mf) - 1;
+            for_each_bit(w.fim, [&](int f) {
                 V3<T> q;
                 T r2;
                 FaceHit hit;
                 if (!face_nearest<T, COUNT>(tab, itab, gi.f_off + f, gi.fi_off + 2 * f, p, rc, &q, &r2, pc,
                                             &hit))
-                    continue;
+                    return;
                 if (r2 < rc2) {
                     if constexpr (REF) {
                         refined(TK_VF_I, f, b, hit, 0.f, 0.f);
@@ -669,16 +723,15 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                     }
                     bump<COUNT>(pc, C_TERMS);
                 }
-            }
+            });
         } else {
-            for (unsigned me = w.eim; me; me &= me - 1u) {
-                const int e = __ffs(me) - 1;
+            for_each_bit(w.eim, [&](int e) {
                 const R4 ea = tab[gi.e_off + 2 * e], ed = tab[gi.e_off + 2 * e + 1];
                 const V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
                 const V3<T> c = A + D * T(0.5) - p;
                 const T lim = ea.w + rc;
                 bump<COUNT>(pc, C_SPHERE);
-                if (!(dot(c, c) < lim * lim)) continue;
+                if (!(dot(c, c) < lim * lim)) return;
                 bump<COUNT>(pc, C_PTSEG);
                 const T t = clamp01(dot(p - A, D) * ed.w);
                 const V3<T> q = A + D * t;
@@ -694,25 +747,23 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                     }
                     bump<COUNT>(pc, C_TERMS);
                 }
-            }
+            });
         }
-    }
+    });
     // vertex of i against the faces (2D: edges) of j, in j's frame
-    for (unsigned ma = w.vim; ma; ma &= ma - 1u) {
-        const int ai = __ffs(ma) - 1;
+    for_each_bit(w.vim, [&](int ai) {
         const V3<T> u = xyz<T>(tab[gi.v_off + ai]);
         const V3<T> p = mul_t(w.M, u - dl);
         bump<COUNT>(pc, C_VTX);
-        if (!(dot(p, p) < reach_j * reach_j)) continue;
+        if (!(dot(p, p) < reach_j * reach_j)) return;
         if constexpr (DIM == 3) {
-            for (unsigned mf = w.fjm; mf; mf &= mf - 1u) {
-                const int f = __ffs(mf) - 1;
+            for_each_bit(w.fjm, [&](int f) {
                 V3<T> q;
                 T r2;
                 FaceHit hit;
                 if (!face_nearest<T, COUNT>(tab, itab, gj.f_off + f, gj.fi_off + 2 * f, p, rc, &q, &r2, pc,
                                             &hit))
-                    continue;
+                    return;
                 if (r2 < rc2) {
                     if constexpr (REF) {
                         refined(TK_VF_J, ai, f, hit, 0.f, 0.f);
@@ -724,16 +775,15 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                     bump<COUNT>(pc, C_TERMS);
                     bump<COUNT>(pc, C_JTERMS);
                 }
-            }
+            });
         } else {
-            for (unsigned me = w.ejm; me; me &= me - 1u) {
-                const int e = __ffs(me) - 1;
+            for_each_bit(w.ejm, [&](int e) {
                 const R4 ea = tab[gj.e_off + 2 * e], ed = tab[gj.e_off + 2 * e + 1];
                 const V3<T> A = xyz<T>(ea), D = xyz<T>(ed);
                 const V3<T> c = A + D * T(0.5) - p;
                 const T lim = ea.w + rc;
                 bump<COUNT>(pc, C_SPHERE);
-                if (!(dot(c, c) < lim * lim)) continue;
+                if (!(dot(c, c) < lim * lim)) return;
                 bump<COUNT>(pc, C_PTSEG);
                 const T t = clamp01(dot(p - A, D) * ed.w);
                 const V3<T> q = A + D * t;
@@ -750,35 +800,32 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                     bump<COUNT>(pc, C_TERMS);
                     bump<COUNT>(pc, C_JTERMS);
                 }
-            }
+            });
         }
-    }
+    });
     if constexpr (DIM == 3) {
         // edges of j against the edges of i, in i's frame
-        const unsigned eim = w.eim;
-        for (unsigned mb = eim ? w.ejm : 0u; mb; mb &= mb - 1u) {
-            const int eb = __ffs(mb) - 1;
+        if (mask_any(w.eim)) for_each_bit(w.ejm, [&](int eb) {
             const R4 ba = tab[gj.e_off + 2 * eb], bd = tab[gj.e_off + 2 * eb + 1];
             const V3<T> A2 = dl + mul(w.M, xyz<T>(ba));
             const V3<T> D2 = mul(w.M, xyz<T>(bd));
             const V3<T> C2 = A2 + D2 * T(0.5);
             const T reach = reach_i + ba.w;
             bump<COUNT>(pc, C_EDGE);
-            if (!(dot(C2, C2) < reach * reach)) continue;
-            for (unsigned ma = eim; ma; ma &= ma - 1u) {
-                const int ea = __ffs(ma) - 1;
+            if (!(dot(C2, C2) < reach * reach)) return;
+            for_each_bit(w.eim, [&](int ea) {
                 const R4 aa = tab[gi.e_off + 2 * ea], ad = tab[gi.e_off + 2 * ea + 1];
                 const V3<T> A1 = xyz<T>(aa), D1 = xyz<T>(ad);
                 const V3<T> dc = A1 + D1 * T(0.5) - C2;
                 const T lim = aa.w + ba.w + rc;
                 bump<COUNT>(pc, C_SPHERE);
-                if (!(dot(dc, dc) < lim * lim)) continue;
+                if (!(dot(dc, dc) < lim * lim)) return;
                 // carrier lines farther apart than r_cut: the segments are too
                 const V3<T> nrm = cross(D1, D2);
                 const T n2 = dot(nrm, nrm);
                 const T sep = dot(A2 - A1, nrm);
                 bump<COUNT>(pc, C_LINE);
-                if (sep * sep >= rc2 * n2 && n2 > par_eps * dot(D1, D1) * dot(D2, D2)) continue;
+                if (sep * sep >= rc2 * n2 && n2 > par_eps * dot(D1, D1) * dot(D2, D2)) return;
                 bump<COUNT>(pc, C_SEGSEG);
                 V3<T> P1, P2;
                 T ps, pt;
@@ -797,8 +844,8 @@ __device__ __forceinline__ void eval_pair(const typename R4T<T>::type *tab, cons
                     }
                     bump<COUNT>(pc, C_TERMS);
                 }
-            }
-        }
+            });
+        });
     }
 }
 

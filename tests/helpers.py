@@ -70,6 +70,8 @@ SHAPES_3D = {
     "octahedron": lambda: W.octahedron(1.0, 0.1),
     "prism": lambda: W.triangular_prism(1.0, 1.0, 0.15),
     "icosahedron": lambda: W.icosahedron(0.8, 0.15),
+    # 42 V / 120 E / 80 F: beyond one 32-bit feature mask
+    "icosphere": lambda: W.icosphere(0.7, 0.12),
 }
 
 

@@ -250,3 +250,23 @@ def test_virial_affine_derivative(oracle_mod, name, s):
             dU = (_energy(oracle_mod, sp, 0.0) - _energy(oracle_mod, sm, 0.0)) / (2 * h)
             # x_a -> x_a + gamma x_b : dU/dgamma = sum (dU/dd)_a d_b = -W[b][a]
             assert dU == pytest.approx(-W9[b, a], abs=1e-6 * (1 + o["fscale"].sum()))
+
+
+@pytest.mark.parametrize("vertex,valence", [(0, 5), (12, 6)])
+def test_icosphere_vertex_valence(oracle_mod, vertex, valence):
+    """A small sphere straight out from a vertex of the 80-face icosphere,
+    at distance d: the vertex's nearest point on each of its incident faces
+    is the vertex itself, and every other face lies beyond r_cut, so
+    U = valence U(d): 5 faces meet at the icosahedron's own vertices, 6 at
+    the edge midpoints the subdivision added (Eq. DEM, vertex-face terms)."""
+    ico = W.icosphere(0.7, 0.02)
+    tip = ico["verts"][vertex]
+    d = 0.036
+    s = two_body(ico, W.sphere(0.02), tip * (1 + d / np.linalg.norm(tip)), sigma=0.04)
+    o = oracle_mod.forces(s)
+    u1, f1 = oracle_mod.wca(d, 1.0, 0.04)
+    assert o["counts"][0, 2] == valence
+    assert o["U"][0] == pytest.approx(valence * u1, rel=1e-12)
+    # the net force points along the vertex's radius
+    np.testing.assert_allclose(o["force"][1], valence * f1 * tip / np.linalg.norm(tip), rtol=1e-9,
+                               atol=1e-12 * valence * abs(f1))
