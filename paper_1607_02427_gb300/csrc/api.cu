@@ -848,10 +848,15 @@ int launch_forces(dem_ctx *ctx, bool count, cudaEvent_t e0 = nullptr, cudaEvent_
     NlistArgs na = nlist_args(ctx);
     CK(launch_cells(na, ctx->n_cells, ctx->stream));
     CK(launch_nlist(na, ctx->stream));
-    // external records: under stream capture they become event-record nodes
-    if (e0) CK(cudaEventRecordWithFlags(e0, ctx->stream, cudaEventRecordExternal));
+    // under stream capture the events are external records (they become
+    // event-record nodes of the graph); launched directly, plain records
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (e0 || e1) CK(cudaStreamIsCapturing(ctx->stream, &cap));
+    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                   : cudaEventRecordDefault;
+    if (e0) CK(cudaEventRecordWithFlags(e0, ctx->stream, ev_flags));
     CK(launch_pair(pair_args(ctx), ctx->precision, ctx->decomp, ctx->block, count, ctx->stream));
-    if (e1) CK(cudaEventRecordWithFlags(e1, ctx->stream, cudaEventRecordExternal));
+    if (e1) CK(cudaEventRecordWithFlags(e1, ctx->stream, ev_flags));
     // SPLIT: scan and feature kernels, and in the FP32 + two-sum mode the term kernel
     ctx->launches += 2 + (ctx->decomp == DEM_DECOMP_SPLIT
                               ? (ctx->precision == DEM_FP32_COMP ? 3 : 2) : 1);

@@ -194,59 +194,66 @@ __device__ __forceinline__ void store_ff_state(float4 *quatf_lo, float4 *xff, in
     xff[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.f);
 }
 
+// The first half of a step for particle i of replica rp: the thermostat's
+// velocity scale s1 (NVT), the half kick, the drift (with the box dilation
+// under NPT), the free rotation, the FP32 copies; returns the squared
+// displacement since the list build for the rebuild test.
+__device__ __forceinline__ float first_half_particle(const StepArgs &a, int i, const Rep &rp,
+                                                     double s1) {
+    const ShapeDev &sh = a.shapes[a.shape[i]];
+    double4_32a v = a.vel[i], L = a.angmom[i], F = a.force[i], Tq = a.torque[i];
+    double4_32a x = a.pos[i], q = a.quat[i];
+    if (a.nvt) {
+        v.x *= s1; v.y *= s1; v.z *= s1;
+        L.x *= s1; L.y *= s1; L.z *= s1;
+    }
+    if (a.npt) {
+        // half kick and drift with the box dilation (the box itself moved
+        // by ax in k_box before this kernel)
+        const Thermo &t = a.thermo[a.rep[i]];
+        const double b = t.bv * sh.inv_mass;
+        v.x = t.av * v.x + b * F.x; v.y = t.av * v.y + b * F.y; v.z = t.av * v.z + b * F.z;
+        L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
+        x.x = wrap(t.ax * x.x + t.bx * v.x, rp.L[0], rp.inv_L[0]);
+        x.y = wrap(t.ax * x.y + t.bx * v.y, rp.L[1], rp.inv_L[1]);
+        if (a.dim == 3) x.z = wrap(t.ax * x.z + t.bx * v.z, rp.L[2], rp.inv_L[2]);
+    } else {
+        const double h = 0.5 * a.dt * sh.inv_mass;
+        v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
+        L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
+        x.x = wrap(x.x + a.dt * v.x, rp.L[0], rp.inv_L[0]);
+        x.y = wrap(x.y + a.dt * v.y, rp.L[1], rp.inv_L[1]);
+        if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2], rp.inv_L[2]);
+    }
+    if (a.rotor32) {
+        free_rotor_f32(q, L, sh.inv_inertia, a.dt);
+    } else {
+        free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inv_inertia, 0, a.dt);
+        free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
+        free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
+    }
+    // renormalise: |q|^2 = 1 + e with |e| ~ 1e-10 per step, and
+    // 1/sqrt(1 + e) = 1 - e/2 + 3e^2/8 - ... (remainder below 5|e|^3/16,
+    // < 3e-18 for |e| < 2e-6; otherwise the general rsqrt)
+    const double qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w, e2 = qq - 1.0;
+    const double inq = fabs(e2) < 2e-6 ? fma(fma(0.375, e2, -0.5), e2, 1.0) : rsqrt(qq);
+    q.x *= inq; q.y *= inq; q.z *= inq; q.w *= inq;
+    a.pos[i] = x;
+    a.vel[i] = v;
+    a.angmom[i] = L;
+    a.quat[i] = q;
+    a.quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+    if (a.quatf_lo) store_ff_state(a.quatf_lo, a.xff, i, x, q);
+    return since_build(a, rp, i, x);
+}
+
 __global__ void k_first_half(const StepArgs a) {
     float dmax = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const int r = a.rep[i];
-        const Rep &rp = a.reps[r];
-        const ShapeDev &sh = a.shapes[a.shape[i]];
-        double4_32a v = a.vel[i], L = a.angmom[i], F = a.force[i], Tq = a.torque[i];
-        double4_32a x = a.pos[i], q = a.quat[i];
-        if (a.nvt) {
-            double s = a.thermo[r].s1;
-            v.x *= s; v.y *= s; v.z *= s;
-            L.x *= s; L.y *= s; L.z *= s;
-        }
-        if (a.npt) {
-            // half kick and drift with the box dilation (the box itself moved
-            // by ax in k_box before this kernel)
-            const Thermo &t = a.thermo[r];
-            const double b = t.bv * sh.inv_mass;
-            v.x = t.av * v.x + b * F.x; v.y = t.av * v.y + b * F.y; v.z = t.av * v.z + b * F.z;
-            L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
-            x.x = wrap(t.ax * x.x + t.bx * v.x, rp.L[0], rp.inv_L[0]);
-            x.y = wrap(t.ax * x.y + t.bx * v.y, rp.L[1], rp.inv_L[1]);
-            if (a.dim == 3) x.z = wrap(t.ax * x.z + t.bx * v.z, rp.L[2], rp.inv_L[2]);
-        } else {
-            const double h = 0.5 * a.dt * sh.inv_mass;
-            v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
-            L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
-            x.x = wrap(x.x + a.dt * v.x, rp.L[0], rp.inv_L[0]);
-            x.y = wrap(x.y + a.dt * v.y, rp.L[1], rp.inv_L[1]);
-            if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2], rp.inv_L[2]);
-        }
-        if (a.rotor32) {
-            free_rotor_f32(q, L, sh.inv_inertia, a.dt);
-        } else {
-            free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
-            free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
-            free_rotor_axis(q, L, sh.inv_inertia, 0, a.dt);
-            free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
-            free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
-        }
-        // renormalise: |q|^2 = 1 + e with |e| ~ 1e-10 per step, and
-        // 1/sqrt(1 + e) = 1 - e/2 + 3e^2/8 - ... (remainder below 5|e|^3/16,
-        // < 3e-18 for |e| < 2e-6; otherwise the general rsqrt)
-        const double qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w, e2 = qq - 1.0;
-        const double inq = fabs(e2) < 2e-6 ? fma(fma(0.375, e2, -0.5), e2, 1.0) : rsqrt(qq);
-        q.x *= inq; q.y *= inq; q.z *= inq; q.w *= inq;
-        a.pos[i] = x;
-        a.vel[i] = v;
-        a.angmom[i] = L;
-        a.quat[i] = q;
-        a.quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
-        if (a.quatf_lo) store_ff_state(a.quatf_lo, a.xff, i, x, q);
-        dmax = fmaxf(dmax, since_build(a, rp, i, x));
+        dmax = fmaxf(dmax, first_half_particle(a, i, a.reps[r], a.nvt ? a.thermo[r].s1 : 1.0));
     }
     max_to_status(a, dmax);
 }
@@ -272,24 +279,30 @@ __device__ __forceinline__ double kinetic_trans(const ShapeDev &sh, const double
     return 0.5 * sh.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
 }
 
-__global__ void k_second_half(const StepArgs a) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        const ShapeDev &sh = a.shapes[a.shape[i]];
-        double4_32a v = a.vel[i], L = a.angmom[i], F = a.force[i], Tq = a.torque[i];
-        if (a.npt) {
-            const Thermo &t = a.thermo[a.rep[i]];
-            const double b = t.bv * sh.inv_mass;
-            v.x = t.av * v.x + b * F.x; v.y = t.av * v.y + b * F.y; v.z = t.av * v.z + b * F.z;
-            a.ket[i] = kinetic_trans(sh, v);
-        } else {
-            const double h = 0.5 * a.dt * sh.inv_mass;
-            v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
-        }
-        L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
-        a.vel[i] = v;
-        a.angmom[i] = L;
-        a.ke[i] = kinetic_of(sh, v, L);
+// The second half kick of particle i; returns (and stores) its kinetic energy.
+__device__ __forceinline__ double second_half_particle(const StepArgs &a, int i) {
+    const ShapeDev &sh = a.shapes[a.shape[i]];
+    double4_32a v = a.vel[i], L = a.angmom[i], F = a.force[i], Tq = a.torque[i];
+    if (a.npt) {
+        const Thermo &t = a.thermo[a.rep[i]];
+        const double b = t.bv * sh.inv_mass;
+        v.x = t.av * v.x + b * F.x; v.y = t.av * v.y + b * F.y; v.z = t.av * v.z + b * F.z;
+        a.ket[i] = kinetic_trans(sh, v);
+    } else {
+        const double h = 0.5 * a.dt * sh.inv_mass;
+        v.x += h * F.x; v.y += h * F.y; v.z += h * F.z;
     }
+    L.x += 0.5 * a.dt * Tq.x; L.y += 0.5 * a.dt * Tq.y; L.z += 0.5 * a.dt * Tq.z;
+    a.vel[i] = v;
+    a.angmom[i] = L;
+    const double k = kinetic_of(sh, v, L);
+    a.ke[i] = k;
+    return k;
+}
+
+__global__ void k_second_half(const StepArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
+        second_half_particle(a, i);
 }
 
 __global__ void k_kinetic(const StepArgs a) {

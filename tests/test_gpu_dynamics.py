@@ -145,6 +145,30 @@ def test_graph_equals_eager(dem):
         np.testing.assert_array_equal(out[0][k], out[1][k])
 
 
+@pytest.mark.parametrize("ens", ["nve", "nvt"])
+def test_graph_eager_profiling(dem, ens):
+    """Steps replayed from the captured graph and launched directly, with
+    the pair-kernel profiling (CUDA events around the pair kernels: graph
+    event nodes, or plain records) on and off, in calls of several lengths,
+    give identical trajectories, and the profiled totals cover every step."""
+    small = _cluster([W.cube(1.0, 0.15)], 150, [14.0] * 3, 55, sigma=0.3, gap=(0.95, 1.1),
+                     gap_min=0.9)
+    e = dem.DEM_NVE if ens == "nve" else dem.DEM_NVT
+    out = []
+    for graph, prof in ((1, 0), (1, 1), (0, 1), (0, 0)):
+        with dem.DEM(small, dem.DEM_FP32_COMP, graph=graph) as d:
+            d.set_param("profile", prof)
+            for n in (7, 1, 12):
+                d.step(n, 1e-3, e, kT=1.0, tau_T=0.5)
+            if prof:
+                assert d.get_param("pair_launches") == 20
+                assert d.get_param("pair_ms_total") > 0
+            out.append(d.state())
+    for o in out[1:]:
+        for k in ("pos", "vel", "orient", "angmom", "thermo"):
+            np.testing.assert_array_equal(o[k], out[0][k])
+
+
 def test_overflow_retry_same_trajectory(dem):
     s = _cluster([W.cube(1.0, 0.15)], 150, [14.0] * 3, 54, sigma=0.3, gap=(0.95, 1.1), gap_min=0.9)
     out = []
