@@ -114,6 +114,9 @@ def parse():
                    help="skip the e2e, FP64 and CPU-baseline measurements")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--decomp", default="auto", choices=["auto", "thread", "warp", "staged", "split"])
+    p.add_argument("--profile-evals", type=int, default=0,
+                   help="after the preparation and the autotune, run this many eager force "
+                        "evaluations inside the NVTX range dem_profile (for ncu) and exit")
     return p.parse_args()
 
 
@@ -250,7 +253,7 @@ def algorithmic_flops(counts, comp, split=True):
 
 def pair_source_hash():
     h = hashlib.sha256()
-    for name in ("pair.cu", "pair_staged.cu", "pair_kernels.cuh", "pair_common.cuh"):
+    for name in ("pair.cu", "pair_staged.cu", "pair_kernels.cuh", "pair_common.cuh", "ff.cuh"):
         with open(os.path.join(ROOT, "paper_1607_02427_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -403,6 +406,22 @@ def main():
             tune[nm] = d.get_param(f"autotune_ms_{k}")
     if decomp_name == "split":
         decomp_name = f"split, {int(d.get_param('split_group'))} particles per warp"
+
+    if a.profile_evals:
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("dem_profile")
+        for _ in range(a.profile_evals):
+            d.compute()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        if rank == 0:
+            counts = d.counters()
+            print(json.dumps({"profile_evals": a.profile_evals, "workload": system.name,
+                              "particles": system.n, "decomposition": decomp_name,
+                              "work_counters": {nm: int(counts[k])
+                                                for k, nm in WORK_COUNTERS.items()}}))
+        d.close()
+        return
 
     # warm-up
     d.step(a.warmup, run["dt"], ens, kT=run["kT"], tau_T=run["tau"])

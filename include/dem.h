@@ -276,6 +276,10 @@ int dem_set_box(dem_ctx *ctx, const double *box);
  *   "block"       threads per block of the pair kernel (0 = default)
  *   "graph"       1 = replay each step as a captured CUDA graph (default 1)
  *   "nlist_cap"   neighbour slots per particle (grown automatically, at most 768)
+ *   "term_cap"    DEM_FP32_COMP in the SPLIT decomposition: term records per
+ *                 warp of the feature kernel (0 until first needed; default
+ *                 sixteen per particle on average, at least 512; grown
+ *                 automatically, the evaluation redone)
  *   "npt_chunk"   DEM_NPT steps between host updates of the cell grids (100)
  *   "profile"     1 = time every pair-kernel launch of dem_step with a pair
  *                 of CUDA events on the context's stream (inside the
@@ -343,7 +347,7 @@ int dem_shape_info(const dem_shape *shape, double *out);
  * It computes, for ONE periodic system, the forces, torques and per-particle
  * energies dem_compute would, holding every intermediate array (packed
  * state, geometry tables, neighbour list, status) in one static device array
- * of the library: about 20 MiB, reserved on every GPU that loads libdem until
+ * of the library: about 21 MiB, reserved on every GPU that loads libdem until
  * the process exits.
  *   shapes, n_shapes, epsilon, sigma, precision   as for dem_create (host)
  *   box        dim box lengths (host); each edge at least twice the

@@ -1280,6 +1280,14 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
             int rc = force_rebuild(ctx);
             if (rc) return rc;
         }
+    } else if (n == "term_cap") {
+        int c = (int)value;
+        if (c < 1 || c > (1 << 24)) return set_err(ctx, DEM_ERR_ARG, "bad term_cap");
+        ctx->term_capw = c;
+        cudaFree(ctx->term_a); cudaFree(ctx->term_b); cudaFree(ctx->term_info);
+        ctx->term_a = ctx->term_b = nullptr;
+        ctx->term_info = nullptr;
+        ctx->term_recs = 0;
     } else {
         return set_err(ctx, DEM_ERR_ARG, "unknown parameter '%s'", name);
     }
@@ -1307,6 +1315,7 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
         *value = ctx->tune_ms[k];
     }
     else if (n == "nlist_cap") *value = ctx->cap;
+    else if (n == "term_cap") *value = ctx->term_capw;
     else if (n == "n_cells") *value = ctx->n_cells;
     else if (n == "allpairs_replicas") {
         int k = 0;

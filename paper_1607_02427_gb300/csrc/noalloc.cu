@@ -9,7 +9,7 @@
 // synchronisation cudaMalloc and cudaFree can cause.  They can still get
 // forces from this entry point.
 //
-// The static array is about 20 MiB and is reserved on every GPU that loads
+// The static array is about 21 MiB and is reserved on every GPU that loads
 // the library, until the process exits.  All calls on a device share it and
 // it keeps the last call's contents, so each call clears what must start at
 // zero (the status word, the replica index of every particle), and calls

@@ -1173,10 +1173,13 @@ __global__ void __launch_bounds__(SBLOCK, apply_blocks<T, COMP>())
             st.batch(nb);
         }
         if constexpr (REF) {
-            // the group's terms for the term kernel
+            // the group's terms for the term kernel: only the records that
+            // were stored (the region holds term_capw); on an overflow the
+            // evaluation is redone with a larger buffer
             if (lane == 0) {
+                const int stored_end = min(st.tcur, a.term_capw);
                 a.term_start[g] = (int)(st.region + gstart);
-                a.term_cnt[g] = st.tcur - gstart;
+                a.term_cnt[g] = max(0, stored_end - gstart);
                 if (st.tcur > a.term_capw) atomicMax(&a.status->term_overflow, st.tcur);
             }
         } else {

@@ -9,7 +9,11 @@ arrays, and a state whose forces are not finite.
 * two coincident particles give non-finite forces: DEM_ERR_NONFINITE;
 * after either error the context has no state (dem_step returns
   DEM_ERR_STATE), and a valid dem_set_state makes it usable again, with
-  forces matching the oracle.
+  forces matching the oracle;
+* a term buffer too small for the FP32 + two-sum SPLIT evaluation (one
+  record per warp) overflows: the evaluation is redone with a larger
+  buffer and gives the same forces and trajectory as one that never
+  overflowed.
 """
 import numpy as np
 import pytest
@@ -122,3 +126,30 @@ def test_noalloc_rejects_nonfinite(dem):
                                dev(s.shape_id, torch.int32), dev(pos, torch.float64),
                                dev(s.orient, torch.float64), 2, f, t)
     assert ei.value.code == dem.DEM_ERR_ARG and "particle 3" in str(ei.value)
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_term_buffer_overflow_retry(dem, dim):
+    import oracle
+    s = _system(dim)
+    out = []
+    for cap in (None, 1):
+        params = {"decomp": dem.DEM_DECOMP_SPLIT}
+        if cap:
+            params["term_cap"] = cap
+        with dem.DEM(s, dem.DEM_FP32_COMP, **params) as d:
+            f, t = d.forces()
+            e = d.particle_energy()
+            if cap:
+                assert d.get_param("term_cap") > cap
+                out_o = dict(force=f, torque=t, U=d.energy()[0], W=d.virial(), energy=e,
+                             counts=None)
+                assert_parity(force_errors(s, oracle.forces(s), out_o), dem.DEM_FP32_COMP,
+                              f"term overflow {dim}d")
+                d.set_param("term_cap", 1)          # overflow again inside a step call
+            d.step(30, 1e-3, dem.DEM_NVE)
+            out.append((f, t, e, d.state()))
+    for k in range(3):
+        np.testing.assert_array_equal(out[1][k], out[0][k])
+    for k in ("pos", "vel", "orient", "angmom"):
+        np.testing.assert_array_equal(out[1][3][k], out[0][3][k])
