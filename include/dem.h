@@ -229,10 +229,20 @@ int dem_get_box(dem_ctx *ctx, double *box);
  * close), pair forces, half kick, barostat and thermostat half steps.  NPT
  * calls run in chunks of "npt_chunk" steps; between chunks the boxes come
  * back to the host and the cell grids follow them.
+ * Execution: NVE and NVT calls on small systems (parameter "persistent")
+ * run as cooperative launches of one kernel that does many whole steps,
+ * with grid-wide barriers between the phases of a step; a list rebuild ends
+ * a launch, the list is rebuilt and the next launch continues.  In the FP32
+ * modes the result is bit-identical to the per-step kernels with the WARP
+ * decomposition; in FP64 it agrees with them to rounding.
+ * Other calls replay one captured CUDA graph per step ("graph").
  * Errors: DEM_ERR_ARG, DEM_ERR_STATE, DEM_ERR_NONFINITE,
  * DEM_ERR_NLIST_OVERFLOW (after an internal grow-and-retry from the state at
  * the start of the call), DEM_ERR_BOX (NPT: a box shrank by more than 5%
- * within a chunk or below twice the list cutoff), DEM_ERR_CUDA. */
+ * within a chunk or below twice the list cutoff), DEM_ERR_TIMEOUT (a barrier
+ * of the cooperative kernel waited longer than "persistent_wait_ms"; the
+ * state is restored to the start of the call and the context stays
+ * usable), DEM_ERR_CUDA. */
 int dem_step(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T);
 
 /* Evaluate forces, torques, energies and virials at the current state. */
@@ -276,6 +286,15 @@ int dem_set_box(dem_ctx *ctx, const double *box);
  *   "block"       threads per block of the pair kernel (0 = default)
  *   "graph"       1 = replay each step as a captured CUDA graph (default 1)
  *   "nlist_cap"   neighbour slots per particle (grown automatically, at most 768)
+ *   "persistent"  cooperative multi-step kernel for dem_step: -1 (default) as
+ *                 dem_autotune timed it, and before any dem_autotune for NVE
+ *                 and NVT calls on systems of at most 2048 particles; 1 for
+ *                 every NVE and NVT call; 0 never.  Not with "profile" on, nor
+ *                 for shapes of more than 32 vertices, edges or faces
+ *   "persistent_wait_ms"  limit of one barrier wait of that kernel (1000)
+ *   "persistent_test_stall"  testing: 1 = in the next cooperative launch one
+ *                 block never reaches the barriers, so the others' waits run
+ *                 out and dem_step returns DEM_ERR_TIMEOUT
  *   "term_cap"    DEM_FP32_COMP in the SPLIT decomposition: term records per
  *                 warp of the feature kernel (0 until first needed; default
  *                 sixteen per particle on average, at least 512; grown
@@ -288,6 +307,10 @@ int dem_set_box(dem_ctx *ctx, const double *box);
  *   "pair_ms_total"  summed pair-kernel time of the profiled steps (ms)
  *   "pair_launches"  number of profiled pair-kernel launches
  *   "launches"       kernel launches issued by this context so far
+ *   "persistent_used"  1 if the last dem_step ran the cooperative kernel
+ *   "persistent_auto"  dem_autotune's choice: 1 cooperative, 0 per-step
+ *                    kernels, -1 not timed
+ *   "autotune_step_ms_graph", "autotune_step_ms_persistent"  its step times
  *   "n_cells", "allpairs_replicas"  cell-list layout
  * Setting an unknown name or an invalid value returns DEM_ERR_ARG. */
 int dem_set_param(dem_ctx *ctx, const char *name, double value);
@@ -301,7 +324,11 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value);
  * one fixed with "split_group"); their mean times are readable as
  * parameters "autotune_ms_0" ... "autotune_ms_7".  Results are identical for
  * every choice up to floating-point summation order; the chosen one is the
- * "decomp", "block" and "split_group" parameters. */
+ * "decomp", "block" and "split_group" parameters.
+ * With "persistent" at -1 it then times a few NVT steps (dt = 1e-6, too short
+ * to rebuild the list) with the per-step kernels and with the cooperative
+ * multi-step kernel from the same state, keeps the faster for dem_step, and
+ * puts the state back as it was. */
 int dem_autotune(dem_ctx *ctx);
 
 /* Work counters of one force evaluation at the current state (host array of

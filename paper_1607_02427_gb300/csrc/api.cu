@@ -527,6 +527,20 @@ struct dem_ctx {
     double prof_ms = 0.0;
     long long prof_n = 0;
     std::vector<float> tune_ms;   // pair-kernel ms of each autotuner candidate
+    // cooperative multi-step kernel (persistent.cu): -1 = as dem_autotune
+    // timed it (before that: for systems of at most COOP_AUTO_MAX_N
+    // particles), 0 = never, 1 = whenever it can run
+    int persistent = -1;
+    int coop_auto = -1;               // -1: by size; 0 / 1: chosen by dem_autotune
+    float tune_step_ms[2] = {-1.f, -1.f};   // dem_autotune: ms per step, graph / cooperative
+    bool coop_used = false;           // the last dem_step ran the cooperative kernel
+    double coop_wait_ms = 1000.0;     // barrier wait limit
+    int coop_test_stall = 0;          // test hook: the next launch stalls one block
+    CoopCtl *coop_ctl = nullptr;
+    void *coop_part = nullptr;
+    size_t coop_part_bytes = 0;
+    unsigned char *coop_act = nullptr;
+    size_t coop_act_bytes = 0;
     std::string err;
 };
 
@@ -549,6 +563,15 @@ int set_err(dem_ctx *c, int code, const char *fmt, ...) {
             return set_err(ctx, e_ == cudaErrorMemoryAllocation ? DEM_ERR_NOMEM : DEM_ERR_CUDA, \
                            "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
+
+// Host-to-device copy ordered on the context's stream (a non-blocking stream:
+// copies on the legacy stream would not be ordered with its kernels), done
+// when it returns, so that the host buffer may go.
+cudaError_t upload(dem_ctx *ctx, void *dst, const void *src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e;
+}
 
 template <class T> cudaError_t dalloc(T **p, size_t count) {
     *p = nullptr;
@@ -576,23 +599,22 @@ int upload_tables(dem_ctx *ctx) {
     if (ctx->mask_words > 1) ctx->decomp = DEM_DECOMP_THREAD;
     ctx->n_geoms = (int)t.geoms.size();
     CK(dalloc(&ctx->d_geoms, t.geoms.size()));
-    CK(cudaMemcpy(ctx->d_geoms, t.geoms.data(), sizeof(Geom) * t.geoms.size(), cudaMemcpyHostToDevice));
+    CK(upload(ctx, ctx->d_geoms, t.geoms.data(), sizeof(Geom) * t.geoms.size()));
     CK(dalloc(&ctx->d_itable, t.itab.size()));
-    CK(cudaMemcpy(ctx->d_itable, t.itab.data(), sizeof(int) * t.itab.size(), cudaMemcpyHostToDevice));
+    CK(upload(ctx, ctx->d_itable, t.itab.data(), sizeof(int) * t.itab.size()));
     if (ctx->precision == DEM_FP64) {
         CK(dalloc((double4_32a **)&ctx->d_table, t.td.size()));
-        CK(cudaMemcpy(ctx->d_table, t.td.data(), sizeof(double4_32a) * t.td.size(), cudaMemcpyHostToDevice));
+        CK(upload(ctx, ctx->d_table, t.td.data(), sizeof(double4_32a) * t.td.size()));
     } else {
         CK(dalloc((float4 **)&ctx->d_table, t.tf.size()));
-        CK(cudaMemcpy(ctx->d_table, t.tf.data(), sizeof(float4) * t.tf.size(), cudaMemcpyHostToDevice));
+        CK(upload(ctx, ctx->d_table, t.tf.data(), sizeof(float4) * t.tf.size()));
         if (ctx->precision == DEM_FP32_COMP) {
             CK(dalloc(&ctx->d_table_lo, t.tf_lo.size()));
-            CK(cudaMemcpy(ctx->d_table_lo, t.tf_lo.data(), sizeof(float4) * t.tf_lo.size(),
-                          cudaMemcpyHostToDevice));
+            CK(upload(ctx, ctx->d_table_lo, t.tf_lo.data(), sizeof(float4) * t.tf_lo.size()));
         }
     }
     CK(dalloc(&ctx->d_shapes, t.shapes.size()));
-    CK(cudaMemcpy(ctx->d_shapes, t.shapes.data(), sizeof(ShapeDev) * t.shapes.size(), cudaMemcpyHostToDevice));
+    CK(upload(ctx, ctx->d_shapes, t.shapes.data(), sizeof(ShapeDev) * t.shapes.size()));
     return DEM_OK;
 }
 
@@ -691,7 +713,7 @@ int setup_replicas(dem_ctx *ctx) {
         CK(dalloc(&ctx->partial, 3 * (size_t)ctx->n_chunks));
         free_graph(ctx);
     }
-    CK(cudaMemcpy(ctx->chunk_rep, chunk_rep.data(), sizeof(int) * ctx->n_chunks, cudaMemcpyHostToDevice));
+    CK(upload(ctx, ctx->chunk_rep, chunk_rep.data(), sizeof(int) * ctx->n_chunks));
     ctx->reps = reps;
     int want_cap = (int)(2.0 * worst_ratio + 16);
     want_cap = (want_cap + 7) / 8 * 8;
@@ -712,7 +734,7 @@ int setup_replicas(dem_ctx *ctx) {
         CK(dalloc(&ctx->cell_slots, (size_t)std::max(cell_off, 1) * ctx->cell_cap));
         free_graph(ctx);
     }
-    CK(cudaMemcpy(ctx->d_reps, reps.data(), sizeof(Rep) * ctx->R, cudaMemcpyHostToDevice));
+    CK(upload(ctx, ctx->d_reps, reps.data(), sizeof(Rep) * ctx->R));
     return DEM_OK;
 }
 
@@ -992,10 +1014,9 @@ int snapshot(dem_ctx *ctx, bool restore) {
         CK(cudaMemcpyAsync(ctx->snap_reps, ctx->d_reps, sizeof(Rep) * ctx->R, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (restore) {
-        // float copy of the orientations
-        CK(launch_prepare_state(ctx->N, ctx->dim, ctx->pos, ctx->quat, ctx->quatf, ctx->quatf_lo,
-                                    ctx->xff, ctx->angmom,
-                                ctx->rep, ctx->d_reps, 0, ctx->stream));
+        // the float copies of the restored state (left bit for bit as saved)
+        CK(launch_refresh_copies(ctx->N, ctx->pos, ctx->quat, ctx->quatf, ctx->quatf_lo, ctx->xff,
+                                 ctx->stream));
     }
     return DEM_OK;
 }
@@ -1099,7 +1120,7 @@ void dem_destroy(dem_ctx *ctx) {
                     ctx->snap, ctx->snap_thermo, ctx->snap_reps, ctx->ket, ctx->chunk_rep,
                     ctx->partial, ctx->posf, ctx->recs, ctx->rec_count, ctx->quatf_lo, ctx->xff,
                     ctx->d_table_lo, ctx->term_a, ctx->term_b, ctx->term_info, ctx->term_start,
-                    ctx->term_cnt};
+                    ctx->term_cnt, ctx->coop_ctl, ctx->coop_part, ctx->coop_act};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
@@ -1185,22 +1206,22 @@ int dem_create(dem_ctx **out, const dem_shape *shapes, int n_shapes, double epsi
             CK(dalloc(&ctx->quatf_lo, n));
             CK(dalloc(&ctx->xff, 2 * n));
         }
-        CK(cudaMemset(ctx->delta, 0, sizeof(float4) * n));
+        CK(cudaMemsetAsync(ctx->delta, 0, sizeof(float4) * n, ctx->stream));
         CK(dalloc(&ctx->shape, n)); CK(dalloc(&ctx->rep, n)); CK(dalloc(&ctx->nn, n));
         CK(dalloc(&ctx->energy, n)); CK(dalloc(&ctx->virial, 6 * n)); CK(dalloc(&ctx->ke, n)); CK(dalloc(&ctx->ket, n));
         CK(dalloc(&ctx->staging, 4 * n));
         CK(dalloc(&ctx->red, 6 * (size_t)ctx->R)); CK(dalloc(&ctx->scale3, 3 * (size_t)ctx->R));
         CK(dalloc(&ctx->status, 1)); CK(dalloc(&ctx->thermo, (size_t)ctx->R));
         CK(dalloc(&ctx->d_reps, (size_t)ctx->R)); CK(dalloc(&ctx->d_counters, DEM_N_COUNTERS));
-        CK(cudaMemset(ctx->status, 0, sizeof(Status)));
-        CK(cudaMemset(ctx->thermo, 0, sizeof(Thermo) * ctx->R));
-        CK(cudaMemset(ctx->nn, 0, sizeof(int) * n));
-        CK(cudaMemset(ctx->force, 0, sizeof(double4_32a) * n));
-        CK(cudaMemset(ctx->torque, 0, sizeof(double4_32a) * n));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(Status), ctx->stream));
+        CK(cudaMemsetAsync(ctx->thermo, 0, sizeof(Thermo) * ctx->R, ctx->stream));
+        CK(cudaMemsetAsync(ctx->nn, 0, sizeof(int) * n, ctx->stream));
+        CK(cudaMemsetAsync(ctx->force, 0, sizeof(double4_32a) * n, ctx->stream));
+        CK(cudaMemsetAsync(ctx->torque, 0, sizeof(double4_32a) * n, ctx->stream));
         std::vector<int> rep(n);
         for (int r = 0; r < ctx->R; ++r)
             for (int k = 0; k < ctx->sizes[r]; ++k) rep[ctx->offs[r] + k] = r;
-        CK(cudaMemcpy(ctx->rep, rep.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        CK(upload(ctx, ctx->rep, rep.data(), sizeof(int) * n));
         return upload_tables(ctx);
     }();
     if (rc) {
@@ -1280,6 +1301,20 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
             int rc = force_rebuild(ctx);
             if (rc) return rc;
         }
+    } else if (n == "persistent") {
+        int v = (int)value;
+        if (v < -1 || v > 1) return set_err(ctx, DEM_ERR_ARG, "bad persistent (-1, 0 or 1)");
+        if (v == 1 && ctx->mask_words > 1)
+            return set_err(ctx, DEM_ERR_ARG, "the cooperative step kernel takes shapes of at "
+                           "most 32 vertices, edges and faces");
+        ctx->persistent = v;
+        ctx->coop_auto = -1;
+    } else if (n == "persistent_wait_ms") {
+        if (!(value >= 1.0 && value <= 10000.0))
+            return set_err(ctx, DEM_ERR_ARG, "persistent_wait_ms must be in [1, 10000]");
+        ctx->coop_wait_ms = value;
+    } else if (n == "persistent_test_stall") {
+        ctx->coop_test_stall = value != 0;
     } else if (n == "term_cap") {
         int c = (int)value;
         if (c < 1 || c > (1 << 24)) return set_err(ctx, DEM_ERR_ARG, "bad term_cap");
@@ -1316,6 +1351,12 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
     }
     else if (n == "nlist_cap") *value = ctx->cap;
     else if (n == "term_cap") *value = ctx->term_capw;
+    else if (n == "persistent") *value = ctx->persistent;
+    else if (n == "persistent_used") *value = ctx->coop_used;
+    else if (n == "persistent_auto") *value = ctx->coop_auto;
+    else if (n == "autotune_step_ms_graph") *value = ctx->tune_step_ms[0];
+    else if (n == "autotune_step_ms_persistent") *value = ctx->tune_step_ms[1];
+    else if (n == "persistent_wait_ms") *value = ctx->coop_wait_ms;
     else if (n == "n_cells") *value = ctx->n_cells;
     else if (n == "allpairs_replicas") {
         int k = 0;
@@ -1468,6 +1509,90 @@ namespace {
 // n steps with no host work in between (graph replays or launches), with the
 // overflow retry: the state is snapshotted, and after a list or cell overflow
 // the capacities grow and the steps are replayed from the snapshot.
+// ---- cooperative multi-step kernel ----
+constexpr int COOP_AUTO_MAX_N = 2048;
+
+// Whether dem_step runs the cooperative kernel (NVE and NVT, one-word
+// feature masks, no pair-kernel profiling), and its grid (0: it cannot run).
+int coop_plan(dem_ctx *ctx, int ensemble) {
+    if (ctx->persistent == 0 || ensemble == DEM_NPT || ctx->mask_words != 1 || ctx->profile)
+        return 0;
+    if (ctx->persistent < 0 &&
+        (ctx->coop_auto == 0 || (ctx->coop_auto < 0 && ctx->N > COOP_AUTO_MAX_N)))
+        return 0;
+    PairArgs pa = pair_args(ctx);
+    return coop_grid(ctx->precision, ctx->dim, ctx->N, ctx->cap, pair_smem_bytes(pa, ctx->precision));
+}
+
+int ensure_coop(dem_ctx *ctx) {
+    if (!ctx->coop_ctl) CK(dalloc(&ctx->coop_ctl, 1));
+    const size_t pb = coop_partial_bytes(ctx->precision, ctx->N, ctx->cap);
+    if (pb > ctx->coop_part_bytes) {
+        cudaFree(ctx->coop_part);
+        ctx->coop_part = nullptr;
+        ctx->coop_part_bytes = 0;
+        CK(cudaMalloc(&ctx->coop_part, pb));
+        ctx->coop_part_bytes = pb;
+    }
+    const size_t ab = (size_t)ctx->cap * ctx->N;
+    if (ab > ctx->coop_act_bytes) {
+        cudaFree(ctx->coop_act);
+        ctx->coop_act = nullptr;
+        ctx->coop_act_bytes = 0;
+        CK(cudaMalloc((void **)&ctx->coop_act, ab));
+        ctx->coop_act_bytes = ab;
+    }
+    return DEM_OK;
+}
+
+// n steps in cooperative launches.  A launch runs until its steps are done
+// or a list rebuild is due after some step's first half; then the list is
+// rebuilt here and the next launch starts at that step's pair phase.
+int coop_run(dem_ctx *ctx, int grid, int n, double dt, int ensemble, double kT, double tau_T) {
+    int rc = ensure_coop(ctx);
+    if (rc) return rc;
+    const PairArgs pa = pair_args(ctx);
+    const NlistArgs na = nlist_args(ctx);
+    const size_t smem = pair_smem_bytes(pa, ctx->precision);
+    int remaining = n, resume = 0;
+    while (remaining > 0) {
+        CK(cudaMemsetAsync(ctx->coop_ctl, 0, sizeof(CoopCtl), ctx->stream));
+        CoopArgs c = {};
+        c.p = pa;
+        c.s = step_args(ctx, dt, ensemble, kT, tau_T);
+        c.ctl = ctx->coop_ctl;
+        c.part = ctx->coop_part;
+        c.act = ctx->coop_act;
+        c.n_steps = remaining;
+        c.resume = resume;
+        c.half_skin2 = na.half_skin2;
+        c.limit_ns = (long long)(ctx->coop_wait_ms * 1e6);
+        c.test_stall = ctx->coop_test_stall;
+        ctx->coop_test_stall = 0;
+        CK(launch_coop_steps(c, ctx->precision, ctx->dim, grid, smem, ctx->stream));
+        ctx->launches += 1;
+        CoopCtl h;
+        CK(cudaMemcpyAsync(&h, ctx->coop_ctl, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (h.timeout || h.abort)
+            return set_err(ctx, DEM_ERR_TIMEOUT, "a barrier of the cooperative step kernel waited "
+                           "more than %.0f ms", ctx->coop_wait_ms);
+        if (h.stop != 1) {
+            if (h.steps_done != remaining)
+                return set_err(ctx, DEM_ERR_CUDA, "the cooperative step kernel ended after %d of "
+                               "%d steps", h.steps_done, remaining);
+            break;
+        }
+        // the list build of the step whose first half just ran
+        CK(launch_cells(na, ctx->n_cells, ctx->stream));
+        CK(launch_nlist(na, ctx->stream));
+        ctx->launches += 2;
+        remaining -= h.steps_done;
+        resume = 1;
+    }
+    return DEM_OK;
+}
+
 int step_run(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau_T) {
     int rc;
     for (int attempt = 0; attempt < 4; ++attempt) {
@@ -1491,7 +1616,20 @@ int step_run(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau
             rc = ensure_events(ctx, 2 * (size_t)n);
             if (rc) return rc;
         }
-        if (ctx->use_graph) {
+        const int coop = coop_plan(ctx, ensemble);
+        ctx->coop_used = coop > 0;
+        if (coop > 0) {
+            rc = coop_run(ctx, coop, n, dt, ensemble, kT, tau_T);
+            if (rc == DEM_ERR_TIMEOUT) {
+                // the state from before the call, with its list and forces
+                const std::string msg = ctx->err;
+                if (snapshot(ctx, true) == DEM_OK && force_rebuild(ctx) == DEM_OK)
+                    compute_forces(ctx);
+                ctx->err = msg;
+                return DEM_ERR_TIMEOUT;
+            }
+            if (rc) return rc;
+        } else if (ctx->use_graph) {
             rc = get_graph(ctx, dt, ensemble, kT, tau_T);
             if (rc) return rc;
             for (int s = 0; s < n; ++s) {
@@ -1542,6 +1680,46 @@ int step_run(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau
         return DEM_OK;
     }
     return set_err(ctx, DEM_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+}
+
+// The per-step kernels (graph replays) against the cooperative multi-step
+// kernel: a few NVT steps of each from the same state, timed with CUDA
+// events, then the state from before.  The steps are short (dt = 1e-6), so
+// neither run rebuilds its list.
+int tune_persistent(dem_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1) {
+    ctx->tune_step_ms[0] = ctx->tune_step_ms[1] = -1.f;
+    if (ctx->mask_words != 1 || ctx->profile || coop_grid(ctx->precision, ctx->dim, ctx->N, ctx->cap,
+                                                         pair_smem_bytes(pair_args(ctx), ctx->precision)) < 1)
+        return DEM_OK;
+    const double dt = 1e-6, kT = 1.0, tau = 1.0;
+    const int warm = 2, steps = 20;
+    int rc = snapshot(ctx, false);
+    if (rc) return rc;
+    const int keep_persistent = ctx->persistent;
+    float ms[2] = {-1.f, -1.f};
+    for (int mode = 0; mode < 2 && rc == DEM_OK; ++mode) {
+        ctx->persistent = mode;
+        rc = step_run(ctx, warm, dt, DEM_NVT, kT, tau);
+        if (rc == DEM_OK) rc = snapshot(ctx, true);   // back to the state before the warm-up
+        if (rc != DEM_OK) break;
+        CK(cudaEventRecord(e0, ctx->stream));
+        rc = step_run(ctx, steps, dt, DEM_NVT, kT, tau);
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        if (rc == DEM_OK) {
+            CK(cudaEventElapsedTime(&ms[mode], e0, e1));
+            ms[mode] /= steps;
+            rc = snapshot(ctx, true);
+        }
+    }
+    ctx->persistent = keep_persistent;
+    if (rc != DEM_OK) return rc;
+    ctx->tune_step_ms[0] = ms[0];
+    ctx->tune_step_ms[1] = ms[1];
+    ctx->coop_auto = ms[1] < ms[0] ? 1 : 0;
+    rc = force_rebuild(ctx);
+    if (rc) return rc;
+    return compute_forces(ctx);
 }
 
 // After NPT steps: the boxes come back to the host, the cell grids and list
@@ -1782,15 +1960,16 @@ int dem_autotune(dem_ctx *ctx) {
         ctx->tune_ms.push_back(ms);
         if (ms < best) { best = ms; pick = c; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     ctx->launches += kernels;
     ctx->decomp = pick.decomp;
     ctx->block = pick.block;
     ctx->split_G = pick.group ? pick.group : G_keep;
     free_graph(ctx);
-    // the last timed launch left the forces of the current state in place
-    return compute_forces(ctx);
+    rc = compute_forces(ctx);
+    if (rc == DEM_OK && ctx->persistent < 0) rc = tune_persistent(ctx, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 }  // extern "C"

@@ -235,6 +235,38 @@ struct StepArgs {
     float4 *quatf_lo, *xff;  // FP32 + two-sum: hi + lo state (NULL otherwise)
 };
 
+// Cooperative multi-step kernel (persistent.cu): control block in device
+// memory, cleared by the host before each launch.
+struct CoopCtl {
+    unsigned bar_count, bar_gen;   // grid barrier: arrivals, generation
+    int abort;                     // a block gave up waiting: every block returns
+    int timeout;                   // the reason was a wait past the time limit
+    int steps_done;                // steps completed (a stop: its first half done)
+    int stop;                      // 1: stopped for a list rebuild after a first half step
+    int kmax;                      // longest neighbour list of the launch
+    unsigned maxd[2];              // per-step maximum squared displacement (float bits),
+                                   // by step parity
+};
+
+struct CoopArgs {
+    PairArgs p;
+    StepArgs s;
+    CoopCtl *ctl;
+    void *part;                    // partial sums per list entry: component c of entry
+                                   // (i, k) at [(c * cap + k) * n + i] (float or double)
+    unsigned char *act;            // entry (i, k) is an active pair: act[k * n + i]
+    int n_steps;
+    int resume;                    // 1: the first step starts at the pair phase
+    float half_skin2;              // rebuild threshold (skin/2)^2
+    long long limit_ns;            // barrier wait limit
+    int test_stall;                // test hook: block 0 never reaches a barrier
+};
+size_t coop_partial_bytes(int precision, int n, int cap);
+// Blocks of the cooperative launch (0 when the kernel cannot run).
+int coop_grid(int precision, int dim, int n, int cap, size_t smem);
+cudaError_t launch_coop_steps(const CoopArgs &c, int precision, int dim, int grid, size_t smem,
+                              cudaStream_t s);
+
 // ---- launch wrappers (pair.cu, nlist.cu, integrate.cu) ----
 cudaError_t launch_pair(const PairArgs &a, int precision, int decomp, int block, bool count,
                         cudaStream_t s);
@@ -264,6 +296,9 @@ cudaError_t launch_prepare_state(int n, int dim, double4_32a *pos, double4_32a *
                                  float4 *quatf_lo, float4 *xff,
                                  double4_32a *angmom, const int *rep, const Rep *reps,
                                  int world_to_body, cudaStream_t s);
+// FP32 / float-float copies of an FP64 state restored unchanged (snapshots).
+cudaError_t launch_refresh_copies(int n, const double4_32a *pos, const double4_32a *quat,
+                                  float4 *quatf, float4 *quatf_lo, float4 *xff, cudaStream_t s);
 cudaError_t launch_export_state(int n, int dim, const double4_32a *pos, const double4_32a *quat,
                                 const double4_32a *vel, const double4_32a *angmom, double *pos_out,
                                 double *orient_out, double *vel_out, double *angmom_out,

@@ -11,7 +11,10 @@ axis free-rotor splitting, Nose-Hoover Trotter split), through the C ABI.
   Conservation"); the NVT extended energy is conserved.
 * The captured-graph path equals the launch-by-launch path bit for bit, and
   a neighbour-list overflow retried from the start of the call gives the
-  same trajectory bit for bit.
+  same trajectory bit for bit (here through the cooperative multi-step
+  kernel, the default for systems this small).
+* Every trajectory case runs the step kernels with three decompositions and
+  the cooperative multi-step kernel.
 """
 import numpy as np
 import pytest
@@ -72,18 +75,25 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("decomp", [1, 3, 4], ids=["thread", "staged", "split"])
+# the step kernels with three pair-kernel decompositions, and the cooperative
+# multi-step kernel
+MODES = {"thread": {"decomp": 1, "persistent": 0}, "staged": {"decomp": 3, "persistent": 0},
+         "split": {"decomp": 4, "persistent": 0}, "persistent": {"persistent": 1}}
+
+
+@pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("precision,tol", [(0, 1e-9), (2, 1e-4), (1, 1e-4)],
                          ids=["fp64", "fp32c", "fp32"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_trajectory_matches_oracle(dem, name, precision, tol, decomp):
+def test_trajectory_matches_oracle(dem, name, precision, tol, mode):
     mk, ens = CASES[name]
     s = mk()
     n, dt = 100, 1e-3
     ref, tr = oracle.run(s, n, dt, ensemble=ens, kT=1.0, tau=0.5)
     assert tr[0, :, 2].max() > 0.1, "the run must have interactions"
-    with dem.DEM(s, precision, decomp=decomp) as d:
+    with dem.DEM(s, precision, **MODES[mode]) as d:
         d.step(n, dt, dem.DEM_NVT if ens == "nvt" else dem.DEM_NVE, kT=1.0, tau_T=0.5)
+        assert d.get_param("persistent_used") == (mode == "persistent")
         st = d.state()
         U, K, H = d.energy()
     _compare_states(s, st, ref, tol, 10 * tol)
@@ -138,7 +148,7 @@ def test_graph_equals_eager(dem):
     s = _cluster([W.cube(1.0, 0.15)], 150, [14.0] * 3, 53, sigma=0.3, gap=(0.95, 1.1), gap_min=0.9)
     out = []
     for graph in (1, 0):
-        with dem.DEM(s, dem.DEM_FP32_COMP, graph=graph) as d:
+        with dem.DEM(s, dem.DEM_FP32_COMP, graph=graph, persistent=0) as d:
             d.step(50, 1e-3, dem.DEM_NVT, kT=1.0, tau_T=0.5)
             out.append(d.state())
     for k in ("pos", "vel", "orient", "angmom", "thermo"):
@@ -156,7 +166,7 @@ def test_graph_eager_profiling(dem, ens):
     e = dem.DEM_NVE if ens == "nve" else dem.DEM_NVT
     out = []
     for graph, prof in ((1, 0), (1, 1), (0, 1), (0, 0)):
-        with dem.DEM(small, dem.DEM_FP32_COMP, graph=graph) as d:
+        with dem.DEM(small, dem.DEM_FP32_COMP, graph=graph, persistent=0) as d:
             d.set_param("profile", prof)
             for n in (7, 1, 12):
                 d.step(n, 1e-3, e, kT=1.0, tau_T=0.5)

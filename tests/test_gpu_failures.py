@@ -134,7 +134,7 @@ def test_term_buffer_overflow_retry(dem, dim):
     s = _system(dim)
     out = []
     for cap in (None, 1):
-        params = {"decomp": dem.DEM_DECOMP_SPLIT}
+        params = {"decomp": dem.DEM_DECOMP_SPLIT, "persistent": 0}
         if cap:
             params["term_cap"] = cap
         with dem.DEM(s, dem.DEM_FP32_COMP, **params) as d:
