@@ -1015,11 +1015,17 @@ template <class T, bool COMP> constexpr int apply_blocks() {
 
 // ---- SPLIT, FP32 + two-sum: the term kernel ----
 // One warp per 32 consecutive particles (32 / G groups of the feature
-// kernel): the groups' terms, 32 at a time, are refined in float-float
-// (refined_values) and added by their owners' lanes in the order the feature
-// kernel found them; then each lane writes its particle's outputs.  The
-// kernel holds only this code, so the refinement runs on full warps out of
-// a small instruction footprint, with its own registers.
+// kernel).  The terms of its groups form one pool; each chunk of up to
+// TERM_CHUNK of them is put in order of term kind (stable: within a kind,
+// the order the feature kernel found them), so that the lanes of a round
+// mostly run the same code, and pooling keeps the rounds full when a group
+// has few terms.  32 at a time the terms are refined in float-float
+// (refined_values) and added by their owners' lanes in that order; then
+// each lane writes its particle's outputs.  The kernel holds only this
+// code, so the refinement runs out of a small instruction footprint, with
+// its own registers.
+constexpr int TERM_CHUNK = 256;   // terms of a warp sorted at a time
+
 template <int DIM>
 __global__ void __launch_bounds__(SBLOCK, 4) k_pair_terms(const PairArgs a) {
     extern __shared__ __align__(32) unsigned char smem[];
@@ -1030,31 +1036,70 @@ __global__ void __launch_bounds__(SBLOCK, 4) k_pair_terms(const PairArgs a) {
     const float4 *tlo;
     stage_table_lo(a, smem + tb, &tlo);
     stage_tables<float>(a, tab, geo, itab);
-    int *gmask = reinterpret_cast<int *>(smem + tb + table_lo_bytes(a, true)) + 32 * (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, w = threadIdx.x >> 5;
+    int *wsm = reinterpret_cast<int *>(smem + tb + table_lo_bytes(a, true)) + (32 + 2 * TERM_CHUNK + 16) * w;
+    int *gmask = wsm;                       // 32
+    int *srt_r = wsm + 32;                  // TERM_CHUNK: record of the sorted term
+    int *srt_o = srt_r + TERM_CHUNK;        // TERM_CHUNK: its owner (particle lane)
+    int *goff = srt_o + TERM_CHUNK;         // 8 group offsets in the pool, 8 group starts
     gmask[lane] = 0;
     __syncthreads();
     const FFTab ft = {tab, tlo, itab};
     const float eps = (float)a.eps;
-    const int G = a.group;
+    const int G = a.group, ng = 32 / G;
     const int nwarps = gridDim.x * wpb;
-    for (int base = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < a.n; base += nwarps * 32) {
+    for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
         SumSink<float, true> S;
         S.zero();
-        for (int h = 0; h < 32 / G && base + h * G < a.n; ++h) {
-            const int g = base / G + h;
-            const int start = a.term_start[g], cnt = a.term_cnt[g];
-            for (int t0 = 0; t0 < cnt; t0 += 32) {
-                const bool has = t0 + lane < cnt;
+        // the pool: the terms of the warp's groups, group after group
+        int cnt_me = 0, start_me = 0;
+        if (lane < ng && base + lane * G < a.n) {
+            const int g = base / G + lane;
+            cnt_me = a.term_cnt[g];
+            start_me = a.term_start[g];
+        }
+        int total;
+        const int off_me = warp_excl_scan(cnt_me, lane, &total);
+        if (lane < 8) {
+            goff[lane] = lane < ng ? off_me : 0x7fffffff;
+            goff[8 + lane] = start_me;
+        }
+        __syncwarp();
+        for (int c0 = 0; c0 < total; c0 += TERM_CHUNK) {
+            const int nc = min(TERM_CHUNK, total - c0);
+            // counting sort of the chunk by term kind (stable)
+            int base_k = 0;
+            for (int kind = 0; kind < 8; ++kind) {   // every 3-bit kind: each term is placed
+                for (int m = 0; m < nc; m += 32) {
+                    const int p = c0 + m + lane;
+                    bool mine = false;
+                    int r = 0, h = 0;
+                    if (m + lane < nc) {
+                        while (h + 1 < ng && goff[h + 1] <= p) ++h;
+                        r = goff[8 + h] + (p - goff[h]);
+                        mine = ((__float_as_int(a.term_a[r].w) >> 5) & 7) == kind;
+                    }
+                    const unsigned bm = __ballot_sync(FULL, mine);
+                    if (mine) {
+                        const int q = base_k + __popc(bm & ((1u << lane) - 1u));
+                        srt_r[q] = r;
+                        srt_o[q] = h * G + (a.term_info[r] & 255);
+                    }
+                    base_k += __popc(bm);
+                }
+            }
+            __syncwarp();
+            for (int t0 = 0; t0 < nc; t0 += 32) {
+                const bool has = t0 + lane < nc;
                 int owner = 32 + lane;            // lanes without a term: distinct keys
                 bool ok = false;
                 ff vf[6];
                 float v[7];
                 if (has) {
-                    const int r = start + t0 + lane;
+                    const int r = srt_r[t0 + lane];
+                    owner = srt_o[t0 + lane];
                     const float4 sp = a.term_a[r], sr = a.term_b[r];
                     const int code = __float_as_int(sp.w), info = a.term_info[r];
-                    owner = h * G + (info & 255);
                     const TermSpec ts = {(code >> 5) & 7, (code >> 8) & 127, (code >> 15) & 127,
                                          {(code >> 26) & 1, (code >> 22) & 15, sp.y}, sp.x, sp.y,
                                          (info >> 24) & 1};
@@ -1068,7 +1113,7 @@ __global__ void __launch_bounds__(SBLOCK, 4) k_pair_terms(const PairArgs a) {
 #pragma unroll
                     for (int k = 0; k < 7; ++k) v[k] = 0.f;
                 }
-                // each owner's lane adds its terms in order
+                // each owner's lane adds its terms in the round's order
                 const unsigned grp = __match_any_sync(FULL, owner);
                 if (has && lane == __ffs(grp) - 1) gmask[owner] = (int)grp;
                 __syncwarp();
@@ -1243,7 +1288,7 @@ cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, 
     }
     if constexpr (COMP && std::is_same<T, float>::value) {
         // the term kernel: one warp per 32 particles
-        const size_t smem3 = t + table_lo_bytes(a, true) + (SBLOCK / 32) * 32 * sizeof(int);
+        const size_t smem3 = t + table_lo_bytes(a, true) + (SBLOCK / 32) * (32 + 2 * TERM_CHUNK + 16) * sizeof(int);
         auto kernel = k_pair_terms<DIM>;
         if (smem3 > 48 * 1024)
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
