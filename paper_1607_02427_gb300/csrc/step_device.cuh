@@ -12,6 +12,43 @@
 namespace dem {
 namespace {
 
+// Conversions between double and float by integer operations on the
+// IEEE-754 fields, with the results of the conversion instructions (round to
+// nearest, ties to even): those run on the FP64 pipe, a small fraction of the
+// FP32 rate on this part, and the first half step makes about forty per
+// particle.  Results outside the normal float range (subnormal, overflow,
+// infinities, NaN), which the state never produces, take the instruction.
+__device__ __forceinline__ float f32_of(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    const int fe = (int)((u >> 52) & 0x7ff) - 896;          // float exponent field
+    if (fe >= 1 && fe <= 254) {
+        const unsigned long long m = u & 0xfffffffffffffull;
+        const unsigned mant = (unsigned)(m >> 29);
+        const unsigned long long rest = m & 0x1fffffffull;   // the 29 bits rounded off
+        unsigned r = (unsigned)fe << 23 | mant;
+        if (rest > 0x10000000ull || (rest == 0x10000000ull && (mant & 1u))) r += 1u;  // carries into the exponent
+        return __uint_as_float(sign | r);
+    }
+    if ((u << 1) == 0ull) return __uint_as_float(sign);     // signed zero
+    return (float)x;
+}
+__device__ __forceinline__ double f64_of(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    if ((b << 1) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xffu) return (double)x;
+    return __longlong_as_double((long long)(sign | (unsigned long long)(e + 896u) << 52 |
+                                            (unsigned long long)(b & 0x7fffffu) << 29));
+}
+// x = h + l (h = x rounded to float, l = the rest rounded to float)
+__device__ __forceinline__ void split_ff_dev(double x, float *h, float *l) {
+    const float hi = f32_of(x);
+    *h = hi;
+    *l = f32_of(x - f64_of(hi));
+}
+
 __device__ __forceinline__ void quat_rotate_body(double4_32a &q, int k, double c, double s) {
     // r = (c, s e_k); q <- q (x) r ; q = (x:w, y:x, z:y, w:z)
     double w1 = q.x, x1 = q.y, y1 = q.z, z1 = q.w;
@@ -91,8 +128,8 @@ __device__ __forceinline__ void sincosm1_f(float h, float *s, float *cm1) {
 // rounding is of order 1e-7 h: far below the FP32 force error.
 __device__ __forceinline__ void free_rotor_f32(double4_32a &q, double4_32a &L, const double *invI,
                                                double dt) {
-    const float ii[3] = {(float)invI[0], (float)invI[1], (float)invI[2]};
-    float Lc[3] = {(float)L.x, (float)L.y, (float)L.z};
+    const float ii[3] = {f32_of(invI[0]), f32_of(invI[1]), f32_of(invI[2])};
+    float Lc[3] = {f32_of(L.x), f32_of(L.y), f32_of(L.z)};
     float dL[3] = {0.f, 0.f, 0.f};
     float rw = 0.f, rv[3] = {0.f, 0.f, 0.f};
     const float hd = (float)(0.25 * dt);
@@ -122,13 +159,13 @@ __device__ __forceinline__ void free_rotor_f32(double4_32a &q, double4_32a &L, c
         rv[0] = nv[0]; rv[1] = nv[1]; rv[2] = nv[2];
     }
     // q rho in FP32, added to the FP64 quaternion; q = (x: w, y: x, z: y, w: z)
-    const float qw = (float)q.x, qx = (float)q.y, qy = (float)q.z, qz = (float)q.w;
+    const float qw = f32_of(q.x), qx = f32_of(q.y), qy = f32_of(q.z), qz = f32_of(q.w);
     const float dw = qw * rw - (qx * rv[0] + qy * rv[1] + qz * rv[2]);
     const float dx = qw * rv[0] + rw * qx + (qy * rv[2] - qz * rv[1]);
     const float dy = qw * rv[1] + rw * qy + (qz * rv[0] - qx * rv[2]);
     const float dz = qw * rv[2] + rw * qz + (qx * rv[1] - qy * rv[0]);
-    q.x += (double)dw; q.y += (double)dx; q.z += (double)dy; q.w += (double)dz;
-    L.x += (double)dL[0]; L.y += (double)dL[1]; L.z += (double)dL[2];
+    q.x += f64_of(dw); q.y += f64_of(dx); q.z += f64_of(dy); q.w += f64_of(dz);
+    L.x += f64_of(dL[0]); L.y += f64_of(dL[1]); L.z += f64_of(dL[2]);
 }
 
 // x mapped into [0, L) (invL = 1/L)
@@ -161,8 +198,8 @@ __device__ __forceinline__ float since_build(const StepArgs &a, const Rep &rp, i
         const double d = sqrt(d2) + (double)rp.disp_pad;
         d2 = d * d;
     }
-    a.delta[i] = make_float4((float)dx, (float)dy, (float)dz, __int_as_float(a.shape[i]));
-    return (float)d2;
+    a.delta[i] = make_float4(f32_of(dx), f32_of(dy), f32_of(dz), __int_as_float(a.shape[i]));
+    return f32_of(d2);
 }
 
 // Warp max, one atomic per warp (non-negative floats order like their bits);
@@ -178,11 +215,11 @@ __device__ __forceinline__ void max_to_status(const StepArgs &a, float dmax) {
 __device__ __forceinline__ void store_ff_state(float4 *quatf_lo, float4 *xff, int i,
                                                const double4_32a &x, const double4_32a &q) {
     float h, l[4];
-    split_ff(q.x, &h, &l[0]); split_ff(q.y, &h, &l[1]);
-    split_ff(q.z, &h, &l[2]); split_ff(q.w, &h, &l[3]);
+    split_ff_dev(q.x, &h, &l[0]); split_ff_dev(q.y, &h, &l[1]);
+    split_ff_dev(q.z, &h, &l[2]); split_ff_dev(q.w, &h, &l[3]);
     quatf_lo[i] = make_float4(l[0], l[1], l[2], l[3]);
     float xh[3], xl[3];
-    split_ff(x.x, &xh[0], &xl[0]); split_ff(x.y, &xh[1], &xl[1]); split_ff(x.z, &xh[2], &xl[2]);
+    split_ff_dev(x.x, &xh[0], &xl[0]); split_ff_dev(x.y, &xh[1], &xl[1]); split_ff_dev(x.z, &xh[2], &xl[2]);
     xff[2 * i] = make_float4(xh[0], xh[1], xh[2], 0.f);
     xff[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.f);
 }
@@ -237,7 +274,7 @@ __device__ __forceinline__ float first_half_particle(const StepArgs &a, int i, c
     a.vel[i] = v;
     a.angmom[i] = L;
     a.quat[i] = q;
-    a.quatf[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+    a.quatf[i] = make_float4(f32_of(q.x), f32_of(q.y), f32_of(q.z), f32_of(q.w));
     if (a.quatf_lo) store_ff_state(a.quatf_lo, a.xff, i, x, q);
     return since_build(a, rp, i, x);
 }
