@@ -417,8 +417,22 @@ int dem_forces_noalloc(const dem_shape *shapes, int n_shapes, double epsilon, do
  * DEM_ERR_CUDA (dem_last_error(NULL) gives the reason). */
 int dem_fma_peak(int precision, int iters, double *tflops, double *ms);
 
+/* Self-check of the conversions between double and float that the
+ * integrator makes with integer operations on the IEEE-754 fields (to keep
+ * them off the FP64 pipe): n inputs, each a double (a quarter of them on a
+ * rounding tie, a quarter with exponents around the float range) and a
+ * float drawn by a counter-based hash (splitmix64) of seed + index, are
+ * converted both ways and compared with the conversion instructions (round
+ * to nearest even).  mismatches[0] counts double-to-float, mismatches[1]
+ * float-to-double differences (host array of 2).  The paper has no
+ * counterpart.  Allocates 16 bytes of device memory and a stream.  Errors:
+ * DEM_ERR_ARG, DEM_ERR_CUDA (dem_last_error(NULL) gives the reason). */
+int dem_check_conversions(unsigned long long n, unsigned long long seed,
+                          unsigned long long *mismatches);
+
 /* One-line description of the last error of ctx (or of the last failed
- * dem_create, dem_forces_noalloc or dem_fma_peak when ctx is NULL). */
+ * dem_create, dem_forces_noalloc, dem_fma_peak or dem_check_conversions
+ * when ctx is NULL). */
 const char *dem_last_error(const dem_ctx *ctx);
 
 void dem_destroy(dem_ctx *ctx);

@@ -177,6 +177,7 @@ struct PairArgs {
     int *term_info;           // owner | gi << 8 | gj << 16 | jref << 24
     int *term_start, *term_cnt;
     int term_capw;
+    int term_ppw;             // the term kernel's particles per warp (set at its launch)
     int mask_words;           // words per feature mask and incidence row: 1, or
                               // WIDE_WORDS when a shape has more than 32 features
 };
@@ -296,6 +297,8 @@ cudaError_t launch_prepare_state(int n, int dim, double4_32a *pos, double4_32a *
                                  float4 *quatf_lo, float4 *xff,
                                  double4_32a *angmom, const int *rep, const Rep *reps,
                                  int world_to_body, cudaStream_t s);
+cudaError_t launch_check_conversions(unsigned long long n, unsigned long long seed,
+                                    unsigned long long *bad, cudaStream_t s);
 // FP32 / float-float copies of an FP64 state restored unchanged (snapshots).
 cudaError_t launch_refresh_copies(int n, const double4_32a *pos, const double4_32a *quat,
                                   float4 *quatf, float4 *quatf_lo, float4 *xff, cudaStream_t s);

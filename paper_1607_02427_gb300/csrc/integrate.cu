@@ -254,6 +254,38 @@ __global__ void k_prepare(int n, int dim, double4_32a *pos, double4_32a *quat, f
     }
 }
 
+// Self-check of the integer-operation conversions (f32_of, f64_of) against
+// the conversion instructions: input k of a launch is bits of a counter-based
+// hash (splitmix64) of seed + k, taken as a double (with every fourth input
+// put on a rounding tie) and, its low word, as a float.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__global__ void k_check_conversions(unsigned long long n, unsigned long long seed,
+                                    unsigned long long *bad) {
+    unsigned long long nb0 = 0, nb1 = 0;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long r = splitmix64(seed + k);
+        unsigned long long u = r;
+        if ((k & 3) == 1)   // a tie: the 29 bits below a float's last place are 1000...0
+            u = (r & 0xffffffffe0000000ull) | 0x10000000ull;
+        else if ((k & 3) == 2)   // exponents around the float range
+            u = (r & 0x800fffffffffffffull) | (unsigned long long)(860 + (r >> 52) % 340) << 52;
+        const double x = __longlong_as_double((long long)u);
+        const float a = f32_of(x), b = __double2float_rn(x);
+        if (!(a != a && b != b) && __float_as_uint(a) != __float_as_uint(b)) ++nb0;
+        const float f = __uint_as_float((unsigned)r);
+        const double c = f64_of(f), d = (double)f;
+        if (!(c != c && d != d) && __double_as_longlong(c) != __double_as_longlong(d)) ++nb1;
+    }
+    if (nb0) atomicAdd(bad, nb0);
+    if (nb1) atomicAdd(bad + 1, nb1);
+}
+
 // The FP32 (and float-float) copies of positions and orientations from the
 // FP64 state, which is left as it is (a state restored from a snapshot).
 __global__ void k_refresh_copies(int n, const double4_32a *pos, const double4_32a *quat,
@@ -463,6 +495,11 @@ cudaError_t launch_prepare_state(int n, int dim, double4_32a *pos, double4_32a *
                                                reps, world_to_body);
     return cudaGetLastError();
 }
+cudaError_t launch_check_conversions(unsigned long long n, unsigned long long seed,
+                                    unsigned long long *bad, cudaStream_t s) {
+    k_check_conversions<<<1216, 256, 0, s>>>(n, seed, bad);
+    return cudaGetLastError();
+}
 cudaError_t launch_refresh_copies(int n, const double4_32a *pos, const double4_32a *quat,
                                   float4 *quatf, float4 *quatf_lo, float4 *xff, cudaStream_t s) {
     k_refresh_copies<<<grid_for(n, 256), 256, 0, s>>>(n, pos, quat, quatf, quatf_lo, xff);
@@ -498,3 +535,28 @@ cudaError_t launch_rescale(int n, int dim, double4_32a *pos, double4_32a *x_last
 }
 
 }  // namespace dem
+
+// ---- self-check of the conversions (C ABI) ----
+extern "C" int dem_check_conversions(unsigned long long n, unsigned long long seed,
+                                     unsigned long long *mismatches) {
+    if (!mismatches) {
+        dem::set_global_error("dem_check_conversions: mismatches is NULL");
+        return DEM_ERR_ARG;
+    }
+    unsigned long long *bad = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaMalloc(&bad, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess && n > 0) e = dem::launch_check_conversions(n, seed, bad, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mismatches, bad, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (st) cudaStreamDestroy(st);
+    if (bad) cudaFree(bad);
+    if (e != cudaSuccess) {
+        dem::set_global_error(std::string("dem_check_conversions: ") + cudaGetErrorString(e));
+        return DEM_ERR_CUDA;
+    }
+    return DEM_OK;
+}

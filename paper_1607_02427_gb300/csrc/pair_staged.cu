@@ -1014,8 +1014,9 @@ template <class T, bool COMP> constexpr int apply_blocks() {
 }
 
 // ---- SPLIT, FP32 + two-sum: the term kernel ----
-// One warp per 32 consecutive particles (32 / G groups of the feature
-// kernel).  The terms of its groups form one pool; each chunk of up to
+// One warp per P consecutive particles (P / G groups of the feature kernel;
+// P = 32 on large systems, down to G on small ones).  The terms of its
+// groups form one pool; each chunk of up to
 // TERM_CHUNK of them is put in order of term kind (stable: within a kind,
 // the order the feature kernel found them), so that the lanes of a round
 // mostly run the same code, and pooling keeps the rounds full when a group
@@ -1046,9 +1047,9 @@ __global__ void __launch_bounds__(SBLOCK, 4) k_pair_terms(const PairArgs a) {
     __syncthreads();
     const FFTab ft = {tab, tlo, itab};
     const float eps = (float)a.eps;
-    const int G = a.group, ng = 32 / G;
+    const int G = a.group, P = a.term_ppw, ng = P / G;   // P particles (ng groups) per warp
     const int nwarps = gridDim.x * wpb;
-    for (int base = (blockIdx.x * wpb + w) * 32; base < a.n; base += nwarps * 32) {
+    for (int base = (blockIdx.x * wpb + w) * P; base < a.n; base += nwarps * P) {
         SumSink<float, true> S;
         S.zero();
         // the pool: the terms of the warp's groups, group after group
@@ -1139,7 +1140,7 @@ __global__ void __launch_bounds__(SBLOCK, 4) k_pair_terms(const PairArgs a) {
             }
         }
         const int i = base + lane;
-        if (i < a.n) finish_particle(a, i, S, orientation<float>(a, i));
+        if (lane < P && i < a.n) finish_particle(a, i, S, orientation<float>(a, i));
         __syncwarp();
     }
 }
@@ -1287,16 +1288,24 @@ cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, 
         launch(k_pair_apply<T, COMP, DIM, false>, smem2);
     }
     if constexpr (COMP && std::is_same<T, float>::value) {
-        // the term kernel: one warp per 32 particles
+        // the term kernel: one warp per P particles, P = 32 when that fills
+        // the resident warps, else halved down to the group size, so that a
+        // small system's terms spread over more warps (the time of a warp's
+        // chain of rounds sets the kernel's time there)
         const size_t smem3 = t + table_lo_bytes(a, true) + (SBLOCK / 32) * (32 + 2 * TERM_CHUNK + 16) * sizeof(int);
         auto kernel = k_pair_terms<DIM>;
         if (smem3 > 48 * 1024)
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
-        const long long need3 = ((long long)a.n + SBLOCK - 1) / SBLOCK;
         const long long cap3 = (long long)blocks_per_sm(kernel, SBLOCK, smem3) * sm_count();
+        PairArgs b = a;
+        b.term_ppw = 32;
+        while (b.term_ppw > a.group && (long long)a.n < (long long)b.term_ppw * cap3 * (SBLOCK / 32))
+            b.term_ppw >>= 1;
+        const long long per_block = (long long)b.term_ppw * (SBLOCK / 32);
+        const long long need3 = ((long long)a.n + per_block - 1) / per_block;
         int grid3 = (int)(need3 < cap3 ? need3 : cap3);
         if (grid3 < 1) grid3 = 1;
-        kernel<<<grid3, SBLOCK, smem3, s>>>(a);
+        kernel<<<grid3, SBLOCK, smem3, s>>>(b);
     }
     return cudaGetLastError();
 }

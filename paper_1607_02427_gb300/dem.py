@@ -38,7 +38,7 @@ EXPORTS = ["dem_create", "dem_set_state", "dem_get_state", "dem_set_thermostat",
            "dem_get_virial", "dem_set_box", "dem_set_param", "dem_get_param", "dem_autotune",
            "dem_get_counters", "dem_set_stream", "dem_shape_info", "dem_last_error",
            "dem_destroy", "dem_forces_noalloc", "dem_set_barostat", "dem_get_box",
-           "dem_fma_peak"]
+           "dem_fma_peak", "dem_check_conversions"]
 DEM_NOALLOC_MAX_N = 16384
 DEM_NOALLOC_MAX_NEIGHBOURS = 64
 
@@ -94,6 +94,7 @@ def load():
         "dem_forces_noalloc": [C.POINTER(dem_shape), C.c_int, C.c_double, C.c_double, dp,
                                C.c_int, vp, vp, vp, C.c_int, vp, vp, vp, vp],
         "dem_fma_peak": [C.c_int, C.c_int, dp, dp],
+        "dem_check_conversions": [C.c_ulonglong, C.c_ulonglong, C.POINTER(C.c_ulonglong)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -285,6 +286,15 @@ def dem_fma_peak(precision: int, iters: int):
     t, ms = C.c_double(0.0), C.c_double(0.0)
     _check(load().dem_fma_peak(int(precision), int(iters), C.byref(t), C.byref(ms)))
     return t.value, ms.value
+
+
+def dem_check_conversions(n: int, seed: int = 1607_02427):
+    """Mismatches (double to float, float to double) of the integrator's
+    integer-operation conversions against the conversion instructions over n
+    hashed inputs."""
+    out = (C.c_ulonglong * 2)()
+    _check(load().dem_check_conversions(C.c_ulonglong(int(n)), C.c_ulonglong(int(seed)), out))
+    return int(out[0]), int(out[1])
 
 
 def dem_forces_noalloc(shapes: Sequence[dict], epsilon: float, sigma: float, box, shape_id,
