@@ -325,10 +325,11 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value);
  * parameters "autotune_ms_0" ... "autotune_ms_7".  Results are identical for
  * every choice up to floating-point summation order; the chosen one is the
  * "decomp", "block" and "split_group" parameters.
- * With "persistent" at -1 it then times a few NVT steps (dt = 1e-6, too short
- * to rebuild the list) with the per-step kernels and with the cooperative
- * multi-step kernel from the same state, keeps the faster for dem_step, and
- * puts the state back as it was. */
+ * With "persistent" at -1 and at most 65,536 particles it then times a few
+ * NVT steps (dt = 1e-6, too short to rebuild the list) with the per-step
+ * kernels and with the cooperative multi-step kernel from the same state,
+ * keeps the faster for dem_step, and puts the state back as it was; larger
+ * systems keep the per-step kernels. */
 int dem_autotune(dem_ctx *ctx);
 
 /* Work counters of one force evaluation at the current state (host array of

@@ -1510,7 +1510,8 @@ namespace {
 // overflow retry: the state is snapshotted, and after a list or cell overflow
 // the capacities grow and the steps are replayed from the snapshot.
 // ---- cooperative multi-step kernel ----
-constexpr int COOP_AUTO_MAX_N = 2048;
+constexpr int COOP_AUTO_MAX_N = 2048;    // before dem_autotune has timed both
+constexpr int COOP_TUNE_MAX_N = 65536;   // dem_autotune times it up to this size
 
 // Whether dem_step runs the cooperative kernel (NVE and NVT, one-word
 // feature masks, no pair-kernel profiling), and its grid (0: it cannot run).
@@ -1688,6 +1689,12 @@ int step_run(dem_ctx *ctx, int n, double dt, int ensemble, double kT, double tau
 // neither run rebuilds its list.
 int tune_persistent(dem_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1) {
     ctx->tune_step_ms[0] = ctx->tune_step_ms[1] = -1.f;
+    if (ctx->N > COOP_TUNE_MAX_N) {
+        // a thread per list entry cannot compete at this size (each would
+        // take many entries in turn); not worth its partial-sum buffer
+        ctx->coop_auto = 0;
+        return DEM_OK;
+    }
     if (ctx->mask_words != 1 || ctx->profile || coop_grid(ctx->precision, ctx->dim, ctx->N, ctx->cap,
                                                          pair_smem_bytes(pair_args(ctx), ctx->precision)) < 1)
         return DEM_OK;
@@ -1717,6 +1724,13 @@ int tune_persistent(dem_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1) {
     ctx->tune_step_ms[0] = ms[0];
     ctx->tune_step_ms[1] = ms[1];
     ctx->coop_auto = ms[1] < ms[0] ? 1 : 0;
+    if (!ctx->coop_auto) {   // its buffers are not needed
+        cudaFree(ctx->coop_part);
+        cudaFree(ctx->coop_act);
+        ctx->coop_part = nullptr;
+        ctx->coop_act = nullptr;
+        ctx->coop_part_bytes = ctx->coop_act_bytes = 0;
+    }
     rc = force_rebuild(ctx);
     if (rc) return rc;
     return compute_forces(ctx);
