@@ -114,6 +114,8 @@ def parse():
                    help="skip the e2e, FP64 and CPU-baseline measurements")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--decomp", default="auto", choices=["auto", "thread", "warp", "staged", "split"])
+    p.add_argument("--set", action="append", default=[], metavar="NAME=VALUE",
+                   help="a dem_set_param parameter, set after the autotune (repeatable)")
     p.add_argument("--execution", default="auto", choices=["auto", "graph", "persistent"],
                    help="dem_step's execution: as dem_autotune chose, per-step kernels replayed "
                         "from a CUDA graph, or the cooperative multi-step kernel")
@@ -403,6 +405,9 @@ def main():
         d.set_param("decomp", {"thread": 1, "warp": 2, "staged": 3, "split": 4}[a.decomp])
     if a.execution != "auto":
         d.set_param("persistent", 0 if a.execution == "graph" else 1)
+    for kv in a.set:
+        name, value = kv.split("=", 1)
+        d.set_param(name, float(value))
     decomp_name = {1: "thread", 2: "warp", 3: "staged", 4: "split"}[int(d.get_param("decomp"))]
     tune = {}
     if a.decomp == "auto":

@@ -281,6 +281,10 @@ int dem_set_box(dem_ctx *ctx, const double *box);
  *   "split_group" SPLIT decomposition: particles per warp, 4, 8, 16 or 32; 0
  *                 (default) takes 32, or fewer while N leaves the GPU
  *                 underfilled; get_param returns the size in use
+ *   "split_slice" SPLIT decomposition: particles per slice (0, the default: all
+ *                 at once).  The scan, feature and term kernels then run slice
+ *                 after slice, so that a slice's active-pair and term records
+ *                 are read back while they are still in L2
  *   "par_eps"     squared-sine threshold of the parallel-edge rule (1e-6)
  *   "decomp"      DEM_DECOMP_* of the pair kernel
  *   "block"       threads per block of the pair kernel (0 = default)

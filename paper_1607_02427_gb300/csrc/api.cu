@@ -473,6 +473,7 @@ struct dem_ctx {
     double P = 0.0, tau_P = 0.0;
     int npt_chunk = 100;
     int split_G = 0;                  // SPLIT particles per warp (0: from N)
+    int split_slice = 0;              // SPLIT particles per slice (0: all at once)
     bool split_user = false;          // split_G set by the caller (the autotuner keeps it)
     // device memory
     double4_32a *pos = nullptr, *vel = nullptr, *quat = nullptr, *angmom = nullptr;
@@ -759,6 +760,9 @@ PairArgs pair_args(dem_ctx *ctx) {
     a.recs = ctx->recs;
     a.rec_count = ctx->rec_count;
     a.group = ctx_split_group(ctx);
+    a.slice = ctx->split_slice;
+    a.p_lo = 0;
+    a.p_hi = ctx->N;
     a.mask_words = ctx->mask_words;
     if (ctx->precision == DEM_FP32_COMP) {
         a.quatf_lo = ctx->quatf_lo;
@@ -880,8 +884,10 @@ int launch_forces(dem_ctx *ctx, bool count, cudaEvent_t e0 = nullptr, cudaEvent_
     CK(launch_pair(pair_args(ctx), ctx->precision, ctx->decomp, ctx->block, count, ctx->stream));
     if (e1) CK(cudaEventRecordWithFlags(e1, ctx->stream, ev_flags));
     // SPLIT: scan and feature kernels, and in the FP32 + two-sum mode the term kernel
+    const int slice32 = (ctx->split_slice + 31) / 32 * 32;
+    const int slices = slice32 > 0 ? (ctx->N + slice32 - 1) / slice32 : 1;
     ctx->launches += 2 + (ctx->decomp == DEM_DECOMP_SPLIT
-                              ? (ctx->precision == DEM_FP32_COMP ? 3 : 2) : 1);
+                              ? (ctx->precision == DEM_FP32_COMP ? 3 : 2) * slices : 1);
     return DEM_OK;
 }
 
@@ -1315,6 +1321,9 @@ int dem_set_param(dem_ctx *ctx, const char *name, double value) {
         ctx->coop_wait_ms = value;
     } else if (n == "persistent_test_stall") {
         ctx->coop_test_stall = value != 0;
+    } else if (n == "split_slice") {
+        if (!(value >= 0 && value <= 1e9)) return set_err(ctx, DEM_ERR_ARG, "bad split_slice");
+        ctx->split_slice = (int)value;
     } else if (n == "term_cap") {
         int c = (int)value;
         if (c < 1 || c > (1 << 24)) return set_err(ctx, DEM_ERR_ARG, "bad term_cap");
@@ -1351,6 +1360,7 @@ int dem_get_param(dem_ctx *ctx, const char *name, double *value) {
     }
     else if (n == "nlist_cap") *value = ctx->cap;
     else if (n == "term_cap") *value = ctx->term_capw;
+    else if (n == "split_slice") *value = ctx->split_slice;
     else if (n == "persistent") *value = ctx->persistent;
     else if (n == "persistent_used") *value = ctx->coop_used;
     else if (n == "persistent_auto") *value = ctx->coop_auto;

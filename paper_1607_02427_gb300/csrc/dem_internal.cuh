@@ -178,6 +178,12 @@ struct PairArgs {
     int *term_start, *term_cnt;
     int term_capw;
     int term_ppw;             // the term kernel's particles per warp (set at its launch)
+    // SPLIT: particles per slice (0: all at once).  The three kernels run
+    // slice after slice, so that a slice's active-pair and term records are
+    // read back while they are still in L2; [p_lo, p_hi) is the slice of a
+    // launch (set at the launch)
+    int slice;
+    int p_lo, p_hi;
     int mask_words;           // words per feature mask and incidence row: 1, or
                               // WIDE_WORDS when a shape has more than 32 features
 };

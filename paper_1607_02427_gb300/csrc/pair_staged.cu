@@ -969,7 +969,7 @@ __global__ void __launch_bounds__(SBLOCK) k_pair_scan(const PairArgs a) {
     constexpr int QW = sizeof(GRec<T>) / sizeof(uint4);
     const int nwarps = gridDim.x * wpb;
     const int G = a.group;   // particles per warp (lanes G..31 hold none)
-    for (int base = (blockIdx.x * wpb + w) * G; base < a.n; base += nwarps * G) {
+    for (int base = a.p_lo + (blockIdx.x * wpb + w) * G; base < a.p_hi; base += nwarps * G) {
         const int g = base / G;
         const int nn_me = scan_particle<T>(a, ws.s, lane, lane < G ? base + lane : a.n);
         int total;
@@ -1049,7 +1049,7 @@ __global__ void __launch_bounds__(SBLOCK, 4) k_pair_terms(const PairArgs a) {
     const float eps = (float)a.eps;
     const int G = a.group, P = a.term_ppw, ng = P / G;   // P particles (ng groups) per warp
     const int nwarps = gridDim.x * wpb;
-    for (int base = (blockIdx.x * wpb + w) * P; base < a.n; base += nwarps * P) {
+    for (int base = a.p_lo + (blockIdx.x * wpb + w) * P; base < a.p_hi; base += nwarps * P) {
         SumSink<float, true> S;
         S.zero();
         // the pool: the terms of the warp's groups, group after group
@@ -1177,7 +1177,7 @@ __global__ void __launch_bounds__(SBLOCK, apply_blocks<T, COMP>())
                                                 APPLY_PR * sizeof(SPair<T>) - APPLY_PR * sizeof(GRec<T>));
     const int nwarps = gridDim.x * wpb;
     const int G = a.group;   // particles per warp (lanes G..31 own none)
-    for (int base = (blockIdx.x * wpb + w) * G; base < a.n; base += nwarps * G) {
+    for (int base = a.p_lo + (blockIdx.x * wpb + w) * G; base < a.p_hi; base += nwarps * G) {
         const int g = base / G;
         const int cnt = a.rec_count[g];
         const uint4 *in = reinterpret_cast<const uint4 *>(reinterpret_cast<const GRec<T> *>(a.recs) +
@@ -1266,11 +1266,12 @@ cudaError_t launch_prec(const PairArgs &a, bool count, size_t smem_tables, cudaS
 }
 
 template <class T, bool COMP, int DIM>
-cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
+cudaError_t launch_split_slice(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
     const size_t t = (smem_tables + 127) & ~(size_t)127;
     const size_t smem1 = t + (SBLOCK / 32) * sizeof(ScanBlockSmem<T>);
     const size_t smem2 = t + (SBLOCK / 32) * sizeof(BatchSmem<T, APPLY_PR>);
-    const int warps = (a.n + a.group - 1) / a.group;      // a.group particles per warp
+    const int np = a.p_hi - a.p_lo;
+    const int warps = (np + a.group - 1) / a.group;      // a.group particles per warp
     const long long need = (warps + SBLOCK / 32 - 1) / (SBLOCK / 32);
     auto launch = [&](auto kernel, size_t smem) {
         if (smem > 48 * 1024)
@@ -1299,13 +1300,30 @@ cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, 
         const long long cap3 = (long long)blocks_per_sm(kernel, SBLOCK, smem3) * sm_count();
         PairArgs b = a;
         b.term_ppw = 32;
-        while (b.term_ppw > a.group && (long long)a.n < (long long)b.term_ppw * cap3 * (SBLOCK / 32))
+        while (b.term_ppw > a.group && (long long)np < (long long)b.term_ppw * cap3 * (SBLOCK / 32))
             b.term_ppw >>= 1;
         const long long per_block = (long long)b.term_ppw * (SBLOCK / 32);
-        const long long need3 = ((long long)a.n + per_block - 1) / per_block;
+        const long long need3 = ((long long)np + per_block - 1) / per_block;
         int grid3 = (int)(need3 < cap3 ? need3 : cap3);
         if (grid3 < 1) grid3 = 1;
         kernel<<<grid3, SBLOCK, smem3, s>>>(b);
+    }
+    return cudaGetLastError();
+}
+
+// The SPLIT kernels over [0, n), slice after slice (slices of a multiple of
+// 32 particles, so that no group of the scan or warp of the term kernel
+// straddles two).
+template <class T, bool COMP, int DIM>
+cudaError_t launch_split_dim(const PairArgs &a, bool count, size_t smem_tables, cudaStream_t s) {
+    const int S = a.slice > 0 ? (a.slice + 31) / 32 * 32 : a.n;
+    for (int p0 = 0; p0 < a.n; p0 += S) {
+        PairArgs b = a;
+        b.p_lo = p0;
+        b.p_hi = a.n - p0 < S ? a.n : p0 + S;
+        const cudaError_t e = launch_split_slice<T, COMP, DIM>(b, count, smem_tables, s);
+        if (e != cudaSuccess) return e;
+        if (a.n == 0) break;
     }
     return cudaGetLastError();
 }

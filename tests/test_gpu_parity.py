@@ -276,3 +276,24 @@ def test_split_group_sizes(dem, name, precision, group):
         c_thread = d.counters()
     keep = [k for k in range(18) if k not in (3, 13, 14)]
     np.testing.assert_array_equal(c_split[keep], c_thread[keep])
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "fp32", "fp32c"])
+@pytest.mark.parametrize("name", ["mixed3d", "polys2d"])
+def test_split_slices(dem, name, precision):
+    """SPLIT run slice after slice (parameter split_slice): parity with the
+    oracle, and the same forces as one pass (each particle's terms keep their
+    order: the kind order within a warp's pool does not depend on the other
+    particles of the pool while a pool fits one chunk)."""
+    s = system(name)
+    errs, ref, out = compare_forces(dem, s, precision, decomp=4, split_slice=64)
+    assert_parity(errs, precision, f"{name}/split slices")
+    res = []
+    for sl in (0, 64, 96):
+        with dem.DEM(s, precision, decomp=4, split_slice=sl, persistent=0) as d:
+            res.append(d.forces())
+            d.step(10, 1e-3, dem.DEM_NVE)   # the step path (graph) with slices
+            assert np.isfinite(d.energy()[2]).all()
+    for f, t in res[1:]:
+        np.testing.assert_array_equal(f, res[0][0])
+        np.testing.assert_array_equal(t, res[0][1])
