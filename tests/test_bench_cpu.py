@@ -73,3 +73,20 @@ def test_cli_flags_exist(flag):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"],
                        capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert r.returncode == 0 and flag in r.stdout
+
+
+def test_options_parse(monkeypatch):
+    """The bench's options for profiling and for the library's parameters:
+    the defaults keep the driver's contract (N = 1, autotuned execution), and
+    --set takes NAME=VALUE pairs that main() hands to dem_set_param."""
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.execution == "auto" and a.set == [] and a.profile_evals == 0
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--execution", "graph", "--set", "split_slice=131072",
+                                      "--set", "skin=0.3", "--profile-evals", "2"])
+    a = bench.parse()
+    assert a.execution == "graph" and a.profile_evals == 2
+    assert [kv.split("=", 1) for kv in a.set] == [["split_slice", "131072"], ["skin", "0.3"]]
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--execution", "fast"])
+    with pytest.raises(SystemExit):
+        bench.parse()
