@@ -865,6 +865,9 @@ StepArgs step_args(dem_ctx *ctx, double dt, int ens, double kT, double tau) {
     a.direct_sums = !a.npt && ctx->max_rep <= DIRECT_MAX;
     a.quatf_lo = ctx->quatf_lo;
     a.xff = ctx->xff;
+    // the integer-operation conversions pay where the first half step is
+    // bound by the FP64 pipe, on large systems
+    a.int_conv = ctx->N >= 32768;
     return a;
 }
 

@@ -240,6 +240,8 @@ struct StepArgs {
     int direct_sums;         // NVE/NVT, every replica small: k_thermo_end sums the kinetic
                              // energies itself and, under NVT, applies the second scaling
     float4 *quatf_lo, *xff;  // FP32 + two-sum: hi + lo state (NULL otherwise)
+    int int_conv;            // the first half step converts double <-> float by integer
+                             // operations (large systems) or by the instructions
 };
 
 // Cooperative multi-step kernel (persistent.cu): control block in device

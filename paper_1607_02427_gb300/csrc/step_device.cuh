@@ -16,7 +16,10 @@ namespace {
 // IEEE-754 fields, with the results of the conversion instructions (round to
 // nearest, ties to even): those run on the FP64 pipe, a small fraction of the
 // FP32 rate on this part, and the first half step makes about forty per
-// particle.  Results outside the normal float range (subnormal, overflow,
+// particle.  On large systems that step is bound by the FP64 pipe and the
+// integer form is faster; on small ones it is bound by latency and the
+// instruction's shorter chain is (StepArgs.int_conv chooses; the results are
+// the same).  Results outside the normal float range (subnormal, overflow,
 // infinities, NaN), which the state never produces, take the instruction.
 __device__ __forceinline__ float f32_of(double x) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
@@ -42,11 +45,13 @@ __device__ __forceinline__ double f64_of(float x) {
     return __longlong_as_double((long long)(sign | (unsigned long long)(e + 896u) << 52 |
                                             (unsigned long long)(b & 0x7fffffu) << 29));
 }
+__device__ __forceinline__ float cvt_f(double x, bool ic) { return ic ? f32_of(x) : (float)x; }
+__device__ __forceinline__ double cvt_d(float x, bool ic) { return ic ? f64_of(x) : (double)x; }
 // x = h + l (h = x rounded to float, l = the rest rounded to float)
-__device__ __forceinline__ void split_ff_dev(double x, float *h, float *l) {
-    const float hi = f32_of(x);
+__device__ __forceinline__ void split_ff_dev(double x, float *h, float *l, bool ic) {
+    const float hi = cvt_f(x, ic);
     *h = hi;
-    *l = f32_of(x - f64_of(hi));
+    *l = cvt_f(x - cvt_d(hi, ic), ic);
 }
 
 __device__ __forceinline__ void quat_rotate_body(double4_32a &q, int k, double c, double s) {
@@ -127,9 +132,9 @@ __device__ __forceinline__ void sincosm1_f(float h, float *s, float *cm1) {
 // q += q rho.  The increments are of order h ~ dt |L| / I, so their FP32
 // rounding is of order 1e-7 h: far below the FP32 force error.
 __device__ __forceinline__ void free_rotor_f32(double4_32a &q, double4_32a &L, const double *invI,
-                                               double dt) {
-    const float ii[3] = {f32_of(invI[0]), f32_of(invI[1]), f32_of(invI[2])};
-    float Lc[3] = {f32_of(L.x), f32_of(L.y), f32_of(L.z)};
+                                               double dt, bool ic) {
+    const float ii[3] = {cvt_f(invI[0], ic), cvt_f(invI[1], ic), cvt_f(invI[2], ic)};
+    float Lc[3] = {cvt_f(L.x, ic), cvt_f(L.y, ic), cvt_f(L.z, ic)};
     float dL[3] = {0.f, 0.f, 0.f};
     float rw = 0.f, rv[3] = {0.f, 0.f, 0.f};
     const float hd = (float)(0.25 * dt);
@@ -159,13 +164,13 @@ __device__ __forceinline__ void free_rotor_f32(double4_32a &q, double4_32a &L, c
         rv[0] = nv[0]; rv[1] = nv[1]; rv[2] = nv[2];
     }
     // q rho in FP32, added to the FP64 quaternion; q = (x: w, y: x, z: y, w: z)
-    const float qw = f32_of(q.x), qx = f32_of(q.y), qy = f32_of(q.z), qz = f32_of(q.w);
+    const float qw = cvt_f(q.x, ic), qx = cvt_f(q.y, ic), qy = cvt_f(q.z, ic), qz = cvt_f(q.w, ic);
     const float dw = qw * rw - (qx * rv[0] + qy * rv[1] + qz * rv[2]);
     const float dx = qw * rv[0] + rw * qx + (qy * rv[2] - qz * rv[1]);
     const float dy = qw * rv[1] + rw * qy + (qz * rv[0] - qx * rv[2]);
     const float dz = qw * rv[2] + rw * qz + (qx * rv[1] - qy * rv[0]);
-    q.x += f64_of(dw); q.y += f64_of(dx); q.z += f64_of(dy); q.w += f64_of(dz);
-    L.x += f64_of(dL[0]); L.y += f64_of(dL[1]); L.z += f64_of(dL[2]);
+    q.x += cvt_d(dw, ic); q.y += cvt_d(dx, ic); q.z += cvt_d(dy, ic); q.w += cvt_d(dz, ic);
+    L.x += cvt_d(dL[0], ic); L.y += cvt_d(dL[1], ic); L.z += cvt_d(dL[2], ic);
 }
 
 // x mapped into [0, L) (invL = 1/L)
@@ -198,8 +203,9 @@ __device__ __forceinline__ float since_build(const StepArgs &a, const Rep &rp, i
         const double d = sqrt(d2) + (double)rp.disp_pad;
         d2 = d * d;
     }
-    a.delta[i] = make_float4(f32_of(dx), f32_of(dy), f32_of(dz), __int_as_float(a.shape[i]));
-    return f32_of(d2);
+    const bool ic = a.int_conv != 0;
+    a.delta[i] = make_float4(cvt_f(dx, ic), cvt_f(dy, ic), cvt_f(dz, ic), __int_as_float(a.shape[i]));
+    return cvt_f(d2, ic);
 }
 
 // Warp max, one atomic per warp (non-negative floats order like their bits);
@@ -213,13 +219,15 @@ __device__ __forceinline__ void max_to_status(const StepArgs &a, float dmax) {
 // FP32 + two-sum mode: the position and the quaternion as hi + lo floats
 // (the hi part of the quaternion is quatf).
 __device__ __forceinline__ void store_ff_state(float4 *quatf_lo, float4 *xff, int i,
-                                               const double4_32a &x, const double4_32a &q) {
+                                               const double4_32a &x, const double4_32a &q,
+                                               bool ic = false) {
     float h, l[4];
-    split_ff_dev(q.x, &h, &l[0]); split_ff_dev(q.y, &h, &l[1]);
-    split_ff_dev(q.z, &h, &l[2]); split_ff_dev(q.w, &h, &l[3]);
+    split_ff_dev(q.x, &h, &l[0], ic); split_ff_dev(q.y, &h, &l[1], ic);
+    split_ff_dev(q.z, &h, &l[2], ic); split_ff_dev(q.w, &h, &l[3], ic);
     quatf_lo[i] = make_float4(l[0], l[1], l[2], l[3]);
     float xh[3], xl[3];
-    split_ff_dev(x.x, &xh[0], &xl[0]); split_ff_dev(x.y, &xh[1], &xl[1]); split_ff_dev(x.z, &xh[2], &xl[2]);
+    split_ff_dev(x.x, &xh[0], &xl[0], ic); split_ff_dev(x.y, &xh[1], &xl[1], ic);
+    split_ff_dev(x.z, &xh[2], &xl[2], ic);
     xff[2 * i] = make_float4(xh[0], xh[1], xh[2], 0.f);
     xff[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.f);
 }
@@ -256,7 +264,7 @@ __device__ __forceinline__ float first_half_particle(const StepArgs &a, int i, c
         if (a.dim == 3) x.z = wrap(x.z + a.dt * v.z, rp.L[2], rp.inv_L[2]);
     }
     if (a.rotor32) {
-        free_rotor_f32(q, L, sh.inv_inertia, a.dt);
+        free_rotor_f32(q, L, sh.inv_inertia, a.dt, a.int_conv != 0);
     } else {
         free_rotor_axis(q, L, sh.inv_inertia, 2, 0.5 * a.dt);
         free_rotor_axis(q, L, sh.inv_inertia, 1, 0.5 * a.dt);
@@ -274,8 +282,9 @@ __device__ __forceinline__ float first_half_particle(const StepArgs &a, int i, c
     a.vel[i] = v;
     a.angmom[i] = L;
     a.quat[i] = q;
-    a.quatf[i] = make_float4(f32_of(q.x), f32_of(q.y), f32_of(q.z), f32_of(q.w));
-    if (a.quatf_lo) store_ff_state(a.quatf_lo, a.xff, i, x, q);
+    const bool ic = a.int_conv != 0;
+    a.quatf[i] = make_float4(cvt_f(q.x, ic), cvt_f(q.y, ic), cvt_f(q.z, ic), cvt_f(q.w, ic));
+    if (a.quatf_lo) store_ff_state(a.quatf_lo, a.xff, i, x, q, ic);
     return since_build(a, rp, i, x);
 }
 
