@@ -1715,7 +1715,11 @@ int tune_persistent(dem_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1) {
     const int warm = 2, steps = 20;
     int rc = snapshot(ctx, false);
     if (rc) return rc;
-    const int keep_persistent = ctx->persistent;
+    struct KeepPersistent {   // the setting comes back however this returns
+        dem_ctx *c;
+        int v;
+        ~KeepPersistent() { c->persistent = v; }
+    } keep{ctx, ctx->persistent};
     float ms[2] = {-1.f, -1.f};
     for (int mode = 0; mode < 2 && rc == DEM_OK; ++mode) {
         ctx->persistent = mode;
@@ -1732,8 +1736,18 @@ int tune_persistent(dem_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1) {
             rc = snapshot(ctx, true);
         }
     }
-    ctx->persistent = keep_persistent;
-    if (rc != DEM_OK) return rc;
+    ctx->persistent = keep.v;
+    if (rc == DEM_ERR_CUDA || rc == DEM_ERR_NOMEM) return rc;
+    if (rc != DEM_OK) {
+        // these steps could not run here (e.g. a thermostat without degrees
+        // of freedom): the state from before them, and the choice by size
+        rc = snapshot(ctx, true);
+        if (rc) return rc;
+        ctx->err.clear();
+        rc = force_rebuild(ctx);
+        if (rc) return rc;
+        return compute_forces(ctx);
+    }
     ctx->tune_step_ms[0] = ms[0];
     ctx->tune_step_ms[1] = ms[1];
     ctx->coop_auto = ms[1] < ms[0] ? 1 : 0;
