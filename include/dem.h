@@ -100,9 +100,12 @@ extern "C" {
                                 then the queued survivors (face nearest point,
                                 segment-segment, WCA terms) 32 at a time       */
 #define DEM_DECOMP_SPLIT 4   /* STAGED in two kernels: a list scan writes the
-                                active pairs of every 32 particles to device
-                                memory (N * nlist_cap records), a feature
-                                kernel runs the queues on them                 */
+                                active pairs of each group of G particles
+                                ("split_group") to device memory (N *
+                                nlist_cap records), a feature kernel runs the
+                                queues on them; with DEM_FP32_COMP a third
+                                kernel refines the terms the feature kernel
+                                found                                          */
 
 typedef struct dem_ctx dem_ctx;   /* opaque; owned by the library */
 
